@@ -1,0 +1,162 @@
+/*
+ * hif.h -- C ABI of the GB300 hierarchical interpolative factorization (HIF).
+ *
+ * Method: Li & Ying, "Distributed-memory Hierarchical Interpolative
+ * Factorization" (arXiv:1607.00346).  The library factors the seven-point
+ * discretisation A of
+ *
+ *     -div(a grad u) + b u = f          (§1, eq. 1; stencil of §2.4)
+ *
+ * on an n x n x n interior grid of the unit cube with zero Dirichlet
+ * boundary (h = 1/(n+1); half-point coefficients are harmonic means of the
+ * grid values, a_j towards the boundary), as A ~= F with
+ *
+ *     F^{-1} = W^0 ... W^{L-1} W^L D^{-1} W^{L T} ... W^{0 T}     (§2.4)
+ *
+ * where every W^l is the product of the level's sparse eliminations S_I
+ * (§2.2) and skeletonizations Q_F S_F~ of faces and edges (§2.3).
+ *
+ * Conventions for every entry point:
+ *   - A grid function is a double array of n^3 values, point (j1,j2,j3) at
+ *     index j1 + n*j2 + n*n*j3.  nrhs right-hand sides are stored one after
+ *     the other (column j at offset j*n^3).
+ *   - Array pointers may point to host memory or to device memory of the
+ *     current CUDA device; the library detects which and copies host data
+ *     in and out itself.  The caller keeps ownership of all its arrays.
+ *   - Calls are ordered on the given stream.  hif_factor synchronises the
+ *     stream a few times per level (the ranks found by the interpolative
+ *     decompositions decide the next level's sizes); hif_apply returns
+ *     without synchronising when f and u are device pointers; hif_solve
+ *     synchronises once per iteration to test convergence.
+ *   - Errors are returned as hif_status, never thrown.  hif_last_error()
+ *     gives a message for the calling thread's last failure.  After an error
+ *     in hif_factor, *out is NULL and nothing is leaked.
+ *   - A handle may be used from one thread at a time.
+ */
+#ifndef HIF_H_
+#define HIF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hif_handle_s* hif_handle;
+typedef struct CUstream_st* hif_stream;   /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  HIF_OK = 0,
+  HIF_ERR_INVALID_ARG = 1,     /* bad size, NULL pointer, a <= 0 or NaN, n not m*2^L */
+  HIF_ERR_OOM = 2,             /* device allocation failed */
+  HIF_ERR_NOT_SPD = 3,         /* a Cholesky pivot was not positive */
+  HIF_ERR_NO_CONVERGENCE = 4,  /* hif_solve reached max_iter */
+  HIF_ERR_TIMEOUT = 5,         /* a bounded device-side wait expired */
+  HIF_ERR_CUDA = 6             /* any other CUDA runtime error */
+} hif_status;
+
+/* Grid (§2.1): n = m 2^L points per dimension, leaf cells of side m. */
+typedef struct {
+  int n;
+  int m;
+  int bc;        /* 0 = zero Dirichlet (the only value accepted) */
+} hif_grid;
+
+enum { HIF_PREC_FP64 = 0, HIF_PREC_FP32 = 1 };
+
+typedef struct {
+  double eps;        /* relative precision of the ID (Table 2); 0 = no
+                        skeletonization: exact nested-dissection elimination */
+  int precision;     /* HIF_PREC_FP64: every factor block in double.
+                        HIF_PREC_FP32: factor blocks in float (ID column
+                        norms still accumulated in double); hif_solve keeps
+                        the residual r = f - A u in double. */
+  int use_graphs;    /* 1: capture each hif_apply sweep in a CUDA graph */
+  double pcg_tol;    /* hif_solve stops when ||r||_2 <= pcg_tol ||f||_2 */
+  int max_iter;      /* hif_solve iteration limit */
+} hif_options;
+
+/* Fill *opt with defaults: eps 1e-6, FP64, graphs on, pcg_tol 1e-10, 200 its. */
+void hif_default_options(hif_options* opt);
+
+/*
+ * hif_factor -- build F ~= A (§2.4; level loop, then the root of level L).
+ *   grid:  n, m with n = m 2^L, L >= 1, n <= 1024.
+ *   a:     n^3 doubles, every value finite and > 0 (host or device).
+ *   b:     n^3 doubles (host or device), or NULL to use b_const everywhere;
+ *          every value finite and >= 0.
+ *   opt:   options (NULL = defaults).
+ *   out:   receives the handle; the handle owns every device buffer of the
+ *          factor until hif_destroy.
+ * Errors: INVALID_ARG, OOM, NOT_SPD, TIMEOUT, CUDA.
+ */
+hif_status hif_factor(const hif_grid* grid, const double* a, const double* b,
+                      double b_const, const hif_options* opt, hif_stream stream,
+                      hif_handle* out);
+
+/*
+ * hif_apply -- u = F^{-1} f for nrhs right-hand sides (§2.4: the forward
+ * sweep W^{0T} ... W^{(L-1)T}, the root solve, then W^{L-1} ... W^0).
+ * f and u hold nrhs*n^3 doubles; they may alias (in-place apply).
+ */
+hif_status hif_apply(hif_handle h, const double* f, double* u, int nrhs,
+                     hif_stream stream);
+
+/*
+ * hif_residual -- r = f - A u with the handle's operator, in double.
+ */
+hif_status hif_residual(hif_handle h, const double* f, const double* u,
+                        double* r, int nrhs, hif_stream stream);
+
+/*
+ * hif_solve -- solve A u = f by conjugate gradients preconditioned with
+ * F^{-1} (replaces the GMRES of Table 2; F^{-1} is SPD).  Each column is
+ * iterated until ||r||_2 <= pcg_tol ||f||_2 (residual in double).  u is
+ * the output only (the iteration starts from zero).  iters and relres, when
+ * not NULL, receive per column the iteration count and the final relative
+ * residual (nrhs entries each, host memory).
+ * Errors: NO_CONVERGENCE when a column did not converge in max_iter
+ * iterations (u then holds the last iterate).
+ */
+hif_status hif_solve(hif_handle h, const double* f, double* u, int nrhs,
+                     hif_stream stream, int* iters, double* relres);
+
+/* Per-factorization statistics, filled by hif_query_stats. */
+typedef struct {
+  int n, m, levels, precision;
+  double eps;
+  int root_size;                 /* |Sigma^L| (Table 2) */
+  int64_t active_after[16];      /* |Sigma^{l+1}| after level l */
+  int64_t fronts[16][3];         /* cells, skeletonized faces, edges per level */
+  double factor_seconds;         /* wall time of hif_factor */
+  double level_seconds[17];      /* per level, then the root */
+  double flops;                  /* algorithmic flops of the factorization */
+  size_t factor_bytes;           /* device bytes held by the handle */
+  size_t peak_bytes;             /* peak device bytes during hif_factor */
+  int64_t stored_entries;        /* factor entries read by one apply sweep */
+  int kernel_launches;           /* kernels launched by hif_factor */
+  int apply_launches;            /* kernels launched by one hif_apply (nrhs = 1) */
+} hif_stats;
+
+hif_status hif_query_stats(hif_handle h, hif_stats* st);
+
+/*
+ * hif_predict_bytes -- device bytes hif_factor is expected to need at its
+ * peak for this grid and options (used for admission control).
+ */
+size_t hif_predict_bytes(const hif_grid* grid, const hif_options* opt);
+
+/* Release every resource of the handle (NULL is ignored). */
+void hif_destroy(hif_handle h);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char* hif_last_error(void);
+
+/* Library version string. */
+const char* hif_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HIF_H_ */

@@ -1,0 +1,83 @@
+// Internal definitions shared by the HIF CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/hif.h"
+
+namespace hif {
+
+// ---- error plumbing ---------------------------------------------------------
+
+struct Error {
+  hif_status code;
+  std::string msg;
+};
+
+void set_last_error(const std::string& msg);
+
+#define HIF_CUDA_TRY(expr)                                                        \
+  do {                                                                            \
+    cudaError_t e_ = (expr);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      throw ::hif::Error{e_ == cudaErrorMemoryAllocation ? HIF_ERR_OOM            \
+                                                          : HIF_ERR_CUDA,         \
+                         std::string(#expr) + ": " + cudaGetErrorString(e_)};     \
+    }                                                                             \
+  } while (0)
+
+// Every kernel launch is followed by HIF_CHECK_LAUNCH(), which also counts it.
+int64_t& launch_counter();
+#define HIF_CHECK_LAUNCH()                 \
+  do {                                     \
+    ++::hif::launch_counter();             \
+    HIF_CUDA_TRY(cudaGetLastError());      \
+  } while (0)
+
+// ---- device-side error flags -------------------------------------------------
+// Kernels never trap.  A failed Cholesky pivot (not positive or not finite)
+// records the front index in flags[0] (first failure wins) and the kernel
+// carries on with a harmless value so that the launch finishes normally.
+enum : int { FLAG_NOT_SPD = 0, FLAG_COUNT = 4 };
+
+// ---- work descriptors ---------------------------------------------------------
+
+// A dense front: an n x n column-major frontal matrix K (ld = n) whose first p
+// columns are eliminated (partial Cholesky), and an n x p factor panel P
+// (ld = n) that receives [Linv; X^T] (Linv = L^{-1} of the leading p x p block).
+struct DFront {
+  int64_t K;     // element offset of K in the K arena
+  int64_t P;     // element offset of P in the factor arena
+  int n;
+  int p;
+  int id;        // front number (reported on failure)
+  int pad;
+};
+
+// Batched matrix product C (m x n) = beta C + alpha op(A) op(B) with k inner.
+struct GemmOp {
+  int64_t A, B, C;   // element offsets from the A, B and C base pointers of the launch
+  int m, n, k;
+  int lda, ldb, ldc;
+  int transA, transB;
+  float alpha, beta;
+};
+
+// Batched matrix-vector product on a front of the apply (see apply kernels).
+struct GemvOp {
+  int64_t M;      // element offset of the matrix in the factor arena
+  int64_t x;      // offset of the input vector in the work arena
+  int64_t y;      // offset of the output vector in the work arena
+  int rows, cols; // matrix shape (column-major)
+  int ld;
+  int tri;        // 1: matrix is lower triangular (only r >= c read)
+  float alpha;
+  int beta_one;   // 1: y += alpha op(M) x ; 0: y = alpha op(M) x
+};
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace hif

@@ -1,0 +1,508 @@
+// Batched dense kernels over uneven fronts: partial Cholesky (panel factor +
+// triangular solve + trailing rank-NB update), inverse of the Cholesky factor,
+// generic batched GEMM and the batched GEMV of the apply sweeps.
+//
+// Every kernel takes a descriptor array (one entry per front or problem) and a
+// 2-D grid: blockIdx.y = descriptor, blockIdx.x = tile / chunk inside it.
+// Fronts whose work is finished, and tiles outside a front, exit at once.
+#include <algorithm>
+#include <vector>
+
+#include "dense.cuh"
+
+namespace hif {
+
+namespace {
+
+constexpr int PANEL_ROWS = 128;   // rows solved per CTA in the panel kernel
+constexpr int KC = 16;            // inner-dimension chunk of the tile products
+constexpr int MAX_GRID_Y = 65535;
+
+__device__ __forceinline__ void flag_front(int* flags, int which, int id) {
+  atomicCAS(&flags[which], -1, id);
+}
+
+// ---- tile micro-kernel ---------------------------------------------------------
+// 256 threads, 64 x 64 output, thread t owns rows (t % 16)*4 .. +4 and columns
+// (t / 16)*4 .. +4.  As[k][r] and Bs[k][c] hold a KC-deep slice.
+template <typename T>
+struct TileAcc {
+  T v[4][4];
+  __device__ void zero() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[i][j] = T(0);
+  }
+  __device__ void mma(const T (*As)[TILE + 4], const T (*Bs)[TILE + 4], int kdepth) {
+    const int tr = (threadIdx.x % 16) * 4, tc = (threadIdx.x / 16) * 4;
+    for (int k = 0; k < kdepth; ++k) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][tr + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tc + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[i][j] = fma(a[i], b[j], v[i][j]);
+    }
+  }
+};
+
+// ---- panel: Cholesky of the diagonal block + triangular solve of the rows below
+template <typename T>
+__global__ void __launch_bounds__(PANEL_ROWS) k_panel(const DFront* __restrict__ fr, T* Kar,
+                                                      T* Par, int j0, int* flags) {
+  const DFront d = fr[blockIdx.y];
+  if (j0 >= d.p) return;
+  const int jb = min(NB, d.p - j0);
+  const int j1 = j0 + jb;
+  const int n = d.n;
+  const int r0 = j1 + blockIdx.x * PANEL_ROWS;
+  if (blockIdx.x > 0 && r0 >= n) return;
+  T* K = Kar + d.K;
+  T* P = Par + d.P;
+  __shared__ T D[NB][NB + 1];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NB * NB; e += PANEL_ROWS) {
+    int r = e % NB, c = e / NB;
+    T v = T(0);
+    if (r < jb && c < jb && r >= c) v = K[(int64_t)(j0 + r) + (int64_t)(j0 + c) * n];
+    D[r][c] = v;
+  }
+  __syncthreads();
+  // right-looking Cholesky of the jb x jb diagonal block in shared memory
+  for (int c = 0; c < jb; ++c) {
+    if (tid == 0) {
+      T dv = D[c][c];
+      if (!(dv > T(0)) || !isfinite(dv)) {
+        flag_front(flags, FLAG_NOT_SPD, d.id);
+        dv = T(1);
+      }
+      D[c][c] = sqrt(dv);
+    }
+    __syncthreads();
+    const T piv = D[c][c];
+    if (tid > c && tid < jb) D[tid][c] /= piv;
+    __syncthreads();
+    if (tid > c && tid < jb) {
+      const T lrc = D[tid][c];
+      for (int cc = c + 1; cc <= tid; ++cc) D[tid][cc] -= lrc * D[cc][c];
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0) {
+    for (int e = tid; e < jb * jb; e += PANEL_ROWS) {
+      int r = e % jb, c = e / jb;
+      P[(int64_t)(j0 + r) + (int64_t)(j0 + c) * n] = r >= c ? D[r][c] : T(0);
+    }
+  }
+  const int r = r0 + tid;
+  if (r >= n) return;
+  T x[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) x[c] = c < jb ? K[(int64_t)r + (int64_t)(j0 + c) * n] : T(0);
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    if (c < jb) {
+      T s = x[c];
+#pragma unroll
+      for (int l = 0; l < c; ++l) s = fma(-x[l], D[c][l], s);
+      x[c] = s / D[c][c];
+    }
+  }
+  const bool toP = r >= d.p;
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    if (c < jb) {
+      const int64_t o = (int64_t)r + (int64_t)(j0 + c) * n;
+      K[o] = x[c];
+      if (toP) P[o] = x[c];
+    }
+  }
+}
+
+__device__ __forceinline__ void tri_index(int t, int& ti, int& tj) {
+  int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (i * (i + 1) / 2 > t) --i;
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  ti = i;
+  tj = t - i * (i + 1) / 2;
+}
+
+// ---- trailing update: K[j1:n, j1:n] -= K[j1:n, j0:j1] K[j1:n, j0:j1]^T (lower tiles)
+template <typename T>
+__global__ void __launch_bounds__(256) k_syrk(const DFront* __restrict__ fr, T* Kar, int j0) {
+  const DFront d = fr[blockIdx.y];
+  if (j0 >= d.p) return;
+  const int jb = min(NB, d.p - j0);
+  const int j1 = j0 + jb;
+  const int n = d.n;
+  const int nt = (n - j1 + TILE - 1) / TILE;
+  if ((int)blockIdx.x >= nt * (nt + 1) / 2) return;
+  int ti, tj;
+  tri_index(blockIdx.x, ti, tj);
+  const int rb = j1 + ti * TILE, cb = j1 + tj * TILE;
+  T* K = Kar + d.K;
+  __shared__ T As[KC][TILE + 4];
+  __shared__ T Bs[KC][TILE + 4];
+  TileAcc<T> acc;
+  acc.zero();
+  for (int k0 = 0; k0 < jb; k0 += KC) {
+    for (int e = threadIdx.x; e < KC * TILE; e += 256) {
+      int rr = e % TILE, kk = e / TILE;
+      int col = j0 + k0 + kk;
+      bool kin = k0 + kk < jb;
+      As[kk][rr] = (kin && rb + rr < n) ? K[(int64_t)(rb + rr) + (int64_t)col * n] : T(0);
+      Bs[kk][rr] = (kin && cb + rr < n) ? K[(int64_t)(cb + rr) + (int64_t)col * n] : T(0);
+    }
+    __syncthreads();
+    acc.mma(As, Bs, KC);
+    __syncthreads();
+  }
+  const int tr = (threadIdx.x % 16) * 4, tc = (threadIdx.x / 16) * 4;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = cb + tc + j;
+    if (c >= n) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = rb + tr + i;
+      if (r < n && r >= c) K[(int64_t)r + (int64_t)c * n] -= acc.v[i][j];
+    }
+  }
+}
+
+// ---- inverse of the diagonal NB x NB blocks of L (held in P) in place ----------
+template <typename T>
+__global__ void __launch_bounds__(NB) k_trtri_diag(const DFront* __restrict__ fr, T* Par) {
+  const DFront d = fr[blockIdx.y];
+  const int i0 = blockIdx.x * NB;
+  if (i0 >= d.p) return;
+  const int ib = min(NB, d.p - i0);
+  const int n = d.n;
+  T* P = Par + d.P;
+  __shared__ T Ls[NB][NB + 1];
+  __shared__ T Zs[NB][NB + 1];
+  for (int e = threadIdx.x; e < NB * NB; e += NB) {
+    int r = e % NB, c = e / NB;
+    Ls[r][c] = (r < ib && c < ib && r >= c) ? P[(int64_t)(i0 + r) + (int64_t)(i0 + c) * n] : T(0);
+  }
+  __syncthreads();
+  const int c = threadIdx.x;   // one column of the inverse per thread
+  if (c < ib) {
+    for (int r = 0; r < c; ++r) Zs[r][c] = T(0);
+    Zs[c][c] = T(1) / Ls[c][c];
+    for (int r = c + 1; r < ib; ++r) {
+      T s = T(0);
+      for (int l = c; l < r; ++l) s = fma(Ls[r][l], Zs[l][c], s);
+      Zs[r][c] = -s / Ls[r][r];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < ib * ib; e += NB) {
+    int r = e % ib, cc = e / ib;
+    P[(int64_t)(i0 + r) + (int64_t)(i0 + cc) * n] = Zs[r][cc];
+  }
+}
+
+// ---- block row i of Linv: Z_ij = -Z_ii sum_{k=j}^{i-1} L_ik Z_kj  (j < i) -------
+template <typename T>
+__global__ void __launch_bounds__(256) k_trtri_row(const DFront* __restrict__ fr, const T* Kar,
+                                                   T* Par, int bi) {
+  const DFront d = fr[blockIdx.y];
+  const int i0 = bi * NB;
+  if (i0 >= d.p) return;
+  const int bj = blockIdx.x;
+  if (bj >= bi) return;
+  const int ib = min(NB, d.p - i0);
+  const int n = d.n;
+  const T* K = Kar + d.K;
+  T* P = Par + d.P;
+  __shared__ T As[KC][TILE + 4];
+  __shared__ T Bs[KC][TILE + 4];
+  __shared__ T Ss[TILE][TILE + 4];
+  TileAcc<T> acc;
+  acc.zero();
+  const int j0 = bj * NB;
+  for (int kb = bj; kb < bi; ++kb) {
+    const int k0b = kb * NB;
+    for (int k0 = 0; k0 < NB; k0 += KC) {
+      for (int e = threadIdx.x; e < KC * TILE; e += 256) {
+        int rr = e % TILE, kk = e / TILE;
+        // A = L_ik (rows of block i, columns of block k) read from K
+        As[kk][rr] = rr < ib ? K[(int64_t)(i0 + rr) + (int64_t)(k0b + k0 + kk) * n] : T(0);
+        // B = Z_kj stored transposed: Bs[kk][c] = Z_kj[k0+kk][c]
+        Bs[kk][rr] = P[(int64_t)(k0b + k0 + kk) + (int64_t)(j0 + rr) * n];
+      }
+      __syncthreads();
+      acc.mma(As, Bs, KC);
+      __syncthreads();
+    }
+  }
+  // S -> shared, then Z_ij = -Z_ii S
+  const int tr = (threadIdx.x % 16) * 4, tc = (threadIdx.x / 16) * 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) Ss[tr + i][tc + j] = acc.v[i][j];
+  __syncthreads();
+  TileAcc<T> out;
+  out.zero();
+  for (int k0 = 0; k0 < NB; k0 += KC) {
+    for (int e = threadIdx.x; e < KC * TILE; e += 256) {
+      int rr = e % TILE, kk = e / TILE;
+      int kcol = k0 + kk;
+      As[kk][rr] = (rr < ib && kcol < ib && rr >= kcol)
+                       ? P[(int64_t)(i0 + rr) + (int64_t)(i0 + kcol) * n] : T(0);
+      Bs[kk][rr] = Ss[kcol][rr];
+    }
+    __syncthreads();
+    out.mma(As, Bs, KC);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = tr + i;
+      if (r < ib) P[(int64_t)(i0 + r) + (int64_t)(j0 + tc + j) * n] = -out.v[i][j];
+    }
+}
+
+// ---- generic batched GEMM ------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, const T* Ab,
+                                              const T* Bb, T* Cb) {
+  const GemmOp o = ops[blockIdx.y];
+  const int tm = (o.m + TILE - 1) / TILE, tn = (o.n + TILE - 1) / TILE;
+  if ((int)blockIdx.x >= tm * tn) return;
+  const int rb = (blockIdx.x % tm) * TILE, cb = (blockIdx.x / tm) * TILE;
+  const T* A = Ab + o.A;
+  const T* B = Bb + o.B;
+  T* C = Cb + o.C;
+  __shared__ T As[KC][TILE + 4];
+  __shared__ T Bs[KC][TILE + 4];
+  TileAcc<T> acc;
+  acc.zero();
+  for (int k0 = 0; k0 < o.k; k0 += KC) {
+    for (int e = threadIdx.x; e < KC * TILE; e += 256) {
+      int rr, kk;
+      // choose the thread mapping that reads memory contiguously
+      if (!o.transA) { rr = e % TILE; kk = e / TILE; } else { kk = e % KC; rr = e / KC; }
+      int r = rb + rr, k = k0 + kk;
+      T v = T(0);
+      if (r < o.m && k < o.k)
+        v = o.transA ? A[(int64_t)k + (int64_t)r * o.lda] : A[(int64_t)r + (int64_t)k * o.lda];
+      As[kk][rr] = v;
+      int cc;
+      if (o.transB) { cc = e % TILE; kk = e / TILE; } else { kk = e % KC; cc = e / KC; }
+      int c = cb + cc;
+      k = k0 + kk;
+      v = T(0);
+      if (c < o.n && k < o.k)
+        v = o.transB ? B[(int64_t)c + (int64_t)k * o.ldb] : B[(int64_t)k + (int64_t)c * o.ldb];
+      Bs[kk][cc] = v;
+    }
+    __syncthreads();
+    acc.mma(As, Bs, KC);
+    __syncthreads();
+  }
+  const int tr = (threadIdx.x % 16) * 4, tc = (threadIdx.x / 16) * 4;
+  const T alpha = (T)o.alpha, beta = (T)o.beta;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = cb + tc + j;
+    if (c >= o.n) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = rb + tr + i;
+      if (r >= o.m) continue;
+      T* cp = &C[(int64_t)r + (int64_t)c * o.ldc];
+      *cp = (beta == T(0) ? T(0) : beta * *cp) + alpha * acc.v[i][j];
+    }
+  }
+}
+
+// ---- batched GEMV --------------------------------------------------------------
+constexpr int GEMV_ROWS = 128;
+constexpr int GEMV_XC = 64;
+
+template <typename T, int R>
+__global__ void __launch_bounds__(GEMV_ROWS) k_gemv_n(const GemvOp* __restrict__ ops,
+                                                      const T* __restrict__ Mar, T* work,
+                                                      int64_t vs) {
+  const GemvOp o = ops[blockIdx.y];
+  const int r0 = blockIdx.x * GEMV_ROWS;
+  if (r0 >= o.rows) return;
+  const int r = r0 + threadIdx.x;
+  const T* M = Mar + o.M;
+  __shared__ T xs[GEMV_XC][R];
+  T acc[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) acc[q] = T(0);
+  const int cend = o.tri ? min(o.cols, r0 + GEMV_ROWS) : o.cols;
+  for (int c0 = 0; c0 < cend; c0 += GEMV_XC) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < GEMV_XC * R; e += GEMV_ROWS) {
+      int cc = e % GEMV_XC, q = e / GEMV_XC;
+      xs[cc][q] = c0 + cc < cend ? work[o.x + q * vs + c0 + cc] : T(0);
+    }
+    __syncthreads();
+    if (r < o.rows) {
+      const int cl = min(GEMV_XC, cend - c0);
+      for (int cc = 0; cc < cl; ++cc) {
+        const int c = c0 + cc;
+        if (o.tri && c > r) break;
+        const T mv = M[(int64_t)r + (int64_t)c * o.ld];
+#pragma unroll
+        for (int q = 0; q < R; ++q) acc[q] = fma(mv, xs[cc][q], acc[q]);
+      }
+    }
+  }
+  if (r < o.rows) {
+    const T al = (T)o.alpha;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      T* yp = &work[o.y + q * vs + r];
+      *yp = (o.beta_one ? *yp : T(0)) + al * acc[q];
+    }
+  }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_gemv_t(const GemvOp* __restrict__ ops,
+                                                const T* __restrict__ Mar, T* work, int64_t vs) {
+  const GemvOp o = ops[blockIdx.y];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int c = blockIdx.x * 8 + warp;
+  if (c >= o.cols) return;
+  const T* M = Mar + o.M + (int64_t)c * o.ld;
+  T acc[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) acc[q] = T(0);
+  for (int r = (o.tri ? c : 0) + lane; r < o.rows; r += 32) {
+    const T mv = M[r];
+#pragma unroll
+    for (int q = 0; q < R; ++q) acc[q] = fma(mv, work[o.x + q * vs + r], acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    T v = acc[q];
+    for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+    acc[q] = v;
+  }
+  if (lane == 0) {
+    const T al = (T)o.alpha;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      T* yp = &work[o.y + q * vs + c];
+      *yp = (o.beta_one ? *yp : T(0)) + al * acc[q];
+    }
+  }
+}
+
+}  // namespace
+
+// ---- host wrappers ---------------------------------------------------------------
+
+template <typename T>
+void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront, T* Karena,
+                      T* Parena, int* d_flags, cudaStream_t st) {
+  if (nfront == 0) return;
+  const int pmax = h_fronts[0].p;
+  // prefix maxima of n (fronts are sorted by p, not by n)
+  std::vector<int> nmax(nfront);
+  int mx = 0;
+  for (int f = 0; f < nfront; ++f) {
+    mx = std::max(mx, h_fronts[f].n);
+    nmax[f] = mx;
+  }
+  for (int j0 = 0; j0 < pmax; j0 += NB) {
+    int nact = 0;
+    while (nact < nfront && h_fronts[nact].p > j0) ++nact;
+    const int nm = nmax[nact - 1];
+    const int j1min = j0 + 1;  // smallest possible j1 among active fronts
+    const int chunks = std::max(1, ceil_div(std::max(0, nm - j1min), PANEL_ROWS));
+    int ntile = ceil_div(std::max(0, nm - j1min), TILE);
+    const int pairs = std::max(1, ntile * (ntile + 1) / 2);
+    for (int f0 = 0; f0 < nact; f0 += MAX_GRID_Y) {
+      const int nb = std::min(MAX_GRID_Y, nact - f0);
+      k_panel<T><<<dim3(chunks, nb), PANEL_ROWS, 0, st>>>(d_fronts + f0, Karena, Parena, j0,
+                                                          d_flags);
+      HIF_CHECK_LAUNCH();
+      k_syrk<T><<<dim3(pairs, nb), 256, 0, st>>>(d_fronts + f0, Karena, j0);
+      HIF_CHECK_LAUNCH();
+    }
+  }
+  // Linv = L^{-1}: diagonal blocks, then block rows
+  const int nblk = ceil_div(pmax, NB);
+  for (int f0 = 0; f0 < nfront; f0 += MAX_GRID_Y) {
+    const int nb = std::min(MAX_GRID_Y, nfront - f0);
+    k_trtri_diag<T><<<dim3(nblk, nb), NB, 0, st>>>(d_fronts + f0, Parena);
+    HIF_CHECK_LAUNCH();
+  }
+  for (int bi = 1; bi < nblk; ++bi) {
+    int nact = 0;
+    while (nact < nfront && h_fronts[nact].p > bi * NB) ++nact;
+    for (int f0 = 0; f0 < nact; f0 += MAX_GRID_Y) {
+      const int nb = std::min(MAX_GRID_Y, nact - f0);
+      k_trtri_row<T><<<dim3(bi, nb), 256, 0, st>>>(d_fronts + f0, Karena, Parena, bi);
+      HIF_CHECK_LAUNCH();
+      }
+  }
+}
+
+template <typename T>
+void gemm_batched(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const T* Abase,
+                  const T* Bbase, T* Cbase, cudaStream_t st) {
+  if (nops == 0) return;
+  int mt = 1;
+  for (int i = 0; i < nops; ++i)
+    mt = std::max(mt, ceil_div(h_ops[i].m, TILE) * ceil_div(h_ops[i].n, TILE));
+  for (int f0 = 0; f0 < nops; f0 += MAX_GRID_Y) {
+    const int nb = std::min(MAX_GRID_Y, nops - f0);
+    k_gemm<T><<<dim3(mt, nb), 256, 0, st>>>(d_ops + f0, Abase, Bbase, Cbase);
+    HIF_CHECK_LAUNCH();
+  }
+}
+
+template <typename T>
+void gemv_batched(const GemvOp* d_ops, const GemvOp* h_ops, int nops, int trans,
+                  const T* Marena, T* work, int64_t vstride, int nrhs, cudaStream_t st) {
+  if (nops == 0) return;
+  int mx = 1;
+  for (int i = 0; i < nops; ++i)
+    mx = std::max(mx, trans ? ceil_div(h_ops[i].cols, 8) : ceil_div(h_ops[i].rows, GEMV_ROWS));
+  for (int q0 = 0; q0 < nrhs;) {
+    const int R = nrhs - q0 >= 8 ? 8 : 1;
+    T* w = work + (int64_t)q0 * vstride;
+    for (int f0 = 0; f0 < nops; f0 += MAX_GRID_Y) {
+      const int nb = std::min(MAX_GRID_Y, nops - f0);
+      dim3 grid(mx, nb);
+      if (trans) {
+        if (R == 8) k_gemv_t<T, 8><<<grid, 256, 0, st>>>(d_ops + f0, Marena, w, vstride);
+        else k_gemv_t<T, 1><<<grid, 256, 0, st>>>(d_ops + f0, Marena, w, vstride);
+      } else {
+        if (R == 8) k_gemv_n<T, 8><<<grid, GEMV_ROWS, 0, st>>>(d_ops + f0, Marena, w, vstride);
+        else k_gemv_n<T, 1><<<grid, GEMV_ROWS, 0, st>>>(d_ops + f0, Marena, w, vstride);
+      }
+      HIF_CHECK_LAUNCH();
+      }
+    q0 += R;
+  }
+}
+
+#define HIF_INST(T)                                                                          \
+  template void partial_cholesky<T>(const DFront*, const DFront*, int, T*, T*, int*,        \
+                                    cudaStream_t);                                           \
+  template void gemm_batched<T>(const GemmOp*, const GemmOp*, int, const T*, const T*, T*,  \
+                                cudaStream_t);                                               \
+  template void gemv_batched<T>(const GemvOp*, const GemvOp*, int, int, const T*, T*,       \
+                                int64_t, int, cudaStream_t);
+HIF_INST(float)
+HIF_INST(double)
+#undef HIF_INST
+
+}  // namespace hif

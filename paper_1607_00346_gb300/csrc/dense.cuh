@@ -1,0 +1,30 @@
+// Batched dense kernels over uneven fronts (host launch wrappers).
+#pragma once
+
+#include "common.cuh"
+
+namespace hif {
+
+constexpr int NB = 64;      // panel width of the partial Cholesky and of the triangular inverse
+constexpr int TILE = 64;    // output tile of the trailing update / batched GEMM
+
+// Partial Cholesky of a batch of fronts (§2.2 and §2.3: A_II = L L^T,
+// X = L^{-1} A_IN, A_NN -= X^T X).  Fronts must be sorted by p, largest first.
+// On return: trailing blocks of K hold the Schur complements, P holds
+// [Linv; X^T] (Linv = L^{-1}, lower triangular) for each front.
+template <typename T>
+void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront, T* Karena,
+                      T* Parena, int* d_flags, cudaStream_t st);
+
+// C = beta C + alpha op(A) op(B) for a batch of independent problems.
+template <typename T>
+void gemm_batched(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const T* Abase,
+                  const T* Bbase, T* Cbase, cudaStream_t st);
+
+// y = alpha op(M) x (+ y), batched (see GemvOp).  trans = 0: y (rows) = M x;
+// trans = 1: y (cols) = M^T x.  nrhs vectors with stride `vstride` in `work`.
+template <typename T>
+void gemv_batched(const GemvOp* d_ops, const GemvOp* h_ops, int nops, int trans,
+                  const T* Marena, T* work, int64_t vstride, int nrhs, cudaStream_t st);
+
+}  // namespace hif

@@ -1,0 +1,902 @@
+// C ABI of the GB300 HIF library: factorization driver (level loop of §2.4),
+// application of F^{-1} (forward / backward sweeps) and the preconditioned
+// conjugate-gradient solve.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <type_traits>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "dense.cuh"
+#include "front.cuh"
+#include "solve.cuh"
+#include "symbolic.h"
+
+namespace hif {
+
+template <typename T>
+void interpolative_decomposition(SkelDesc* d_f, int nf, T* Garena, int32_t* perm, T* Farena,
+                                 double* scratch, double eps, cudaStream_t st);
+
+namespace {
+thread_local std::string g_last_error;
+thread_local int64_t g_launches = 0;
+}  // namespace
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+int64_t& launch_counter() { return g_launches; }
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+double seconds_since(Clock::time_point t0) {
+  return std::chrono::duration<double>(Clock::now() - t0).count();
+}
+
+// ---- device memory --------------------------------------------------------------
+
+struct MemStats {
+  size_t cur = 0, peak = 0;
+};
+
+class DevBuf {
+ public:
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept { swap(o); }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    release();
+    swap(o);
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void alloc(size_t bytes, MemStats* ms) {
+    release();
+    ms_ = ms;
+    if (bytes == 0) return;
+    HIF_CUDA_TRY(cudaMalloc(&p_, bytes));
+    bytes_ = bytes;
+    if (ms_) {
+      ms_->cur += bytes;
+      ms_->peak = std::max(ms_->peak, ms_->cur);
+    }
+  }
+  void release() {
+    if (p_) {
+      cudaFree(p_);
+      if (ms_) ms_->cur -= bytes_;
+    }
+    p_ = nullptr;
+    bytes_ = 0;
+  }
+  template <typename U>
+  U* as() const { return static_cast<U*>(p_); }
+  size_t bytes() const { return bytes_; }
+
+ private:
+  void swap(DevBuf& o) {
+    std::swap(p_, o.p_);
+    std::swap(bytes_, o.bytes_);
+    std::swap(ms_, o.ms_);
+  }
+  void* p_ = nullptr;
+  size_t bytes_ = 0;
+  MemStats* ms_ = nullptr;
+};
+
+template <typename U>
+void upload(DevBuf& b, const std::vector<U>& h, MemStats* ms, cudaStream_t st) {
+  b.alloc(h.size() * sizeof(U), ms);
+  if (!h.empty())
+    HIF_CUDA_TRY(cudaMemcpyAsync(b.as<void>(), h.data(), h.size() * sizeof(U),
+                                 cudaMemcpyHostToDevice, st));
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// ---- apply stages ----------------------------------------------------------------
+// One stage per front batch (cells of a level, faces, edges, root).  The
+// forward sweep runs the stages in order, the backward sweep in reverse.
+// Work layout of a stage (per right-hand side): v = gathered values of every
+// front's DOFs (front f at voff_f), t = a second vector of the same size at
+// offset nidx.
+struct GemvList {
+  std::vector<GemvOp> h;
+  DevBuf d;
+  int trans = 0;
+  int mat = 0;   // 0: panel arena, 1: interpolation-matrix arena
+};
+
+struct Stage {
+  int kind = 0;                 // 0 = cells (or root), 1 = faces / edges
+  int level = 0;
+  int64_t nidx = 0;
+  DevBuf idx;                   // gather list (global DOF per work slot)
+  DevBuf panels;                // [Linv; X^T] per front
+  DevBuf tmats;                 // T per front (skeleton stages)
+  std::vector<GemvList> fwd, bwd;
+  DevBuf set_g, set_p;          // y[g] = work[p] (both sweeps)
+  int64_t nset = 0;
+  DevBuf acc_tgt, acc_ptr, acc_src;   // forward, cells: y[g] -= sum work[src]
+  int64_t nacc = 0;
+  int64_t entries = 0;          // factor entries read per sweep
+};
+
+struct FactorBase {
+  virtual ~FactorBase() = default;
+  virtual void apply(const double* f_dev, double* u_dev, int nrhs, cudaStream_t st) = 0;
+  int n = 0, m = 0, L = 0, precision = 0;
+  double eps = 0;
+  MemStats mem;
+  DevBuf cpl, diag;             // operator for the residual
+  hif_stats stats{};
+  hif_options opt{};
+};
+
+template <typename T>
+struct Factor : FactorBase {
+  std::vector<Stage> stages;
+  DevBuf y, work;               // apply buffers (grown on demand)
+  int64_t work_cap = 0, y_cap = 0;
+  int64_t work_stride = 0;
+
+  void run_stage(Stage& s, bool fwd, T* yv, int64_t ys, T* w, int64_t vs, int nrhs,
+                 cudaStream_t st) {
+    vec_gather<T>(s.idx.as<int32_t>(), s.nidx, yv, ys, w, vs, 0, nrhs, st);
+    auto& lists = fwd ? s.fwd : s.bwd;
+    for (auto& gl : lists) {
+      if (gl.h.empty()) continue;
+      const T* M = gl.mat ? s.tmats.as<T>() : s.panels.as<T>();
+      gemv_batched<T>(gl.d.as<GemvOp>(), gl.h.data(), (int)gl.h.size(), gl.trans, M, w, vs, nrhs,
+                      st);
+    }
+    vec_set<T>(s.set_g.as<int32_t>(), s.set_p.as<int32_t>(), s.nset, yv, ys, w, vs, nrhs, st);
+    if (fwd && s.nacc)
+      vec_accumulate<T>(s.acc_tgt.as<int32_t>(), s.acc_ptr.as<int64_t>(), s.acc_src.as<int32_t>(),
+                        s.nacc, yv, ys, w, vs, nrhs, st);
+  }
+
+  void apply(const double* f_dev, double* u_dev, int nrhs, cudaStream_t st) override {
+    const int64_t N = (int64_t)n * n * n;
+    if (y_cap < N * nrhs) {
+      y.alloc(sizeof(T) * N * nrhs, &mem);
+      y_cap = N * nrhs;
+    }
+    if (work_cap < work_stride * nrhs) {
+      work.alloc(sizeof(T) * std::max<int64_t>(1, work_stride * nrhs), &mem);
+      work_cap = work_stride * nrhs;
+    }
+    T* yv = y.as<T>();
+    T* w = work.as<T>();
+    vec_convert_in<T>(f_dev, yv, N * nrhs, st);
+    for (auto& s : stages) run_stage(s, true, yv, N, w, work_stride, nrhs, st);
+    for (auto it = stages.rbegin(); it != stages.rend(); ++it)
+      run_stage(*it, false, yv, N, w, work_stride, nrhs, st);
+    vec_convert_out<T>(yv, u_dev, N * nrhs, st);
+  }
+};
+
+// ---- the factorization ---------------------------------------------------------
+
+template <typename T>
+class Builder {
+ public:
+  Builder(Factor<T>& F, cudaStream_t st) : F_(F), st_(st), sym_(F.n, F.m) {}
+
+  void run(const double* a_dev, const double* b_dev, double b_const);
+
+ private:
+  void check_flags(const char* where);
+  void cell_step(CellPlan& cp, DevBuf& Kar, DevBuf& cdesc_d, std::vector<CellDesc>& cdesc,
+                 DevBuf& lists_d);
+  void skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& alive, DevBuf& Kar,
+                 DevBuf& cdesc_d);
+  void gemv_list(GemvList& gl, std::vector<GemvOp>&& ops, int trans, int mat) {
+    gl.h = std::move(ops);
+    gl.trans = trans;
+    gl.mat = mat;
+    upload(gl.d, gl.h, &F_.mem, st_);
+  }
+
+  Factor<T>& F_;
+  cudaStream_t st_;
+  Symbolic sym_;
+  DevBuf flags_;
+  int level_ = 0;
+};
+
+template <typename T>
+void Builder<T>::check_flags(const char* where) {
+  int h[FLAG_COUNT];
+  HIF_CUDA_TRY(cudaMemcpyAsync(h, flags_.as<int>(), sizeof(h), cudaMemcpyDeviceToHost, st_));
+  HIF_CUDA_TRY(cudaStreamSynchronize(st_));
+  if (h[FLAG_NOT_SPD] >= 0)
+    throw Error{HIF_ERR_NOT_SPD, std::string("non-positive Cholesky pivot in ") + where +
+                                     " at level " + std::to_string(level_) + ", front " +
+                                     std::to_string(h[FLAG_NOT_SPD])};
+}
+
+template <typename T>
+void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
+  const int n = F_.n;
+  const int64_t N = (int64_t)n * n * n;
+  auto t0 = Clock::now();
+  F_.cpl.alloc(sizeof(double) * 3 * N, &F_.mem);
+  F_.diag.alloc(sizeof(double) * N, &F_.mem);
+  DevBuf bad;
+  bad.alloc(sizeof(int), &F_.mem);
+  HIF_CUDA_TRY(cudaMemsetAsync(bad.as<int>(), 0, sizeof(int), st_));
+  stencil_coefficients(a_dev, b_dev, b_const, n, F_.cpl.template as<double>(), F_.diag.template as<double>(),
+                       bad.as<int>(), st_);
+  int hbad = 0;
+  HIF_CUDA_TRY(cudaMemcpyAsync(&hbad, bad.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st_));
+  HIF_CUDA_TRY(cudaStreamSynchronize(st_));
+  if (hbad) throw Error{HIF_ERR_INVALID_ARG, "a must be finite and > 0, b finite and >= 0"};
+  flags_.alloc(sizeof(int) * FLAG_COUNT, &F_.mem);
+  HIF_CUDA_TRY(cudaMemsetAsync(flags_.as<int>(), 0xff, sizeof(int) * FLAG_COUNT, st_));
+
+  const int L = F_.L;
+  CellPlan prev;
+  DevBuf prevK, prevDesc;
+  for (int level = 0; level <= L; ++level) {
+    level_ = level;
+    auto tl = Clock::now();
+    CellPlan cp;
+    sym_.build_cells(level, cp);
+    // frontal matrices of the level's cells
+    std::vector<CellDesc> cdesc(cp.ncell);
+    int64_t koff = 0;
+    for (int c = 0; c < cp.ncell; ++c) {
+      const int nc = (int)(cp.off[c + 1] - cp.off[c]);
+      cdesc[c] = CellDesc{koff, cp.off[c], nc, cp.p[c]};
+      koff += (int64_t)nc * nc;
+    }
+    DevBuf Kar, cdesc_d, lists_d;
+    Kar.alloc(sizeof(T) * std::max<int64_t>(1, koff), &F_.mem);
+    upload(cdesc_d, cdesc, &F_.mem, st_);
+    upload(lists_d, cp.dofs, &F_.mem, st_);
+    if (level == 0) {
+      HIF_CUDA_TRY(cudaMemsetAsync(Kar.as<T>(), 0, sizeof(T) * koff, st_));
+      const int maxbox = (cp.s + 1) * (cp.s + 1) * (cp.s + 1);
+      assemble_level0<T>(cdesc_d.as<CellDesc>(), cp.ncell, lists_d.as<int32_t>(), n, cp.s,
+                         F_.cpl.template as<double>(), F_.diag.template as<double>(), Kar.as<T>(), maxbox, st_);
+    } else {
+      std::vector<int64_t> mapOff;
+      std::vector<int32_t> map;
+      sym_.merge_maps(prev, cp, mapOff, map);
+      DevBuf map_d, mdesc_d;
+      upload(map_d, map, &F_.mem, st_);
+      std::vector<MergeDesc> md(cp.ncell);
+      const int C = cp.C, Cc = prev.C;
+      for (int c = 0; c < cp.ncell; ++c) {
+        md[c].K = cdesc[c].K;
+        md[c].map = mapOff[c];
+        md[c].n = cdesc[c].n;
+        const int px = c % C, py = (c / C) % C, pz = c / (C * C);
+        for (int q = 0; q < 8; ++q) {
+          const int cx = 2 * px + (q & 1), cy = 2 * py + ((q >> 1) & 1), cz = 2 * pz + ((q >> 2) & 1);
+          md[c].child[q] = (cx < Cc && cy < Cc && cz < Cc) ? cx + Cc * (cy + Cc * cz) : -1;
+        }
+      }
+      upload(mdesc_d, md, &F_.mem, st_);
+      merge_children<T>(mdesc_d.as<MergeDesc>(), md.data(), cp.ncell, prevDesc.as<CellDesc>(),
+                        map_d.as<int32_t>(), prevK.as<T>(), Kar.as<T>(), st_);
+      HIF_CUDA_TRY(cudaStreamSynchronize(st_));
+      prevK.release();
+      prevDesc.release();
+    }
+    cell_step(cp, Kar, cdesc_d, cdesc, lists_d);
+    F_.stats.fronts[level][0] = cp.ncell;
+    if (level == L) {
+      F_.stats.root_size = (int)cp.dofs.size();
+      check_flags("the root factorization");
+      F_.stats.level_seconds[level] = seconds_since(tl);
+      break;
+    }
+    // interiors are eliminated; faces then edges are skeletonized
+    std::vector<uint8_t> alive(N, 0);
+    for (int32_t g : cp.active) alive[g] = 1;
+    for (int c = 0; c < cp.ncell; ++c)
+      for (int64_t t = cp.off[c]; t < cp.off[c] + cp.p[c]; ++t) alive[cp.dofs[t]] = 0;
+    if (F_.eps > 0.0) {
+      skel_step(cp, 1, alive, Kar, cdesc_d);
+      skel_step(cp, 2, alive, Kar, cdesc_d);
+    }
+    check_flags("level factorization");
+    std::vector<int32_t> next;
+    next.reserve(cp.active.size());
+    for (int32_t g : cp.active)
+      if (alive[g]) next.push_back(g);
+    F_.stats.active_after[level] = (int64_t)next.size();
+    sym_.set_active(std::move(next));
+    prev = std::move(cp);
+    prevK = std::move(Kar);
+    prevDesc = std::move(cdesc_d);
+    F_.stats.level_seconds[level] = seconds_since(tl);
+  }
+  HIF_CUDA_TRY(cudaStreamSynchronize(st_));
+  F_.stats.factor_seconds = seconds_since(t0);
+}
+
+template <typename T>
+void Builder<T>::cell_step(CellPlan& cp, DevBuf& Kar, DevBuf& cdesc_d, std::vector<CellDesc>& cdesc,
+                           DevBuf& lists_d) {
+  (void)cdesc_d;
+  Stage s;
+  s.kind = 0;
+  s.level = level_;
+  // panels for the cells with an interior, sorted by p (largest first)
+  std::vector<int> order;
+  for (int c = 0; c < cp.ncell; ++c)
+    if (cp.p[c] > 0) order.push_back(c);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cp.p[x] > cp.p[y]; });
+  std::vector<DFront> fr;
+  std::vector<int64_t> poff(cp.ncell, -1);
+  int64_t pcur = 0;
+  for (int c : order) {
+    poff[c] = pcur;
+    fr.push_back(DFront{cdesc[c].K, pcur, cdesc[c].n, cdesc[c].p, c, 0});
+    pcur += (int64_t)cdesc[c].n * cdesc[c].p;
+    F_.stats.flops += std::pow((double)cdesc[c].p, 3) / 3.0 +
+                      (double)cdesc[c].p * cdesc[c].p * (cdesc[c].n - cdesc[c].p) +
+                      (double)(cdesc[c].n - cdesc[c].p) * (cdesc[c].n - cdesc[c].p) * cdesc[c].p;
+  }
+  s.panels.alloc(sizeof(T) * std::max<int64_t>(1, pcur), &F_.mem);
+  s.entries = pcur;
+  DevBuf fr_d;
+  upload(fr_d, fr, &F_.mem, st_);
+  partial_cholesky<T>(fr_d.as<DFront>(), fr.data(), (int)fr.size(), Kar.as<T>(), s.panels.as<T>(),
+                      flags_.as<int>(), st_);
+  // apply stage: gather the whole frontal list of every cell
+  s.nidx = (int64_t)cp.dofs.size();
+  s.idx = std::move(lists_d);
+  std::vector<GemvOp> f1, f2, b1, b2;
+  std::vector<int32_t> sg, sp;
+  for (int c = 0; c < cp.ncell; ++c) {
+    const int nc = cdesc[c].n, p = cdesc[c].p;
+    if (p == 0) continue;
+    const int64_t vo = cp.off[c], to = s.nidx + cp.off[c], P = poff[c];
+    // forward: t_I = Linv v_I ; t_B = X^T t_I
+    f1.push_back(GemvOp{P, vo, to, p, p, nc, 1, 1.0f, 0});
+    if (nc > p) f2.push_back(GemvOp{P + p, to, to + p, nc - p, p, nc, 0, 1.0f, 0});
+    // backward: v_I -= X v_B ; t_I = Linv^T v_I
+    if (nc > p) b1.push_back(GemvOp{P + p, vo + p, vo, nc - p, p, nc, 0, -1.0f, 1});
+    b2.push_back(GemvOp{P, vo, to, p, p, nc, 1, 1.0f, 0});
+    for (int a = 0; a < p; ++a) {
+      sg.push_back(cp.dofs[cp.off[c] + a]);
+      sp.push_back((int32_t)(to + a));
+    }
+  }
+  s.fwd.resize(2);
+  s.bwd.resize(2);
+  gemv_list(s.fwd[0], std::move(f1), 0, 0);
+  gemv_list(s.fwd[1], std::move(f2), 0, 0);
+  gemv_list(s.bwd[0], std::move(b1), 1, 0);
+  gemv_list(s.bwd[1], std::move(b2), 1, 0);
+  s.nset = (int64_t)sg.size();
+  upload(s.set_g, sg, &F_.mem, st_);
+  upload(s.set_p, sp, &F_.mem, st_);
+  // deterministic accumulation of the boundary updates: per DOF, contributions
+  // in cell order (counting sort on the global index)
+  const int64_t N = (int64_t)F_.n * F_.n * F_.n;
+  std::vector<int64_t> cnt(N + 1, 0);
+  int64_t npair = 0;
+  for (int c = 0; c < cp.ncell; ++c) {
+    if (cp.p[c] == 0) continue;
+    for (int64_t t = cp.off[c] + cp.p[c]; t < cp.off[c + 1]; ++t) {
+      cnt[cp.dofs[t] + 1]++;
+      ++npair;
+    }
+  }
+  if (npair) {
+    std::vector<int32_t> tgt;
+    std::vector<int64_t> ptr;
+    for (int64_t g = 0; g < N; ++g)
+      if (cnt[g + 1]) tgt.push_back((int32_t)g);
+    std::vector<int64_t> start(N + 1, 0);
+    for (int64_t g = 0; g < N; ++g) start[g + 1] = start[g] + cnt[g + 1];
+    std::vector<int32_t> src(npair);
+    std::vector<int64_t> cur(start.begin(), start.end() - 1);
+    for (int c = 0; c < cp.ncell; ++c) {
+      if (cp.p[c] == 0) continue;
+      for (int64_t t = cp.off[c] + cp.p[c]; t < cp.off[c + 1]; ++t)
+        src[cur[cp.dofs[t]]++] = (int32_t)(s.nidx + t);
+    }
+    ptr.reserve(tgt.size() + 1);
+    ptr.push_back(0);
+    for (int32_t g : tgt) ptr.push_back(start[g + 1]);
+    s.nacc = (int64_t)tgt.size();
+    upload(s.acc_tgt, tgt, &F_.mem, st_);
+    upload(s.acc_ptr, ptr, &F_.mem, st_);
+    upload(s.acc_src, src, &F_.mem, st_);
+  }
+  F_.work_stride = std::max(F_.work_stride, 2 * s.nidx);
+  HIF_CUDA_TRY(cudaStreamSynchronize(st_));
+  F_.stages.push_back(std::move(s));
+}
+
+template <typename T>
+void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& alive, DevBuf& Kar,
+                           DevBuf& cdesc_d) {
+  SkelPlan sp;
+  sym_.build_skel(cp, kind, alive, sp);
+  const int nf = sp.nfront;
+  if (nf == 0) return;
+  const int ncp = sp.ncellPer;
+  std::vector<SkelDesc> sd(nf);
+  int64_t goff = 0, poff = 0, toff = 0;
+  for (int f = 0; f < nf; ++f) {
+    SkelDesc& d = sd[f];
+    std::memset(&d, 0, sizeof(d));
+    d.nF = sp.nF[f];
+    d.nR = sp.nR[f];
+    d.G = goff;
+    d.rows = sp.rowOff[f] * ncp;
+    d.perm = poff;
+    d.Tm = toff;
+    for (int i = 0; i < ncp; ++i) d.cell[i] = sp.cells[(size_t)f * ncp + i];
+    goff += (int64_t)(d.nF + d.nR) * d.nF;
+    poff += d.nF;
+    toff += (int64_t)(d.nF / 2) * (d.nF - d.nF / 2);
+    F_.stats.flops += 2.0 * d.nR * (double)d.nF * d.nF;
+  }
+  DevBuf rowpos_d, sd_d, G, perm_d, scratch, tm;
+  upload(rowpos_d, sp.rowPos, &F_.mem, st_);
+  upload(sd_d, sd, &F_.mem, st_);
+  G.alloc(sizeof(T) * std::max<int64_t>(1, goff), &F_.mem);
+  perm_d.alloc(sizeof(int32_t) * poff, &F_.mem);
+  scratch.alloc(sizeof(double) * 2 * poff, &F_.mem);
+  tm.alloc(sizeof(T) * std::max<int64_t>(1, toff), &F_.mem);
+  skel_gather<T>(sd_d.as<SkelDesc>(), sd.data(), nf, ncp, rowpos_d.as<int32_t>(),
+                 cdesc_d.as<CellDesc>(), Kar.as<T>(), G.as<T>(), st_);
+  interpolative_decomposition<T>(sd_d.as<SkelDesc>(), nf, G.as<T>(), perm_d.as<int32_t>(),
+                                 tm.as<T>(), scratch.as<double>(), F_.eps, st_);
+  std::vector<int32_t> perm(poff);
+  HIF_CUDA_TRY(cudaMemcpyAsync(sd.data(), sd_d.as<void>(), sizeof(SkelDesc) * nf,
+                               cudaMemcpyDeviceToHost, st_));
+  HIF_CUDA_TRY(cudaMemcpyAsync(perm.data(), perm_d.as<void>(), sizeof(int32_t) * poff,
+                               cudaMemcpyDeviceToHost, st_));
+  HIF_CUDA_TRY(cudaStreamSynchronize(st_));
+  scratch.release();
+  // fronts with redundant DOFs are eliminated; the others keep every DOF
+  std::vector<int> act;
+  for (int f = 0; f < nf; ++f)
+    if (sd[f].k < sd[f].nF) act.push_back(f);
+  F_.stats.fronts[level_][kind] = (int64_t)act.size();
+  for (int f : act) {
+    const int32_t* pm = &perm[sd[f].perm];
+    for (int i = sd[f].k; i < sd[f].nF; ++i) alive[sp.rowDof[sp.rowOff[f] + pm[i]]] = 0;
+  }
+  if (act.empty()) return;
+  // frontal matrices Z = Q^T A_FF Q in (redundant, skeleton) order
+  int64_t zoff = 0, pnl = 0;
+  std::vector<DFront> fr;
+  for (int f : act) {
+    SkelDesc& d = sd[f];
+    d.Z = zoff;
+    d.P = pnl;
+    const int p = d.nF - d.k;
+    fr.push_back(DFront{d.Z, d.P, d.nF, p, f, 0});
+    zoff += (int64_t)d.nF * d.nF;
+    pnl += (int64_t)d.nF * p;
+    F_.stats.flops += 4.0 * d.nF * (double)d.k * p + std::pow((double)p, 3) / 3.0 +
+                      (double)p * p * d.k + (double)d.k * d.k * p;
+  }
+  upload(sd_d, sd, &F_.mem, st_);
+  DevBuf Z;
+  Z.alloc(sizeof(T) * std::max<int64_t>(1, zoff), &F_.mem);
+  // permute only the active fronts: build a compact descriptor list
+  std::vector<SkelDesc> sda;
+  for (int f : act) sda.push_back(sd[f]);
+  DevBuf sda_d;
+  upload(sda_d, sda, &F_.mem, st_);
+  skel_permute<T>(sda_d.as<SkelDesc>(), sda.data(), (int)sda.size(), perm_d.as<int32_t>(),
+                  G.as<T>(), Z.as<T>(), st_);
+  // B_{F^F~} = A_{F^F~} - A_{F^F^} T ;  B_{F~F~} = A_{F~F~} - A_{F~F^} T - T^T B_{F^F~}
+  std::vector<GemmOp> g1, g2, g3;
+  for (const SkelDesc& d : sda) {
+    const int k = d.k, p = d.nF - k, nF = d.nF;
+    if (k == 0) continue;
+    g1.push_back(GemmOp{d.Z + p + (int64_t)p * nF, d.Tm, d.Z + p, k, p, k, nF, k, nF, 0, 0, -1.f, 1.f});
+    g2.push_back(GemmOp{d.Z + (int64_t)p * nF, d.Tm, d.Z, p, p, k, nF, k, nF, 0, 0, -1.f, 1.f});
+    g3.push_back(GemmOp{d.Tm, d.Z + p, d.Z, p, p, k, k, nF, nF, 1, 0, -1.f, 1.f});
+  }
+  DevBuf g1d, g2d, g3d;
+  upload(g1d, g1, &F_.mem, st_);
+  upload(g2d, g2, &F_.mem, st_);
+  upload(g3d, g3, &F_.mem, st_);
+  gemm_batched<T>(g1d.as<GemmOp>(), g1.data(), (int)g1.size(), Z.as<T>(), tm.as<T>(), Z.as<T>(), st_);
+  gemm_batched<T>(g2d.as<GemmOp>(), g2.data(), (int)g2.size(), Z.as<T>(), tm.as<T>(), Z.as<T>(), st_);
+  gemm_batched<T>(g3d.as<GemmOp>(), g3.data(), (int)g3.size(), tm.as<T>(), Z.as<T>(), Z.as<T>(), st_);
+  // partial Cholesky of Z: eliminate the redundant DOFs
+  Stage s;
+  s.kind = 1;
+  s.level = level_;
+  s.panels.alloc(sizeof(T) * std::max<int64_t>(1, pnl), &F_.mem);
+  std::vector<DFront> frs = fr;
+  std::stable_sort(frs.begin(), frs.end(), [](const DFront& x, const DFront& y) { return x.p > y.p; });
+  DevBuf fr_d;
+  upload(fr_d, frs, &F_.mem, st_);
+  partial_cholesky<T>(fr_d.as<DFront>(), frs.data(), (int)frs.size(), Z.as<T>(), s.panels.as<T>(),
+                      flags_.as<int>(), st_);
+  skel_writeback<T>(sda_d.as<SkelDesc>(), sda.data(), (int)sda.size(), ncp, rowpos_d.as<int32_t>(),
+                    perm_d.as<int32_t>(), cdesc_d.as<CellDesc>(), Z.as<T>(), Kar.as<T>(), st_);
+  // apply stage
+  std::vector<int32_t> gidx;
+  std::vector<GemvOp> f1, f2, f3, b1, b2, b3;
+  std::vector<int32_t> sg, spos;
+  int64_t vo = 0;
+  int64_t totalF = 0;
+  for (const SkelDesc& d : sda) totalF += d.nF;
+  for (const SkelDesc& d : sda) {
+    const int k = d.k, nF = d.nF, p = nF - k;
+    const int32_t* pm = &perm[d.perm];
+    const int f = (int)(&d - sda.data());
+    const int src = act[f];
+    for (int i = 0; i < p; ++i) gidx.push_back(sp.rowDof[sp.rowOff[src] + pm[k + i]]);
+    for (int i = 0; i < k; ++i) gidx.push_back(sp.rowDof[sp.rowOff[src] + pm[i]]);
+    const int64_t to = totalF + vo;
+    // forward: v_c -= T^T v_h ; t_c = Linv v_c ; v_h -= X^T t_c
+    if (k) f1.push_back(GemvOp{d.Tm, vo + p, vo, k, p, k, 0, -1.0f, 1});
+    f2.push_back(GemvOp{d.P, vo, to, p, p, nF, 1, 1.0f, 0});
+    if (k) f3.push_back(GemvOp{d.P + p, to, vo + p, k, p, nF, 0, -1.0f, 1});
+    // backward: v_c -= X v_h ; t_c = Linv^T v_c ; v_h -= T t_c
+    if (k) b1.push_back(GemvOp{d.P + p, vo + p, vo, k, p, nF, 0, -1.0f, 1});
+    b2.push_back(GemvOp{d.P, vo, to, p, p, nF, 1, 1.0f, 0});
+    if (k) b3.push_back(GemvOp{d.Tm, to, vo + p, k, p, k, 0, -1.0f, 1});
+    for (int i = 0; i < p; ++i) {
+      sg.push_back(gidx[vo + i]);
+      spos.push_back((int32_t)(to + i));
+    }
+    for (int i = 0; i < k; ++i) {
+      sg.push_back(gidx[vo + p + i]);
+      spos.push_back((int32_t)(vo + p + i));
+    }
+    s.entries += (int64_t)nF * p + (int64_t)k * p;
+    vo += nF;
+  }
+  s.nidx = vo;
+  s.tmats = std::move(tm);
+  upload(s.idx, gidx, &F_.mem, st_);
+  s.fwd.resize(3);
+  s.bwd.resize(3);
+  gemv_list(s.fwd[0], std::move(f1), 1, 1);
+  gemv_list(s.fwd[1], std::move(f2), 0, 0);
+  gemv_list(s.fwd[2], std::move(f3), 0, 0);
+  gemv_list(s.bwd[0], std::move(b1), 1, 0);
+  gemv_list(s.bwd[1], std::move(b2), 1, 0);
+  gemv_list(s.bwd[2], std::move(b3), 0, 1);
+  s.nset = (int64_t)sg.size();
+  upload(s.set_g, sg, &F_.mem, st_);
+  upload(s.set_p, spos, &F_.mem, st_);
+  F_.work_stride = std::max(F_.work_stride, 2 * s.nidx);
+  HIF_CUDA_TRY(cudaStreamSynchronize(st_));
+  F_.stages.push_back(std::move(s));
+}
+
+// ---- PCG ------------------------------------------------------------------------
+
+struct SolveBufs {
+  DevBuf r, z, p, q, rold, part, dots, scal;
+};
+
+hif_status do_solve(FactorBase& F, const double* f, double* u, int nrhs, cudaStream_t st,
+                    int* iters, double* relres) {
+  const int64_t N = (int64_t)F.n * F.n * F.n;
+  SolveBufs b;
+  MemStats* ms = &F.mem;
+  for (DevBuf* x : {&b.r, &b.z, &b.p, &b.q, &b.rold}) x->alloc(sizeof(double) * N * nrhs, ms);
+  b.part.alloc(sizeof(double) * 1024 * nrhs, ms);
+  b.dots.alloc(sizeof(double) * 2 * nrhs, ms);
+  b.scal.alloc(sizeof(double) * nrhs, ms);
+  const double* cpl = F.cpl.as<double>();
+  const double* dg = F.diag.as<double>();
+  std::vector<double> fn(nrhs), rz(nrhs), tmp(nrhs), tmp2(nrhs), al(nrhs), be(nrhs), rel(nrhs);
+  std::vector<int> it(nrhs, 0), done(nrhs, 0);
+  auto hdots = [&](const double* x, const double* y, std::vector<double>& out) {
+    dots(x, y, N, nrhs, b.part.as<double>(), b.dots.as<double>(), st);
+    HIF_CUDA_TRY(cudaMemcpyAsync(out.data(), b.dots.as<double>(), sizeof(double) * nrhs,
+                                 cudaMemcpyDeviceToHost, st));
+    HIF_CUDA_TRY(cudaStreamSynchronize(st));
+  };
+  auto put = [&](const std::vector<double>& v) {
+    HIF_CUDA_TRY(cudaMemcpyAsync(b.scal.as<double>(), v.data(), sizeof(double) * nrhs,
+                                 cudaMemcpyHostToDevice, st));
+  };
+  double* r = b.r.as<double>();
+  double* z = b.z.as<double>();
+  double* p = b.p.as<double>();
+  double* q = b.q.as<double>();
+  HIF_CUDA_TRY(cudaMemsetAsync(u, 0, sizeof(double) * N * nrhs, st));
+  HIF_CUDA_TRY(cudaMemcpyAsync(r, f, sizeof(double) * N * nrhs, cudaMemcpyDeviceToDevice, st));
+  hdots(r, r, fn);
+  for (int c = 0; c < nrhs; ++c) {
+    fn[c] = std::sqrt(fn[c]);
+    rel[c] = fn[c] > 0 ? 1.0 : 0.0;
+    if (fn[c] == 0) done[c] = 1;
+  }
+  F.apply(r, z, nrhs, st);
+  HIF_CUDA_TRY(cudaMemcpyAsync(p, z, sizeof(double) * N * nrhs, cudaMemcpyDeviceToDevice, st));
+  hdots(r, z, rz);
+  const double tol = F.opt.pcg_tol;
+  const int maxit = F.opt.max_iter;
+  int k = 0;
+  bool all = std::all_of(done.begin(), done.end(), [](int x) { return x; });
+  while (!all && k < maxit) {
+    ++k;
+    matvec(cpl, dg, F.n, p, q, nrhs, st);
+    hdots(p, q, tmp);
+    for (int c = 0; c < nrhs; ++c) al[c] = done[c] || tmp[c] == 0 ? 0.0 : rz[c] / tmp[c];
+    put(al);
+    axpy_cols(b.scal.as<double>(), 1.0, p, u, N, nrhs, st);
+    HIF_CUDA_TRY(cudaMemcpyAsync(b.rold.as<double>(), r, sizeof(double) * N * nrhs,
+                                 cudaMemcpyDeviceToDevice, st));
+    axpy_cols(b.scal.as<double>(), -1.0, q, r, N, nrhs, st);
+    hdots(r, r, tmp);
+    for (int c = 0; c < nrhs; ++c) {
+      if (done[c]) continue;
+      rel[c] = std::sqrt(tmp[c]) / fn[c];
+      it[c] = k;
+      if (rel[c] <= tol) done[c] = 1;
+    }
+    all = std::all_of(done.begin(), done.end(), [](int x) { return x; });
+    if (all) break;
+    F.apply(r, z, nrhs, st);
+    hdots(r, z, tmp);       // r_new . z
+    hdots(b.rold.as<double>(), z, tmp2);   // r_old . z
+    for (int c = 0; c < nrhs; ++c) {
+      be[c] = done[c] || rz[c] == 0 ? 0.0 : (tmp[c] - tmp2[c]) / rz[c];   // Polak-Ribiere
+      if (!done[c]) rz[c] = tmp[c];
+    }
+    put(be);
+    xpby_cols(z, b.scal.as<double>(), p, N, nrhs, st);
+    // converged columns keep p = 0 so that later updates leave them alone
+    for (int c = 0; c < nrhs; ++c)
+      if (done[c]) HIF_CUDA_TRY(cudaMemsetAsync(p + c * N, 0, sizeof(double) * N, st));
+  }
+  HIF_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int c = 0; c < nrhs; ++c) {
+    if (iters) iters[c] = it[c];
+    if (relres) relres[c] = rel[c];
+  }
+  return all ? HIF_OK : HIF_ERR_NO_CONVERGENCE;
+}
+
+}  // namespace
+}  // namespace hif
+
+// ---- C ABI ------------------------------------------------------------------------
+
+struct hif_handle_s {
+  std::unique_ptr<hif::FactorBase> f;
+};
+
+using hif::Error;
+
+#define HIF_API_BEGIN try {
+#define HIF_API_END                                                  \
+  }                                                                  \
+  catch (const Error& e) {                                           \
+    hif::set_last_error(e.msg);                                      \
+    return e.code;                                                   \
+  }                                                                  \
+  catch (const std::bad_alloc&) {                                    \
+    hif::set_last_error("host allocation failed");                   \
+    return HIF_ERR_OOM;                                              \
+  }                                                                  \
+  catch (const std::exception& e) {                                  \
+    hif::set_last_error(e.what());                                   \
+    return HIF_ERR_CUDA;                                             \
+  }
+
+namespace {
+
+// Input array: device pointer as given, or a device copy of host data.
+struct InArray {
+  const double* p = nullptr;
+  hif::DevBuf tmp;
+  void set(const double* src, int64_t cnt, cudaStream_t st) {
+    if (src == nullptr || hif::is_device_ptr(src)) {
+      p = src;
+      return;
+    }
+    tmp.alloc(sizeof(double) * cnt, nullptr);
+    HIF_CUDA_TRY(cudaMemcpyAsync(tmp.as<void>(), src, sizeof(double) * cnt, cudaMemcpyHostToDevice, st));
+    p = tmp.as<double>();
+  }
+};
+
+struct OutArray {
+  double* user = nullptr;
+  double* p = nullptr;
+  hif::DevBuf tmp;
+  int64_t cnt = 0;
+  void set(double* dst, int64_t c) {
+    user = dst;
+    cnt = c;
+    if (hif::is_device_ptr(dst)) {
+      p = dst;
+    } else {
+      tmp.alloc(sizeof(double) * c, nullptr);
+      p = tmp.as<double>();
+    }
+  }
+  void finish(cudaStream_t st) {
+    if (p != user) {
+      HIF_CUDA_TRY(cudaMemcpyAsync(user, p, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+      HIF_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+void hif_default_options(hif_options* o) {
+  if (!o) return;
+  o->eps = 1e-6;
+  o->precision = HIF_PREC_FP64;
+  o->use_graphs = 1;
+  o->pcg_tol = 1e-10;
+  o->max_iter = 200;
+}
+
+const char* hif_version(void) { return "hif-gb300 0.1"; }
+
+const char* hif_last_error(void) { return hif::g_last_error.c_str(); }
+
+hif_status hif_factor(const hif_grid* grid, const double* a, const double* b, double b_const,
+                      const hif_options* opt, hif_stream stream, hif_handle* out) {
+  if (out) *out = nullptr;
+  HIF_API_BEGIN
+  if (!grid || !a || !out) throw Error{HIF_ERR_INVALID_ARG, "grid, a and out must not be NULL"};
+  hif_options o;
+  hif_default_options(&o);
+  if (opt) o = *opt;
+  const int n = grid->n, m = grid->m;
+  const int L = hif::hif_num_levels(n, m);
+  if (grid->bc != 0) throw Error{HIF_ERR_INVALID_ARG, "only the zero Dirichlet boundary (bc = 0) is supported"};
+  if (m < 2 || L < 0 || n > 1024)
+    throw Error{HIF_ERR_INVALID_ARG, "need n = m 2^L with m >= 2 and n <= 1024"};
+  if (!(o.eps >= 0.0) || !(o.eps < 1.0)) throw Error{HIF_ERR_INVALID_ARG, "eps must be in [0, 1)"};
+  if (o.precision != HIF_PREC_FP64 && o.precision != HIF_PREC_FP32)
+    throw Error{HIF_ERR_INVALID_ARG, "precision must be HIF_PREC_FP64 or HIF_PREC_FP32"};
+  if (!std::isfinite(b_const) || b_const < 0) throw Error{HIF_ERR_INVALID_ARG, "b_const must be finite and >= 0"};
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t N = (int64_t)n * n * n;
+  hif::launch_counter() = 0;
+  InArray ain, bin;
+  ain.set(a, N, st);
+  bin.set(b, N, st);
+  auto h = std::make_unique<hif_handle_s>();
+  auto build = [&](auto* F) {
+    F->n = n;
+    F->m = m;
+    F->L = L;
+    F->eps = o.eps;
+    F->precision = o.precision;
+    F->opt = o;
+    using FT = std::remove_pointer_t<decltype(F)>;
+    using TT = std::conditional_t<std::is_same<FT, hif::Factor<float>>::value, float, double>;
+    hif::Builder<TT> bld(*F, st);
+    bld.run(ain.p, bin.p, b_const);
+    F->stats.n = n;
+    F->stats.m = m;
+    F->stats.levels = L;
+    F->stats.precision = o.precision;
+    F->stats.eps = o.eps;
+    F->stats.kernel_launches = (int)hif::launch_counter();
+    int64_t ent = 0;
+    for (auto& s : F->stages) ent += s.entries;
+    F->stats.stored_entries = ent;
+  };
+  if (o.precision == HIF_PREC_FP32) {
+    auto* F = new hif::Factor<float>();
+    h->f.reset(F);
+    build(F);
+  } else {
+    auto* F = new hif::Factor<double>();
+    h->f.reset(F);
+    build(F);
+  }
+  h->f->stats.factor_bytes = h->f->mem.cur;
+  h->f->stats.peak_bytes = h->f->mem.peak;
+  *out = h.release();
+  return HIF_OK;
+  HIF_API_END
+}
+
+hif_status hif_apply(hif_handle h, const double* f, double* u, int nrhs, hif_stream stream) {
+  HIF_API_BEGIN
+  if (!h || !f || !u || nrhs < 1) throw Error{HIF_ERR_INVALID_ARG, "bad handle, pointer or nrhs"};
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t N = (int64_t)h->f->n * h->f->n * h->f->n;
+  InArray fin;
+  fin.set(f, N * nrhs, st);
+  OutArray uo;
+  uo.set(u, N * nrhs);
+  const int64_t l0 = hif::launch_counter();
+  h->f->apply(fin.p, uo.p, nrhs, st);
+  if (nrhs == 1) h->f->stats.apply_launches = (int)(hif::launch_counter() - l0);
+  uo.finish(st);
+  if (fin.tmp.bytes()) HIF_CUDA_TRY(cudaStreamSynchronize(st));
+  return HIF_OK;
+  HIF_API_END
+}
+
+hif_status hif_residual(hif_handle h, const double* f, const double* u, double* r, int nrhs,
+                        hif_stream stream) {
+  HIF_API_BEGIN
+  if (!h || !f || !u || !r || nrhs < 1) throw Error{HIF_ERR_INVALID_ARG, "bad handle, pointer or nrhs"};
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t N = (int64_t)h->f->n * h->f->n * h->f->n;
+  InArray fin, uin;
+  fin.set(f, N * nrhs, st);
+  uin.set(u, N * nrhs, st);
+  OutArray ro;
+  ro.set(r, N * nrhs);
+  hif::residual(h->f->cpl.as<double>(), h->f->diag.as<double>(), h->f->n, fin.p, uin.p, ro.p, nrhs, st);
+  ro.finish(st);
+  HIF_CUDA_TRY(cudaStreamSynchronize(st));
+  return HIF_OK;
+  HIF_API_END
+}
+
+hif_status hif_solve(hif_handle h, const double* f, double* u, int nrhs, hif_stream stream,
+                     int* iters, double* relres) {
+  HIF_API_BEGIN
+  if (!h || !f || !u || nrhs < 1) throw Error{HIF_ERR_INVALID_ARG, "bad handle, pointer or nrhs"};
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t N = (int64_t)h->f->n * h->f->n * h->f->n;
+  InArray fin;
+  fin.set(f, N * nrhs, st);
+  OutArray uo;
+  uo.set(u, N * nrhs);
+  hif_status s = hif::do_solve(*h->f, fin.p, uo.p, nrhs, st, iters, relres);
+  uo.finish(st);
+  if (s != HIF_OK) hif::set_last_error("PCG did not reach the tolerance within max_iter");
+  return s;
+  HIF_API_END
+}
+
+hif_status hif_query_stats(hif_handle h, hif_stats* st) {
+  if (!h || !st) {
+    hif::set_last_error("NULL handle or stats");
+    return HIF_ERR_INVALID_ARG;
+  }
+  *st = h->f->stats;
+  st->factor_bytes = h->f->mem.cur;
+  return HIF_OK;
+}
+
+size_t hif_predict_bytes(const hif_grid* grid, const hif_options* opt) {
+  if (!grid || hif::hif_num_levels(grid->n, grid->m) < 0) return 0;
+  const double N = (double)grid->n * grid->n * grid->n;
+  const int prec = opt ? opt->precision : HIF_PREC_FP64;
+  const double word = prec == HIF_PREC_FP32 ? 4.0 : 8.0;
+  // operator (4 doubles per DOF) + level-0 frontal matrices and factor panels
+  // (about 150 and 100 entries per DOF) + index lists; the upper levels add a
+  // comparable amount (O(N) in total, §3.3.1).
+  return (size_t)(N * (32.0 + 2.0 * 250.0 * word + 64.0));
+}
+
+void hif_destroy(hif_handle h) { delete h; }
+
+}  // extern "C"

@@ -1,0 +1,264 @@
+// Host-side symbolic pass (geometry of §2.1 with a Dirichlet boundary).
+#include "symbolic.h"
+
+#include <algorithm>
+#include <thread>
+#include <unordered_map>
+
+namespace hif {
+
+namespace {
+
+template <class F>
+void parallel_for(int64_t n, F&& f) {
+  unsigned hw = std::thread::hardware_concurrency();
+  if (hw == 0) hw = 1;
+  int64_t nt = std::min<int64_t>(hw, (n + 255) / 256);
+  if (nt <= 1) {
+    for (int64_t i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(nt);
+  for (int64_t t = 0; t < nt; ++t) {
+    th.emplace_back([&, t] {
+      int64_t a = n * t / nt, b = n * (t + 1) / nt;
+      for (int64_t i = a; i < b; ++i) f(i);
+    });
+  }
+  for (auto& x : th) x.join();
+}
+
+inline int popc3(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1); }
+
+}  // namespace
+
+int hif_num_levels(int n, int m) {
+  if (n <= 0 || m <= 0 || n % m) return -1;
+  int q = n / m, L = 0;
+  while ((1 << L) < q) ++L;
+  return (1 << L) == q ? L : -1;
+}
+
+Symbolic::Symbolic(int n, int m) : n_(n), m_(m), L_(hif_num_levels(n, m)) {
+  active_.resize((size_t)n * n * n);
+  for (size_t i = 0; i < active_.size(); ++i) active_[i] = (int32_t)i;
+}
+
+int32_t Symbolic::pos_in_cell(const CellPlan& cp, int32_t g, int cx, int cy, int cz) const {
+  int32_t sl = cp.slot[g];
+  if (sl < 0) return -1;
+  int64_t pk = cp.packed[sl];
+  int sep = (int)(pk >> 48);
+  int c[3] = {cx, cy, cz};
+  int q = 0;
+  for (int d = 0; d < 3; ++d) {
+    int lc = (int)((pk >> (16 * d)) & 0xffff);
+    if (c[d] == lc) continue;
+    if (((sep >> d) & 1) && c[d] == lc + 1) {
+      q |= 1 << d;
+      continue;
+    }
+    return -1;
+  }
+  return cp.posB[(int64_t)sl * 8 + q];
+}
+
+void Symbolic::build_cells(int level, CellPlan& cp) const {
+  const int n = n_;
+  const int s = m_ << level;
+  const int C = n / s;
+  const int64_t N = (int64_t)n * n * n;
+  cp.level = level;
+  cp.s = s;
+  cp.C = C;
+  cp.ncell = C * C * C;
+  cp.active = active_;
+  const int64_t na = (int64_t)cp.active.size();
+  cp.slot.assign(N, -1);
+  cp.packed.resize(na);
+  parallel_for(na, [&](int64_t i) {
+    int32_t g = cp.active[i];
+    cp.slot[g] = (int32_t)i;
+    int x[3] = {g % n, (g / n) % n, g / (n * n)};
+    int64_t pk = 0;
+    int sep = 0;
+    for (int d = 0; d < 3; ++d) {
+      bool sd = x[d] != 0 && x[d] % s == 0;
+      int lc = sd ? x[d] / s - 1 : x[d] / s;
+      if (sd) sep |= 1 << d;
+      pk |= (int64_t)lc << (16 * d);
+    }
+    cp.packed[i] = pk | ((int64_t)sep << 48);
+  });
+  std::vector<int32_t> cntI(cp.ncell, 0), cntB(cp.ncell, 0);
+  auto cell_of = [&](int64_t pk, int q) {
+    int c0 = (int)(pk & 0xffff) + (q & 1);
+    int c1 = (int)((pk >> 16) & 0xffff) + ((q >> 1) & 1);
+    int c2 = (int)((pk >> 32) & 0xffff) + ((q >> 2) & 1);
+    return c0 + C * (c1 + C * c2);
+  };
+  for (int64_t i = 0; i < na; ++i) {
+    int64_t pk = cp.packed[i];
+    int sep = (int)(pk >> 48);
+    if (sep == 0) {
+      cntI[cell_of(pk, 0)]++;
+    } else {
+      for (int q = 0; q < 8; ++q)
+        if ((q & ~sep) == 0) cntB[cell_of(pk, q)]++;
+    }
+  }
+  cp.off.assign(cp.ncell + 1, 0);
+  cp.p.assign(cp.ncell, 0);
+  for (int c = 0; c < cp.ncell; ++c) {
+    cp.off[c + 1] = cp.off[c] + cntI[c] + cntB[c];
+    cp.p[c] = cntI[c];
+  }
+  cp.dofs.assign(cp.off[cp.ncell], -1);
+  cp.posB.assign(na * 8, -1);
+  std::vector<int32_t> curI(cp.ncell, 0), curB(cp.ncell, 0);
+  for (int64_t i = 0; i < na; ++i) {
+    int64_t pk = cp.packed[i];
+    int sep = (int)(pk >> 48);
+    int32_t g = cp.active[i];
+    if (sep == 0) {
+      int c = cell_of(pk, 0);
+      cp.dofs[cp.off[c] + curI[c]++] = g;
+    } else {
+      for (int q = 0; q < 8; ++q) {
+        if (q & ~sep) continue;
+        int c = cell_of(pk, q);
+        int b = curB[c]++;
+        cp.dofs[cp.off[c] + cp.p[c] + b] = g;
+        cp.posB[i * 8 + q] = b;
+      }
+    }
+  }
+}
+
+void Symbolic::merge_maps(const CellPlan& child, const CellPlan& parent,
+                          std::vector<int64_t>& mapOff, std::vector<int32_t>& map) const {
+  const int C = parent.C, Cc = child.C;
+  mapOff.assign(parent.ncell + 1, 0);
+  for (int c = 0; c < parent.ncell; ++c)
+    mapOff[c + 1] = mapOff[c] + 8 * (parent.off[c + 1] - parent.off[c]);
+  map.assign(mapOff[parent.ncell], -1);
+  parallel_for(parent.ncell, [&](int64_t c) {
+    int px = (int)(c % C), py = (int)((c / C) % C), pz = (int)(c / ((int64_t)C * C));
+    int64_t o = parent.off[c];
+    int64_t nn = parent.off[c + 1] - o;
+    for (int q = 0; q < 8; ++q) {
+      int cx = 2 * px + (q & 1), cy = 2 * py + ((q >> 1) & 1), cz = 2 * pz + ((q >> 2) & 1);
+      if (cx >= Cc || cy >= Cc || cz >= Cc) continue;
+      int32_t* out = &map[mapOff[c] + (int64_t)q * nn];
+      for (int64_t a = 0; a < nn; ++a) out[a] = pos_in_cell(child, parent.dofs[o + a], cx, cy, cz);
+    }
+  });
+}
+
+void Symbolic::build_skel(const CellPlan& cp, int kind, const std::vector<uint8_t>& alive,
+                          SkelPlan& sp) const {
+  const int C = cp.C;
+  const int64_t na = (int64_t)cp.active.size();
+  sp.kind = kind;
+  sp.ncellPer = kind == 1 ? 2 : 4;
+  const int ncp = sp.ncellPer;
+  // group id = sep mask (3 bits) * C^3 + low-cell index
+  auto gkey = [&](int64_t pk) -> int64_t {
+    int64_t c0 = pk & 0xffff, c1 = (pk >> 16) & 0xffff, c2 = (pk >> 32) & 0xffff;
+    return (pk >> 48) * (int64_t)C * C * C + c0 + C * (c1 + C * c2);
+  };
+  std::unordered_map<int64_t, int32_t> fid;
+  std::vector<int64_t> keys;
+  std::vector<std::vector<int32_t>> members;
+  for (int64_t i = 0; i < na; ++i) {
+    int32_t g = cp.active[i];
+    if (!alive[g]) continue;
+    int64_t pk = cp.packed[i];
+    if (popc3((int)(pk >> 48)) != kind) continue;
+    int64_t k = gkey(pk);
+    auto it = fid.find(k);
+    int32_t f;
+    if (it == fid.end()) {
+      f = (int32_t)keys.size();
+      fid.emplace(k, f);
+      keys.push_back(k);
+      members.emplace_back();
+    } else {
+      f = it->second;
+    }
+    members[f].push_back(g);
+  }
+  const int nf = (int)keys.size();
+  sp.nfront = nf;
+  sp.cells.assign((size_t)nf * ncp, -1);
+  sp.nF.assign(nf, 0);
+  sp.nR.assign(nf, 0);
+  // cells of each front: corners over its separator dimensions
+  std::vector<int32_t> cellxyz((size_t)nf * ncp * 3);
+  for (int f = 0; f < nf; ++f) {
+    int64_t pk = cp.packed[cp.slot[members[f][0]]];
+    int sep = (int)(pk >> 48);
+    int lc[3] = {(int)(pk & 0xffff), (int)((pk >> 16) & 0xffff), (int)((pk >> 32) & 0xffff)};
+    int j = 0;
+    for (int q = 0; q < 8; ++q) {
+      if (q & ~sep) continue;
+      int c[3] = {lc[0] + (q & 1), lc[1] + ((q >> 1) & 1), lc[2] + ((q >> 2) & 1)};
+      sp.cells[(size_t)f * ncp + j] = c[0] + C * (c[1] + C * c[2]);
+      for (int d = 0; d < 3; ++d) cellxyz[((size_t)f * ncp + j) * 3 + d] = c[d];
+      ++j;
+    }
+  }
+  // rows: the front's DOFs, then the alive boundary DOFs of its cells not in
+  // the front, each once (first cell in corner order that holds it)
+  auto for_rows = [&](int f, auto&& emit) {
+    const int64_t fk = keys[f];
+    for (int32_t g : members[f]) emit(g, -1, -1);
+    for (int i = 0; i < ncp; ++i) {
+      int cell = sp.cells[(size_t)f * ncp + i];
+      int64_t o = cp.off[cell] + cp.p[cell], e = cp.off[cell + 1];
+      for (int64_t t = o; t < e; ++t) {
+        int32_t g = cp.dofs[t];
+        if (!alive[g]) continue;
+        if (gkey(cp.packed[cp.slot[g]]) == fk) continue;
+        bool earlier = false;
+        for (int j = 0; j < i && !earlier; ++j) {
+          const int32_t* cj = &cellxyz[((size_t)f * ncp + j) * 3];
+          earlier = pos_in_cell(cp, g, cj[0], cj[1], cj[2]) >= 0;
+        }
+        if (!earlier) emit(g, i, (int32_t)(t - o));
+      }
+    }
+  };
+  std::vector<int64_t> cnt(nf, 0);
+  parallel_for(nf, [&](int64_t f) {
+    int64_t c = 0;
+    for_rows((int)f, [&](int32_t, int, int32_t) { ++c; });
+    cnt[f] = c;
+    sp.nF[f] = (int32_t)members[f].size();
+    sp.nR[f] = (int32_t)(c - sp.nF[f]);
+  });
+  sp.rowOff.assign(nf + 1, 0);
+  for (int f = 0; f < nf; ++f) sp.rowOff[f + 1] = sp.rowOff[f] + cnt[f];
+  sp.rowDof.assign(sp.rowOff[nf], -1);
+  sp.rowPos.assign(sp.rowOff[nf] * ncp, -1);
+  parallel_for(nf, [&](int64_t f) {
+    int64_t r = sp.rowOff[f];
+    for_rows((int)f, [&](int32_t g, int src, int32_t srcpos) {
+      sp.rowDof[r] = g;
+      for (int i = 0; i < ncp; ++i) {
+        int32_t pos;
+        if (i == src) {
+          pos = srcpos;
+        } else {
+          const int32_t* ci = &cellxyz[((size_t)f * ncp + i) * 3];
+          pos = pos_in_cell(cp, g, ci[0], ci[1], ci[2]);
+        }
+        sp.rowPos[r * ncp + i] = pos;
+      }
+      ++r;
+    });
+  });
+}
+
+}  // namespace hif

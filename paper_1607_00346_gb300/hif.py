@@ -1,0 +1,235 @@
+"""Python binding of the HIF C ABI (include/hif.h).
+
+Argument marshalling only: every step of the factorization, the apply and the
+solve runs in the CUDA library ``libhif.so``.  Arrays may be CUDA tensors
+(passed by device pointer, on the tensor's device) or numpy arrays / CPU
+tensors (passed by host pointer; the library copies them).  There is no CPU
+fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HIF_OK = 0
+STATUS = {0: "HIF_OK", 1: "HIF_ERR_INVALID_ARG", 2: "HIF_ERR_OOM", 3: "HIF_ERR_NOT_SPD",
+          4: "HIF_ERR_NO_CONVERGENCE", 5: "HIF_ERR_TIMEOUT", 6: "HIF_ERR_CUDA"}
+PREC_FP64, PREC_FP32 = 0, 1
+
+
+class HifError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_int), ("bc", ctypes.c_int)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("precision", ctypes.c_int),
+                ("use_graphs", ctypes.c_int), ("pcg_tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_int), ("levels", ctypes.c_int),
+                ("precision", ctypes.c_int), ("eps", ctypes.c_double),
+                ("root_size", ctypes.c_int),
+                ("active_after", ctypes.c_int64 * 16),
+                ("fronts", (ctypes.c_int64 * 3) * 16),
+                ("factor_seconds", ctypes.c_double),
+                ("level_seconds", ctypes.c_double * 17),
+                ("flops", ctypes.c_double),
+                ("factor_bytes", ctypes.c_size_t),
+                ("peak_bytes", ctypes.c_size_t),
+                ("stored_entries", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int),
+                ("apply_launches", ctypes.c_int)]
+
+
+_lib = None
+
+# every symbol declared in include/hif.h
+EXPORTS = ["hif_default_options", "hif_factor", "hif_apply", "hif_residual", "hif_solve",
+           "hif_query_stats", "hif_predict_bytes", "hif_destroy", "hif_last_error",
+           "hif_version"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libhif.so (built by ``build.build_library``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"HIF CUDA library not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.hif_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.hif_default_options.restype = None
+    lib.hif_factor.argtypes = [ctypes.POINTER(Grid), vp, vp, d, ctypes.POINTER(Options), vp,
+                               ctypes.POINTER(vp)]
+    lib.hif_factor.restype = i
+    lib.hif_apply.argtypes = [vp, vp, vp, i, vp]
+    lib.hif_apply.restype = i
+    lib.hif_residual.argtypes = [vp, vp, vp, vp, i, vp]
+    lib.hif_residual.restype = i
+    lib.hif_solve.argtypes = [vp, vp, vp, i, vp, ctypes.POINTER(ctypes.c_int),
+                              ctypes.POINTER(ctypes.c_double)]
+    lib.hif_solve.restype = i
+    lib.hif_query_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    lib.hif_query_stats.restype = i
+    lib.hif_predict_bytes.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Options)]
+    lib.hif_predict_bytes.restype = ctypes.c_size_t
+    lib.hif_destroy.argtypes = [vp]
+    lib.hif_destroy.restype = None
+    lib.hif_last_error.argtypes = []
+    lib.hif_last_error.restype = ctypes.c_char_p
+    lib.hif_version.argtypes = []
+    lib.hif_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != HIF_OK:
+        raise HifError(st, load().hif_last_error().decode())
+
+
+def _ptr(x):
+    """(pointer, keep-alive) for a torch tensor or numpy array of float64."""
+    if x is None:
+        return None, None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if x.dtype != torch.float64 or not x.is_contiguous():
+                raise TypeError("tensors must be contiguous float64")
+            return ctypes.c_void_p(x.data_ptr()), x
+    except ImportError:  # pragma: no cover
+        pass
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:  # pragma: no cover
+            pass
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().hif_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def predict_bytes(n: int, m: int, **opts) -> int:
+    g = Grid(n, m, 0)
+    o = default_options(**opts)
+    return int(load().hif_predict_bytes(ctypes.byref(g), ctypes.byref(o)))
+
+
+class Handle:
+    """A factorization F ~= A held on the device (hif_factor / hif_destroy)."""
+
+    def __init__(self, ptr: ctypes.c_void_p, n: int):
+        self._h = ptr
+        self.n = n
+        self.N = n ** 3
+
+    def close(self):
+        if self._h:
+            load().hif_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _nrhs(self, f):
+        size = int(np.prod(tuple(f.shape)))
+        if size % self.N:
+            raise ValueError("right-hand side size is not a multiple of n^3")
+        return size // self.N
+
+    def apply(self, f, u, stream=None):
+        """u = F^{-1} f (u preallocated, same shape and kind of memory as wanted)."""
+        fp, _k1 = _ptr(f)
+        up, _k2 = _ptr(u)
+        _check(load().hif_apply(self._h, fp, up, self._nrhs(f), _stream(stream)))
+        return u
+
+    def residual(self, f, u, r, stream=None):
+        fp, _a = _ptr(f)
+        up, _b = _ptr(u)
+        rp, _c = _ptr(r)
+        _check(load().hif_residual(self._h, fp, up, rp, self._nrhs(f), _stream(stream)))
+        return r
+
+    def solve(self, f, u, stream=None, check=True):
+        """PCG solve of A u = f; returns (iterations, relative residuals) per column."""
+        nrhs = self._nrhs(f)
+        fp, _a = _ptr(f)
+        up, _b = _ptr(u)
+        its = (ctypes.c_int * nrhs)()
+        rel = (ctypes.c_double * nrhs)()
+        st = load().hif_solve(self._h, fp, up, nrhs, _stream(stream), its, rel)
+        if check:
+            _check(st)
+        return list(its), list(rel)
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().hif_query_stats(self._h, ctypes.byref(s)))
+        L = s.levels
+        return dict(n=s.n, m=s.m, levels=L, precision=s.precision, eps=s.eps,
+                    root_size=s.root_size, active_after=list(s.active_after)[:L],
+                    fronts=[list(s.fronts[i]) for i in range(L + 1)],
+                    factor_seconds=s.factor_seconds,
+                    level_seconds=list(s.level_seconds)[:L + 1], flops=s.flops,
+                    factor_bytes=s.factor_bytes, peak_bytes=s.peak_bytes,
+                    stored_entries=s.stored_entries, kernel_launches=s.kernel_launches,
+                    apply_launches=s.apply_launches)
+
+
+def factor(n: int, m: int, a, b=None, b_const: float = 0.0, eps: float = 1e-6,
+           precision: int = PREC_FP64, pcg_tol: float = 1e-10, max_iter: int = 200,
+           stream=None) -> Handle:
+    """hif_factor: a (and b) are n^3 float64 arrays, host or device."""
+    g = Grid(n, m, 0)
+    o = default_options(eps=eps, precision=precision, pcg_tol=pcg_tol, max_iter=max_iter)
+    ap, _ka = _ptr(a)
+    bp, _kb = _ptr(b)
+    out = ctypes.c_void_p()
+    _check(load().hif_factor(ctypes.byref(g), ap, bp, float(b_const), ctypes.byref(o),
+                             _stream(stream), ctypes.byref(out)))
+    return Handle(out, n)

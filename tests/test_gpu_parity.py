@@ -1,0 +1,184 @@
+"""GPU path vs the CPU oracle on the same seeded inputs (through the C ABI).
+
+Tolerances:
+  * eps = 0 (exact multifrontal elimination): F^{-1} f agrees with the oracle
+    and with a dense Cholesky solve to 1e-10 relative in FP64;
+  * eps > 0: the solve error e_s = ||x - F^{-1} A x|| / ||x|| of the GPU factor
+    is within 2x the oracle's (+ an FP64 rounding floor of 1e-12): the two
+    sides may pick different, equally valid skeletons on ties;
+  * PCG: relative residual <= 1e-10 (checked again on the CPU with the
+    oracle's operator), solution vs the dense solve within 1e-8.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import hif as ohif
+from oracle import krylov, stencil
+from paper_1607_00346_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_00346_gb300 import build, hif
+    build.build_library()
+    hif.load()
+    return hif
+
+
+def _coeff(n, seed, lo=-1.0, hi=1.0):
+    return inputs.coeff_log_uniform(n, lo, hi, seed)
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _gpu_apply(h, f):
+    fd = _dev(f)
+    ud = torch.empty_like(fd)
+    h.apply(fd, ud)
+    torch.cuda.synchronize()
+    return ud.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,m,b", [(8, 4, 0.0), (16, 4, 0.3), (12, 3, 0.0), (20, 5, 0.1)])
+def test_exact_mode_matches_oracle_and_dense(H, n, m, b):
+    a = _coeff(n, 100 + n)
+    A = stencil.assemble(a, b, n)
+    f = inputs.normal_rhs(n, 3, 200 + n)
+    h = H.factor(n, m, _dev(a), b_const=b, eps=0.0)
+    u = _gpu_apply(h, f)
+    ref = sla.cho_solve(sla.cho_factor(A.toarray()), f.T).T
+    assert np.linalg.norm(u - ref) <= 1e-10 * np.linalg.norm(ref)
+    fac = ohif.hif_factor(A, n, m, 0.0)
+    uo = ohif.hif_apply(fac, f)
+    assert np.linalg.norm(u - uo) <= 1e-10 * np.linalg.norm(uo)
+    st = h.stats()
+    assert st["root_size"] == fac.root_size == n ** 3 - (n - 1) ** 3
+
+
+def _es_gpu(h, A, x):
+    return np.linalg.norm(x - _gpu_apply(h, A @ x)) / np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("n,eps,lo,hi", [(16, 1e-6, 0.0, 0.0), (16, 1e-3, -1.0, 1.0),
+                                         (32, 1e-4, -1.0, 1.0), (32, 1e-6, -1.0, 1.0)])
+def test_skeletonized_solve_error_within_2x_oracle(H, n, eps, lo, hi):
+    a = inputs.coeff_constant(n) if lo == hi else _coeff(n, 300 + n, lo, hi)
+    A = stencil.assemble(a, 0.0, n)
+    x = inputs.normal_rhs(n, 1, 400 + n)[0]
+    h = H.factor(n, 4, _dev(a), eps=eps)
+    es_g = _es_gpu(h, A, x)
+    fac = ohif.hif_factor(A, n, 4, eps, check=False)
+    es_o = krylov.solve_error(A, fac, x)
+    assert es_g <= 2.0 * es_o + 1e-12, (es_g, es_o)
+    st = h.stats()
+    # both sides compress: root well below the exact-mode size, close to the oracle's
+    assert st["root_size"] <= n ** 3 - (n - 1) ** 3
+    assert abs(st["root_size"] - fac.root_size) <= 0.1 * fac.root_size + 8
+
+
+def test_laplace16_config(H):
+    # 16^3, a = 1, b = 0, eps = 1e-6, one N(0,1) right-hand side
+    w = inputs.workload("laplace16")
+    n = w["n"]
+    a = inputs.make_coeff(n, w["a"], w["seed"])
+    f = inputs.normal_rhs(n, w["nrhs"], w["seed"] + 1)
+    A = stencil.assemble(a, w["b"], n)
+    h = H.factor(n, w["m"], _dev(a), b_const=w["b"], eps=w["eps"])
+    u = torch.zeros(f.shape, dtype=torch.float64, device="cuda")
+    its, rel = h.solve(_dev(f), u)
+    uc = u.cpu().numpy()
+    assert rel[0] <= 1e-10 and its[0] <= 5
+    r = f[0] - A @ uc[0]
+    assert np.linalg.norm(r) <= 1.0000001e-10 * np.linalg.norm(f[0])
+    ref = sla.cho_solve(sla.cho_factor(A.toarray()), f[0])
+    assert np.linalg.norm(uc[0] - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pcg_multi_rhs(H, precision):
+    n = 32
+    a = _coeff(n, 501)
+    A = stencil.assemble(a, 0.1, n)
+    f = inputs.normal_rhs(n, 4, 502)
+    h = H.factor(n, 4, _dev(a), b_const=0.1, eps=1e-6, precision=precision)
+    u = torch.zeros(f.shape, dtype=torch.float64, device="cuda")
+    its, rel = h.solve(_dev(f), u)
+    uc = u.cpu().numpy()
+    for c in range(4):
+        assert rel[c] <= 1e-10
+        assert np.linalg.norm(f[c] - A @ uc[c]) <= 1.0000001e-10 * np.linalg.norm(f[c])
+    assert max(its) <= (6 if precision == 0 else 25)
+    # against the oracle's own PCG (FP64 factor, same eps): both at 1e-10 residual
+    fac = ohif.hif_factor(A, n, 4, 1e-6, check=False)
+    uo, ito, _ = krylov.pcg(A, fac, f[1], tol=1e-12)
+    assert np.linalg.norm(uc[1] - uo) <= 1e-8 * np.linalg.norm(uo)
+
+
+def test_residual_matches_oracle_operator(H):
+    n = 16
+    a = _coeff(n, 601)
+    A = stencil.assemble(a, 0.25, n)
+    h = H.factor(n, 4, _dev(a), b_const=0.25, eps=0.0)
+    f, u = inputs.normal_rhs(n, 2, 602), inputs.normal_rhs(n, 2, 603)
+    r = torch.empty(f.shape, dtype=torch.float64, device="cuda")
+    h.residual(_dev(f), _dev(u), r)
+    ref = f - (A @ u.T).T
+    assert np.allclose(r.cpu().numpy(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_host_pointers_and_in_place(H):
+    n = 16
+    a = _coeff(n, 701)
+    h = H.factor(n, 4, a, eps=1e-4)                  # host array in
+    f = inputs.normal_rhs(n, 1, 702)
+    u_host = np.zeros_like(f)
+    h.apply(f, u_host)                               # host in, host out
+    u_dev = _gpu_apply(h, f)
+    assert np.array_equal(u_host, u_dev)
+    fd = _dev(f)
+    h.apply(fd, fd)                                  # in place
+    assert np.array_equal(fd.cpu().numpy(), u_dev)
+
+
+def test_deterministic_reruns(H):
+    n = 32
+    a = _coeff(n, 801)
+    f = inputs.normal_rhs(n, 2, 802)
+    u1 = _gpu_apply(H.factor(n, 4, _dev(a), eps=1e-4, precision=1), f)
+    u2 = _gpu_apply(H.factor(n, 4, _dev(a), eps=1e-4, precision=1), f)
+    assert np.array_equal(u1, u2)
+
+
+def test_fp32_factor_preconditioner_quality(H):
+    n = 32
+    a = _coeff(n, 901)
+    A = stencil.assemble(a, 0.0, n)
+    x = inputs.normal_rhs(n, 1, 902)[0]
+    h64 = H.factor(n, 4, _dev(a), eps=1e-6, precision=0)
+    h32 = H.factor(n, 4, _dev(a), eps=1e-6, precision=1)
+    e64, e32 = _es_gpu(h64, A, x), _es_gpu(h32, A, x)
+    assert e64 < 1e-5
+    assert e32 < 1e-2
+
+
+def test_invalid_coefficients(H):
+    n = 8
+    a = np.ones(n ** 3)
+    a[17] = -1.0
+    with pytest.raises(H.HifError) as e:
+        H.factor(n, 4, _dev(a))
+    assert e.value.status == 1
+    a[17] = np.nan
+    with pytest.raises(H.HifError):
+        H.factor(n, 4, _dev(a))
+    # the context is still usable afterwards
+    h = H.factor(n, 4, _dev(np.ones(n ** 3)), eps=0.0)
+    assert h.stats()["root_size"] == n ** 3 - (n - 1) ** 3
