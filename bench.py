@@ -1,0 +1,366 @@
+"""Benchmark: HIF factorization + PCG solve on one GB300 (or N independent replicas).
+
+A step = one pass of the whole hot path on one synthetic operator: the
+factorization F ~= A (every level: cell elimination, face and edge
+skeletonization, merge; then the root) and the PCG solve of A u = f with F^{-1}
+as preconditioner to ||r|| <= 1e-10 ||f||.  Workload (default): 128^3 grid
+(N = 2,097,152), a = 10^U(-1,1) iid per grid point, b = 0.1, eps = 1e-6, FP32
+factor, FP64 residual, one N(0,1) right-hand side.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints ONE JSON line (rank 0).  value = MDOF/s over all ranks = N * nrhs * K *
+ranks / (max over ranks of the timed seconds).  --impl reference times the CPU
+oracle (test infrastructure, FP64) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HIF factor s + PCG solve MDOF/s at 128^3, eps=1e-6, 1e-10 resid; p50/p99 latency"
+UNIT = "MDOF/s"
+
+WORKLOADS = {
+    "contrast128": dict(n=128, m=4, lo=-1.0, hi=1.0, b=0.1, eps=1e-6, nrhs=1),
+    "contrast64": dict(n=64, m=4, lo=-1.0, hi=1.0, b=0.0, eps=1e-6, nrhs=8),
+    "laplace16": dict(n=16, m=4, lo=0.0, hi=0.0, b=0.0, eps=1e-6, nrhs=1),
+    "contrast256": dict(n=256, m=4, lo=-3.0, hi=3.0, b=0.0, eps=1e-4, nrhs=1),
+}
+
+# FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 peak of the part (1.25 TFLOP/s, the quoted dense FP64 rate of GB300)
+FP64_ALU_PEAK_TFLOPS = 1.25
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(w: dict, n_sample: int, seed: int):
+    """Time the CPU oracle (factor + PCG) on an n_sample^3 grid of the same law."""
+    import numpy as np
+
+    from oracle import hif as ohif
+    from oracle import krylov, stencil
+    from paper_1607_00346_gb300 import inputs
+
+    a = inputs.coeff_log_uniform(n_sample, w["lo"], w["hi"], seed) if w["hi"] > w["lo"] \
+        else inputs.coeff_constant(n_sample)
+    f = inputs.normal_rhs(n_sample, 1, seed + 1)[0]
+    t0 = time.perf_counter()
+    A = stencil.assemble(a, w["b"], n_sample)
+    fac = ohif.hif_factor(A, n_sample, w["m"], w["eps"], check=False)
+    u, its, hist = krylov.pcg(A, fac, f, tol=1e-10)
+    dt = time.perf_counter() - t0
+    return dt, its, hist[-1], float(np.linalg.norm(f - A @ u) / np.linalg.norm(f))
+
+
+def run_reference(args, w):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    n_s = args.cpu_sample_n
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt, its, rel, _ = cpu_oracle_sample(w, n_s, 20260101 + i)
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = n_s ** 3 * len(times) / total / 1e6
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload} law on a {n_s}^3 sample grid "
+                               f"(N={n_s ** 3}): CPU oracle factor + PCG to 1e-10"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n_s}^3 grid of the same coefficient law, factor + PCG"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="contrast128", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--nrhs", type=int, default=0)
+    ap.add_argument("--no-fp64-form", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-n", type=int, default=32)
+    args = ap.parse_args()
+    w = dict(WORKLOADS[args.workload])
+    if args.nrhs:
+        w["nrhs"] = args.nrhs
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if dist.is_nccl_available() else "gloo")
+
+    import __graft_entry__ as ge
+    if rank == 0:
+        ge.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_1607_00346_gb300 import hif, inputs
+    hif.load()
+
+    n, m, nrhs = w["n"], w["m"], w["nrhs"]
+    N = n ** 3
+    prec = hif.PREC_FP32 if args.precision == "fp32" else hif.PREC_FP64
+    seed = inputs.SEED_BASE + 2
+    a_h = inputs.coeff_log_uniform(n, w["lo"], w["hi"], seed) if w["hi"] > w["lo"] \
+        else inputs.coeff_constant(n)
+    f_h = inputs.normal_rhs(n, nrhs, seed + 1)
+    a_d = torch.from_numpy(a_h).cuda()
+    f_d = torch.from_numpy(f_h).cuda()
+    u_d = torch.zeros_like(f_d)
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None, keep=False):
+        if evs:
+            evs[0].record(stream)
+        h = hif.factor(n, m, a_d, b_const=w["b"], eps=w["eps"], precision=prec)
+        if evs:
+            evs[1].record(stream)
+        its, rel = h.solve(f_d, u_d)
+        if evs:
+            evs[2].record(stream)
+        st = h.stats()
+        if keep:
+            return its, rel, st, h
+        h.close()
+        return its, rel, st, None
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    # timed region: device events on the launching stream, barrier + sync around
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    hif.profile_begin()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    sub = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    ev[0].record(stream)
+    per_step, its_all, rel_all, stats, hlast = [], [], [], None, None
+    for k in range(args.steps):
+        its, rel, stats, hk = step(sub[k], keep=(k == args.steps - 1))
+        ev[k + 1].record(stream)
+        its_all.append(its)
+        rel_all.append(rel)
+        hlast = hk or hlast
+    barrier()
+    prof = hif.profile_end()
+    clocks = clk.stop()
+    for k in range(args.steps):
+        per_step.append(ev[k].elapsed_time(ev[k + 1]) / 1e3)
+    fac_s = [sub[k][0].elapsed_time(sub[k][1]) / 1e3 for k in range(args.steps)]
+    sol_s = [sub[k][1].elapsed_time(sub[k][2]) / 1e3 for k in range(args.steps)]
+    total = sum(per_step)
+    if dist is not None:
+        t = torch.tensor([total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    value = N * nrhs * args.steps * ws / total / 1e6
+
+    # residual check of the last solve (FP64 operator, through the C ABI)
+    r = torch.empty_like(f_d)
+    hlast.residual(f_d, u_d, r)
+    relres_chk = float((r.norm() / f_d.norm()).item())
+    hlast.close()
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    a_pin = torch.from_numpy(a_h).pin_memory()
+    f_pin = torch.from_numpy(f_h).pin_memory()
+    u_pin = torch.zeros(f_h.shape, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with hif.factor(n, m, a_pin.numpy(), b_const=w["b"], eps=w["eps"], precision=prec) as h2:
+            h2.solve(f_pin.numpy(), u_pin.numpy())
+    barrier()
+    e2e_t = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_value = N * nrhs * e2e_steps * ws / e2e_t / 1e6
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    hbm_peak, peak_src = _peaks()
+    dom = max(prof, key=lambda p: p["seconds"])
+    launches = sum(p["launches"] for p in prof)
+    per_launch_s = dom["seconds"] / max(dom["launches"], 1)
+    if dom["name"] in ("chol_trailing_update", "trtri_row", "gemm_batched", "chol_panel"):
+        peak = FP32_ALU_PEAK_TFLOPS if prec == hif.PREC_FP32 else FP64_ALU_PEAK_TFLOPS
+        ach = dom["flops"] / max(dom["launches"], 1) / per_launch_s / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "kernel": dom["name"],
+                "peak_source": "unit counts x max clock"}
+    else:
+        ach = dom["bytes"] / max(dom["launches"], 1) / per_launch_s / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": None, "kernel": dom["name"],
+                "peak_source": f"{peak_src} hbm_gbs"}
+    roof["share"] = dom["seconds"] / max(sum(p["seconds"] for p in prof), 1e-12)
+
+    # the plain FP64 GPU form of the same step (comparison point), one run
+    fp64_form = None
+    if not args.no_fp64_form and prec == hif.PREC_FP32:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = hif.factor(n, m, a_d, b_const=w["b"], eps=w["eps"], precision=hif.PREC_FP64)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        its64, rel64 = h.solve(f_d, torch.zeros_like(f_d))
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        h.close()
+        fp64_form = {"factor_s": t1 - t0, "solve_s": t2 - t1, "pcg_iters": its64,
+                     "value": N * nrhs / (t2 - t0) / 1e6}
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and ws == 1:
+        dt, its_c, rel_c, _ = cpu_oracle_sample(w, args.cpu_sample_n, seed)
+        cpu = {"value": args.cpu_sample_n ** 3 / dt / 1e6, "unit": UNIT, "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"CPU oracle factor + PCG on a {args.cpu_sample_n}^3 grid of the same "
+                         f"coefficient law (N={args.cpu_sample_n ** 3}), {dt:.1f} s"}
+
+    lat = sorted(per_step)
+    p50 = statistics.median(lat)
+    p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == hif.PREC_FP32 else "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: n={n} (N={N}), m={m}, "
+                                   f"a=10^U({w['lo']},{w['hi']}) iid per point, b={w['b']}, "
+                                   f"eps={w['eps']}, {args.precision} factor, FP64 PCG to 1e-10, "
+                                   f"nrhs={nrhs}",
+                       "l2": "inputs and factor larger than L2 (no flush needed)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "latency_ms": {"p50": 1e3 * p50, "p99": 1e3 * p99},
+            "factor_s": statistics.median(fac_s), "solve_s": statistics.median(sol_s),
+            "solve_mdofs": N * nrhs / statistics.median(sol_s) / 1e6,
+            "pcg_iters": its_all[-1], "relres": rel_all[-1], "relres_check": relres_chk,
+            "root_size": stats["root_size"], "factor_gflop": stats["flops"] / 1e9,
+            "factor_bytes": stats["factor_bytes"], "peak_bytes": stats["peak_bytes"],
+            "clocks": clocks, "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N * (1 + nrhs),
+                    "d2h_bytes_per_step": 8 * N * nrhs},
+            "roofline": roof, "cpu_baseline": cpu, "fp64_form": fp64_form,
+            "kernels": {p["name"]: round(p["seconds"] / args.steps, 5) for p in
+                        sorted(prof, key=lambda p: -p["seconds"])[:8]},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

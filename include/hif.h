@@ -147,6 +147,25 @@ hif_status hif_query_stats(hif_handle h, hif_stats* st);
  */
 size_t hif_predict_bytes(const hif_grid* grid, const hif_options* opt);
 
+/*
+ * Kernel profiling.  hif_profile_begin() clears the record and starts timing
+ * every kernel the library launches (CUDA events on the launching stream);
+ * hif_profile_end() stops, waits for the recorded events and writes up to
+ * cap per-kernel aggregates (*count receives the number available).  flops
+ * and bytes are the algorithmic counts of the launches (0 where not defined).
+ * Process-wide; meant for benchmarking, not for concurrent use.
+ */
+typedef struct {
+  char name[48];
+  int64_t launches;
+  double seconds;
+  double flops;
+  double bytes;
+} hif_kernel_profile;
+
+hif_status hif_profile_begin(void);
+hif_status hif_profile_end(hif_kernel_profile* out, int cap, int* count);
+
 /* Release every resource of the handle (NULL is ignored). */
 void hif_destroy(hif_handle h);
 

@@ -31,6 +31,28 @@ void set_last_error(const std::string& msg);
 
 // Every kernel launch is followed by HIF_CHECK_LAUNCH(), which also counts it.
 int64_t& launch_counter();
+// Profiling: while hif_profile_begin() is in force, a ProfScope records CUDA
+// events around the launches made during its lifetime, attributed to `name`
+// with the given algorithmic flops and bytes.
+bool prof_enabled();
+// Add algorithmic counts to a kernel's record without a launch (used when the
+// counts are only known after the launch, e.g. the ranks found by the ID).
+void prof_add(const char* name, double flops, double bytes);
+class ProfScope {
+ public:
+  ProfScope(const char* name, cudaStream_t st, double flops = 0.0, double bytes = 0.0);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  cudaStream_t st_;
+  bool active_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+  std::string name_;
+  double flops_ = 0.0, bytes_ = 0.0;
+};
+
 #define HIF_CHECK_LAUNCH()                 \
   do {                                     \
     ++::hif::launch_counter();             \

@@ -6,6 +6,7 @@
 // 2-D grid: blockIdx.y = descriptor, blockIdx.x = tile / chunk inside it.
 // Fronts whose work is finished, and tiles outside a front, exit at once.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "dense.cuh"
@@ -427,19 +428,41 @@ void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront
     const int chunks = std::max(1, ceil_div(std::max(0, nm - j1min), PANEL_ROWS));
     int ntile = ceil_div(std::max(0, nm - j1min), TILE);
     const int pairs = std::max(1, ntile * (ntile + 1) / 2);
+    // algorithmic counts of this step (only while profiling)
+    double pf = 0, pb = 0, sf = 0, sb = 0;
+    if (prof_enabled()) {
+      for (int f = 0; f < nact; ++f) {
+        const double jb = std::min(NB, h_fronts[f].p - j0);
+        const double rest = h_fronts[f].n - j0 - jb;
+        pf += jb * jb * jb / 3.0 + rest * jb * jb;
+        pb += sizeof(T) * (jb * jb / 2.0 + 2.0 * rest * jb);
+        sf += rest * (rest + 1.0) * jb;
+        sb += sizeof(T) * (rest * jb + rest * (rest + 1.0));
+      }
+    }
     for (int f0 = 0; f0 < nact; f0 += MAX_GRID_Y) {
       const int nb = std::min(MAX_GRID_Y, nact - f0);
-      k_panel<T><<<dim3(chunks, nb), PANEL_ROWS, 0, st>>>(d_fronts + f0, Karena, Parena, j0,
-                                                          d_flags);
-      HIF_CHECK_LAUNCH();
-      k_syrk<T><<<dim3(pairs, nb), 256, 0, st>>>(d_fronts + f0, Karena, j0);
-      HIF_CHECK_LAUNCH();
+      {
+        ProfScope ps("chol_panel", st, pf, pb);
+        k_panel<T><<<dim3(chunks, nb), PANEL_ROWS, 0, st>>>(d_fronts + f0, Karena, Parena, j0,
+                                                            d_flags);
+        HIF_CHECK_LAUNCH();
+      }
+      {
+        ProfScope ps("chol_trailing_update", st, sf, sb);
+        k_syrk<T><<<dim3(pairs, nb), 256, 0, st>>>(d_fronts + f0, Karena, j0);
+        HIF_CHECK_LAUNCH();
+      }
     }
   }
   // Linv = L^{-1}: diagonal blocks, then block rows
   const int nblk = ceil_div(pmax, NB);
   for (int f0 = 0; f0 < nfront; f0 += MAX_GRID_Y) {
     const int nb = std::min(MAX_GRID_Y, nfront - f0);
+    double fl = 0;
+    if (prof_enabled())
+      for (int f = f0; f < f0 + nb; ++f) fl += std::pow((double)h_fronts[f].p, 1) * NB * NB / 3.0;
+    ProfScope ps("trtri_diag", st, fl, 0.0);
     k_trtri_diag<T><<<dim3(nblk, nb), NB, 0, st>>>(d_fronts + f0, Parena);
     HIF_CHECK_LAUNCH();
   }
@@ -448,6 +471,9 @@ void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront
     while (nact < nfront && h_fronts[nact].p > bi * NB) ++nact;
     for (int f0 = 0; f0 < nact; f0 += MAX_GRID_Y) {
       const int nb = std::min(MAX_GRID_Y, nact - f0);
+      double fl = 0;
+      if (prof_enabled()) fl = (double)nb * (bi * (bi + 1) / 2.0 + bi) * 2.0 * NB * NB * NB;
+      ProfScope ps("trtri_row", st, fl, 0.0);
       k_trtri_row<T><<<dim3(bi, nb), 256, 0, st>>>(d_fronts + f0, Karena, Parena, bi);
       HIF_CHECK_LAUNCH();
       }
@@ -463,6 +489,10 @@ void gemm_batched(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const T* A
     mt = std::max(mt, ceil_div(h_ops[i].m, TILE) * ceil_div(h_ops[i].n, TILE));
   for (int f0 = 0; f0 < nops; f0 += MAX_GRID_Y) {
     const int nb = std::min(MAX_GRID_Y, nops - f0);
+    double fl = 0;
+    if (prof_enabled())
+      for (int i = f0; i < f0 + nb; ++i) fl += 2.0 * h_ops[i].m * (double)h_ops[i].n * h_ops[i].k;
+    ProfScope ps("gemm_batched", st, fl, 0.0);
     k_gemm<T><<<dim3(mt, nb), 256, 0, st>>>(d_ops + f0, Abase, Bbase, Cbase);
     HIF_CHECK_LAUNCH();
   }
@@ -481,6 +511,17 @@ void gemv_batched(const GemvOp* d_ops, const GemvOp* h_ops, int nops, int trans,
     for (int f0 = 0; f0 < nops; f0 += MAX_GRID_Y) {
       const int nb = std::min(MAX_GRID_Y, nops - f0);
       dim3 grid(mx, nb);
+      double by = 0, fl = 0;
+      if (prof_enabled()) {
+        for (int i = f0; i < f0 + nb; ++i) {
+          const GemvOp& o = h_ops[i];
+          double ent = (double)o.rows * o.cols;
+          if (o.tri) ent = 0.5 * (double)o.cols * (o.cols + 1);
+          by += sizeof(T) * (ent + (double)R * (o.rows + o.cols) * (o.beta_one ? 1.5 : 1.0));
+          fl += 2.0 * ent * R;
+        }
+      }
+      ProfScope ps(trans ? "apply_gemv_t" : "apply_gemv_n", st, fl, by);
       if (trans) {
         if (R == 8) k_gemv_t<T, 8><<<grid, 256, 0, st>>>(d_ops + f0, Marena, w, vstride);
         else k_gemv_t<T, 1><<<grid, 256, 0, st>>>(d_ops + f0, Marena, w, vstride);

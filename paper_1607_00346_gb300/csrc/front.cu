@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(256) k_skel_writeback(const SkelDesc* __restri
 void stencil_coefficients(const double* a, const double* b, double b_const, int n,
                           double* cpl, double* diag, int* d_bad, cudaStream_t st) {
   const int64_t N = (int64_t)n * n * n;
+  ProfScope ps("stencil_coefficients", st, 0.0, 8.0 * N * (b ? 6.0 : 5.0));
   k_stencil<<<ceil_div(N, 256), 256, 0, st>>>(a, b, b_const, n, cpl, diag, d_bad);
   HIF_CHECK_LAUNCH();
 }
@@ -247,6 +248,7 @@ void assemble_level0(const CellDesc* d_cells, int ncell, const int32_t* lists, i
   if (smem > 48 * 1024)
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_assemble0<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
+  ProfScope ps("assemble_level0", st);
   k_assemble0<T><<<ncell, 128, smem, st>>>(d_cells, lists, n, s, cpl, diag, Karena);
   HIF_CHECK_LAUNCH();
 }
@@ -260,6 +262,10 @@ void merge_children(const MergeDesc* d_par, const MergeDesc* h_par, int npar,
   const int nt = ceil_div(nmax, 64);
   for (int f0 = 0; f0 < npar; f0 += MAX_GRID_Y) {
     const int nb = std::min(MAX_GRID_Y, npar - f0);
+    double by = 0;
+    if (prof_enabled())
+      for (int i = f0; i < f0 + nb; ++i) by += sizeof(T) * 0.5 * (double)h_par[i].n * (h_par[i].n + 1);
+    ProfScope ps("merge_children", st, 0.0, by);
     k_merge<T><<<dim3(nt * (nt + 1) / 2, nb), 256, 0, st>>>(d_par + f0, d_child, maps, Kchild,
                                                             Kpar);
     HIF_CHECK_LAUNCH();
@@ -274,6 +280,10 @@ void skel_gather(const SkelDesc* d_f, const SkelDesc* h_f, int nf, int ncp,
   for (int i = 0; i < nf; ++i) mx = std::max<int64_t>(mx, (int64_t)(h_f[i].nF + h_f[i].nR) * h_f[i].nF);
   for (int f0 = 0; f0 < nf; f0 += MAX_GRID_Y) {
     const int nb = std::min(MAX_GRID_Y, nf - f0);
+    double by = 0;
+    if (prof_enabled())
+      for (int i = f0; i < f0 + nb; ++i) by += sizeof(T) * (double)(h_f[i].nF + h_f[i].nR) * h_f[i].nF;
+    ProfScope ps("skel_gather", st, 0.0, by);
     k_skel_gather<T><<<dim3(ceil_div(mx, 256), nb), 256, 0, st>>>(d_f + f0, ncp, rowPos, d_cells,
                                                                   Karena, Garena);
     HIF_CHECK_LAUNCH();
@@ -287,6 +297,7 @@ void skel_permute(const SkelDesc* d_f, const SkelDesc* h_f, int nf, const int32_
   for (int i = 0; i < nf; ++i) mx = std::max<int64_t>(mx, (int64_t)h_f[i].nF * h_f[i].nF);
   for (int f0 = 0; f0 < nf; f0 += MAX_GRID_Y) {
     const int nb = std::min(MAX_GRID_Y, nf - f0);
+    ProfScope ps("skel_permute", st);
     k_skel_permute<T><<<dim3(ceil_div(mx, 256), nb), 256, 0, st>>>(d_f + f0, perm, Garena, Zarena);
     HIF_CHECK_LAUNCH();
   }
@@ -300,6 +311,7 @@ void skel_writeback(const SkelDesc* d_f, const SkelDesc* h_f, int nf, int ncp,
   for (int i = 0; i < nf; ++i) mx = std::max<int64_t>(mx, (int64_t)h_f[i].k * h_f[i].k);
   for (int f0 = 0; f0 < nf; f0 += MAX_GRID_Y) {
     const int nb = std::min(MAX_GRID_Y, nf - f0);
+    ProfScope ps("skel_writeback", st);
     k_skel_writeback<T><<<dim3(ceil_div(mx, 256), nb), 256, 0, st>>>(d_f + f0, ncp, rowPos, perm,
                                                                      d_cells, Zarena, Karena);
     HIF_CHECK_LAUNCH();

@@ -22,8 +22,9 @@
 namespace hif {
 
 template <typename T>
-void interpolative_decomposition(SkelDesc* d_f, int nf, T* Garena, int32_t* perm, T* Farena,
-                                 double* scratch, double eps, cudaStream_t st);
+void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* Garena,
+                                 int32_t* perm, T* Farena, double* scratch, int32_t* stepAr,
+                                 double eps, cudaStream_t st);
 
 namespace {
 thread_local std::string g_last_error;
@@ -456,17 +457,19 @@ void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& a
     toff += (int64_t)(d.nF / 2) * (d.nF - d.nF / 2);
     F_.stats.flops += 2.0 * d.nR * (double)d.nF * d.nF;
   }
-  DevBuf rowpos_d, sd_d, G, perm_d, scratch, tm;
+  DevBuf rowpos_d, sd_d, G, perm_d, scratch, steps, tm;
   upload(rowpos_d, sp.rowPos, &F_.mem, st_);
   upload(sd_d, sd, &F_.mem, st_);
   G.alloc(sizeof(T) * std::max<int64_t>(1, goff), &F_.mem);
   perm_d.alloc(sizeof(int32_t) * poff, &F_.mem);
   scratch.alloc(sizeof(double) * 2 * poff, &F_.mem);
+  steps.alloc(sizeof(int32_t) * poff, &F_.mem);
   tm.alloc(sizeof(T) * std::max<int64_t>(1, toff), &F_.mem);
   skel_gather<T>(sd_d.as<SkelDesc>(), sd.data(), nf, ncp, rowpos_d.as<int32_t>(),
                  cdesc_d.as<CellDesc>(), Kar.as<T>(), G.as<T>(), st_);
-  interpolative_decomposition<T>(sd_d.as<SkelDesc>(), nf, G.as<T>(), perm_d.as<int32_t>(),
-                                 tm.as<T>(), scratch.as<double>(), F_.eps, st_);
+  interpolative_decomposition<T>(sd_d.as<SkelDesc>(), sd.data(), nf, G.as<T>(),
+                                 perm_d.as<int32_t>(), tm.as<T>(), scratch.as<double>(),
+                                 steps.as<int32_t>(), F_.eps, st_);
   std::vector<int32_t> perm(poff);
   HIF_CUDA_TRY(cudaMemcpyAsync(sd.data(), sd_d.as<void>(), sizeof(SkelDesc) * nf,
                                cudaMemcpyDeviceToHost, st_));
@@ -474,6 +477,20 @@ void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& a
                                cudaMemcpyDeviceToHost, st_));
   HIF_CUDA_TRY(cudaStreamSynchronize(st_));
   scratch.release();
+  steps.release();
+  if (prof_enabled()) {
+    // unblocked CPQR: each of the k steps reads and writes the trailing
+    // (nR - i) x (nF - i - 1) block once and spends 4 flops per entry on it
+    double fl = 0.0, by = 0.0;
+    for (int f = 0; f < nf; ++f) {
+      for (int i = 0; i < sd[f].k; ++i) {
+        const double e = (double)(sd[f].nR - i) * (sd[f].nF - i - 1);
+        fl += 4.0 * e;
+        by += 2.0 * sizeof(T) * e;
+      }
+    }
+    prof_add("id_cpqr", fl, by);
+  }
   // fronts with redundant DOFs are eliminated; the others keep every DOF
   std::vector<int> act;
   for (int f = 0; f < nf; ++f)

@@ -1,6 +1,8 @@
 // Vector kernels: gathers and scatters of the apply sweeps (deterministic, no
 // atomics), the seven-point residual in double, dot products and updates of
 // the preconditioned conjugate gradients.
+#include <algorithm>
+
 #include "solve.cuh"
 
 namespace hif {
@@ -134,6 +136,7 @@ template <typename T>
 void vec_gather(const int32_t* idx, int64_t cnt, const T* y, int64_t ys, T* work, int64_t vs,
                 int64_t voff, int nrhs, cudaStream_t st) {
   if (cnt == 0) return;
+  ProfScope ps("apply_gather", st, 0.0, (double)cnt * (4.0 + 2.0 * sizeof(T) * nrhs));
   k_gather<T><<<grid1(cnt), VT, 0, st>>>(idx, cnt, y, ys, work, vs, voff, nrhs);
   HIF_CHECK_LAUNCH();
 }
@@ -142,6 +145,7 @@ template <typename T>
 void vec_set(const int32_t* g, const int32_t* pos, int64_t cnt, T* y, int64_t ys,
              const T* work, int64_t vs, int nrhs, cudaStream_t st) {
   if (cnt == 0) return;
+  ProfScope ps("apply_scatter", st, 0.0, (double)cnt * (8.0 + 2.0 * sizeof(T) * nrhs));
   k_set<T><<<grid1(cnt), VT, 0, st>>>(g, pos, cnt, y, ys, work, vs, nrhs);
   HIF_CHECK_LAUNCH();
 }
@@ -150,6 +154,7 @@ template <typename T>
 void vec_accumulate(const int32_t* tgt, const int64_t* ptr, const int32_t* src, int64_t ntgt,
                     T* y, int64_t ys, const T* work, int64_t vs, int nrhs, cudaStream_t st) {
   if (ntgt == 0) return;
+  ProfScope ps("apply_accumulate", st);
   k_acc<T><<<grid1(ntgt), VT, 0, st>>>(tgt, ptr, src, ntgt, y, ys, work, vs, nrhs);
   HIF_CHECK_LAUNCH();
 }
@@ -157,6 +162,7 @@ void vec_accumulate(const int32_t* tgt, const int64_t* ptr, const int32_t* src, 
 template <typename T>
 void vec_convert_in(const double* x, T* y, int64_t cnt, cudaStream_t st) {
   if (cnt == 0) return;
+  ProfScope ps("convert", st, 0.0, (double)cnt * (8.0 + sizeof(T)));
   k_cin<T><<<grid1(cnt), VT, 0, st>>>(x, y, cnt);
   HIF_CHECK_LAUNCH();
 }
@@ -164,6 +170,7 @@ void vec_convert_in(const double* x, T* y, int64_t cnt, cudaStream_t st) {
 template <typename T>
 void vec_convert_out(const T* y, double* x, int64_t cnt, cudaStream_t st) {
   if (cnt == 0) return;
+  ProfScope ps("convert", st, 0.0, (double)cnt * (8.0 + sizeof(T)));
   k_cout<T><<<grid1(cnt), VT, 0, st>>>(y, x, cnt);
   HIF_CHECK_LAUNCH();
 }
@@ -171,6 +178,7 @@ void vec_convert_out(const T* y, double* x, int64_t cnt, cudaStream_t st) {
 void residual(const double* cpl, const double* diag, int n, const double* f, const double* u,
               double* r, int nrhs, cudaStream_t st) {
   const int64_t N = (int64_t)n * n * n;
+  ProfScope ps("residual", st, 14.0 * N * nrhs, 8.0 * N * (4.0 + 3.0 * nrhs));
   k_stencil_apply<<<grid1(N), VT, 0, st>>>(cpl, diag, n, f, u, r, nrhs, 1);
   HIF_CHECK_LAUNCH();
 }
@@ -178,12 +186,14 @@ void residual(const double* cpl, const double* diag, int n, const double* f, con
 void matvec(const double* cpl, const double* diag, int n, const double* p, double* q, int nrhs,
             cudaStream_t st) {
   const int64_t N = (int64_t)n * n * n;
+  ProfScope ps("spmv", st, 13.0 * N * nrhs, 8.0 * N * (4.0 + 2.0 * nrhs));
   k_stencil_apply<<<grid1(N), VT, 0, st>>>(cpl, diag, n, nullptr, p, q, nrhs, 0);
   HIF_CHECK_LAUNCH();
 }
 
 void dots(const double* x, const double* y, int64_t N, int ncol, double* part, double* out,
           cudaStream_t st) {
+  ProfScope ps("dots", st, 2.0 * N * ncol, 16.0 * N * ncol);
   k_dot_part<<<dim3(DOT_BLOCKS, ncol), VT, 0, st>>>(x, y, N, part);
   HIF_CHECK_LAUNCH();
   k_dot_final<<<ncol, VT, 0, st>>>(part, out);
@@ -192,11 +202,13 @@ void dots(const double* x, const double* y, int64_t N, int ncol, double* part, d
 
 void axpy_cols(const double* a, double sign, const double* x, double* y, int64_t N, int ncol,
                cudaStream_t st) {
+  ProfScope ps("axpy", st, 2.0 * N * ncol, 24.0 * N * ncol);
   k_axpy<<<dim3(std::min<int64_t>(grid1(N), 2048), ncol), VT, 0, st>>>(a, sign, x, y, N);
   HIF_CHECK_LAUNCH();
 }
 
 void xpby_cols(const double* z, const double* b, double* p, int64_t N, int ncol, cudaStream_t st) {
+  ProfScope ps("axpy", st, 2.0 * N * ncol, 24.0 * N * ncol);
   k_xpby<<<dim3(std::min<int64_t>(grid1(N), 2048), ncol), VT, 0, st>>>(z, b, p, N);
   HIF_CHECK_LAUNCH();
 }

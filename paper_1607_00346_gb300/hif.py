@@ -57,8 +57,14 @@ _lib = None
 
 # every symbol declared in include/hif.h
 EXPORTS = ["hif_default_options", "hif_factor", "hif_apply", "hif_residual", "hif_solve",
-           "hif_query_stats", "hif_predict_bytes", "hif_destroy", "hif_last_error",
-           "hif_version"]
+           "hif_query_stats", "hif_predict_bytes", "hif_profile_begin", "hif_profile_end",
+           "hif_destroy", "hif_last_error", "hif_version"]
+
+
+class KernelProfile(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
+                ("seconds", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
 
 
 def library_path() -> str:
@@ -91,6 +97,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.hif_query_stats.restype = i
     lib.hif_predict_bytes.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Options)]
     lib.hif_predict_bytes.restype = ctypes.c_size_t
+    lib.hif_profile_begin.argtypes = []
+    lib.hif_profile_begin.restype = i
+    lib.hif_profile_end.argtypes = [ctypes.POINTER(KernelProfile), i, ctypes.POINTER(ctypes.c_int)]
+    lib.hif_profile_end.restype = i
     lib.hif_destroy.argtypes = [vp]
     lib.hif_destroy.restype = None
     lib.hif_last_error.argtypes = []
@@ -142,6 +152,21 @@ def default_options(**kw) -> Options:
     for k, v in kw.items():
         setattr(o, k, v)
     return o
+
+
+def profile_begin():
+    """Start timing every kernel the library launches (CUDA events)."""
+    _check(load().hif_profile_begin())
+
+
+def profile_end() -> list:
+    """Stop timing; per-kernel dicts (name, launches, seconds, flops, bytes)."""
+    cap = 128
+    arr = (KernelProfile * cap)()
+    cnt = ctypes.c_int()
+    _check(load().hif_profile_end(arr, cap, ctypes.byref(cnt)))
+    return [dict(name=arr[i].name.decode(), launches=arr[i].launches, seconds=arr[i].seconds,
+                 flops=arr[i].flops, bytes=arr[i].bytes) for i in range(min(cnt.value, cap))]
 
 
 def predict_bytes(n: int, m: int, **opts) -> int:
