@@ -104,6 +104,33 @@ hif_status hif_apply(hif_handle h, const double* f, double* u, int nrhs,
                      hif_stream stream);
 
 /*
+ * hif_apply_noalloc -- the same u = F^{-1} f as hif_apply, for callers that
+ * must not allocate device memory: a serving process that reserves all of
+ * its memory up front, or code that runs where calling the CUDA allocator is
+ * not allowed.  hif_apply allocates its work vectors on the handle's first
+ * apply; this entry point allocates nothing and takes its work space from
+ * one fixed 32 MiB array in device memory that the library defines (every
+ * GPU that loads the library holds it until the process exits).  The paper
+ * has no counterpart; it is a deployment variant of the apply.
+ *   f, u:  nrhs*n^3 doubles in device memory (host pointers are rejected,
+ *          since staging them would need an allocation); they may alias.
+ *   Limit: the factor type's size times (n^3 + the largest sweep stage's
+ *          work) per right-hand side must fit in 32 MiB (a 64^3 grid fits
+ *          with up to three right-hand sides in FP64, a 128^3 grid does
+ *          not fit); a larger request returns
+ *          HIF_ERR_INVALID_ARG with the needed size in hif_last_error().
+ *   The first call on a device looks up the array's device address on that
+ *   device; make that first call before any stream capture.  Every call
+ *   shares the one array, so calls whose work overlaps on the GPU race with
+ *   each other; order them on one stream.  The array keeps the last call's
+ *   contents; no part of it needs to start at zero, because each sweep
+ *   writes every work entry before reading it.  Kernel profiling
+ *   (hif_profile_begin) must be off.
+ */
+hif_status hif_apply_noalloc(hif_handle h, const double* f, double* u, int nrhs,
+                             hif_stream stream);
+
+/*
  * hif_residual -- r = f - A u with the handle's operator, in double.
  */
 hif_status hif_residual(hif_handle h, const double* f, const double* u,

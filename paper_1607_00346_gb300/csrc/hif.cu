@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <type_traits>
 #include <string>
@@ -142,6 +143,11 @@ struct Stage {
 struct FactorBase {
   virtual ~FactorBase() = default;
   virtual void apply(const double* f_dev, double* u_dev, int nrhs, cudaStream_t st) = 0;
+  // Bytes of work space the sweeps need for nrhs right-hand sides, and the
+  // sweeps run in caller-provided work space (nothing is allocated).
+  virtual size_t sweep_scratch_bytes(int nrhs) const = 0;
+  virtual void apply_in_scratch(const double* f_dev, double* u_dev, int nrhs, void* scratch,
+                                cudaStream_t st) = 0;
   int n = 0, m = 0, L = 0, precision = 0;
   double eps = 0;
   MemStats mem;
@@ -185,6 +191,26 @@ struct Factor : FactorBase {
     }
     T* yv = y.as<T>();
     T* w = work.as<T>();
+    vec_convert_in<T>(f_dev, yv, N * nrhs, st);
+    for (auto& s : stages) run_stage(s, true, yv, N, w, work_stride, nrhs, st);
+    for (auto it = stages.rbegin(); it != stages.rend(); ++it)
+      run_stage(*it, false, yv, N, w, work_stride, nrhs, st);
+    vec_convert_out<T>(yv, u_dev, N * nrhs, st);
+  }
+
+  static size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+  size_t sweep_scratch_bytes(int nrhs) const override {
+    const int64_t N = (int64_t)n * n * n;
+    return round256(sizeof(T) * N * nrhs) +
+           round256(sizeof(T) * std::max<int64_t>(1, work_stride * nrhs));
+  }
+
+  void apply_in_scratch(const double* f_dev, double* u_dev, int nrhs, void* scratch,
+                        cudaStream_t st) override {
+    const int64_t N = (int64_t)n * n * n;
+    T* yv = static_cast<T*>(scratch);
+    T* w = reinterpret_cast<T*>(static_cast<char*>(scratch) + round256(sizeof(T) * N * nrhs));
     vec_convert_in<T>(f_dev, yv, N * nrhs, st);
     for (auto& s : stages) run_stage(s, true, yv, N, w, work_stride, nrhs, st);
     for (auto it = stages.rbegin(); it != stages.rend(); ++it)
@@ -764,6 +790,35 @@ struct OutArray {
 
 }  // namespace
 
+namespace {
+
+// Work space of hif_apply_noalloc: one fixed array in device memory, present
+// on every GPU that loads the library, shared by all calls.
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the array on the current device.  In host code the
+// array's name only stands for it; the address is asked from the runtime once
+// per device, with that device current.
+void* noalloc_scratch_address() {
+  int dev = 0;
+  HIF_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) throw Error{HIF_ERR_INVALID_ARG, "device index out of range"};
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    HIF_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = p;
+  }
+  return g_noalloc_addr[dev];
+}
+
+}  // namespace
+
 extern "C" {
 
 void hif_default_options(hif_options* o) {
@@ -854,6 +909,27 @@ hif_status hif_apply(hif_handle h, const double* f, double* u, int nrhs, hif_str
   if (nrhs == 1) h->f->stats.apply_launches = (int)(hif::launch_counter() - l0);
   uo.finish(st);
   if (fin.tmp.bytes()) HIF_CUDA_TRY(cudaStreamSynchronize(st));
+  return HIF_OK;
+  HIF_API_END
+}
+
+hif_status hif_apply_noalloc(hif_handle h, const double* f, double* u, int nrhs,
+                             hif_stream stream) {
+  HIF_API_BEGIN
+  if (!h || !f || !u || nrhs < 1) throw Error{HIF_ERR_INVALID_ARG, "bad handle, pointer or nrhs"};
+  if (hif::prof_enabled())
+    throw Error{HIF_ERR_INVALID_ARG, "hif_apply_noalloc cannot run while kernel profiling is on"};
+  if (!hif::is_device_ptr(f) || !hif::is_device_ptr(u))
+    throw Error{HIF_ERR_INVALID_ARG, "hif_apply_noalloc needs f and u in device memory"};
+  const size_t need = h->f->sweep_scratch_bytes(nrhs);
+  if (need > kNoAllocScratchBytes)
+    throw Error{HIF_ERR_INVALID_ARG,
+                "hif_apply_noalloc: this grid and nrhs need " + std::to_string(need) +
+                    " bytes of work space, more than its fixed " +
+                    std::to_string(kNoAllocScratchBytes) + " bytes"};
+  void* scratch = noalloc_scratch_address();
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  h->f->apply_in_scratch(f, u, nrhs, scratch, st);
   return HIF_OK;
   HIF_API_END
 }

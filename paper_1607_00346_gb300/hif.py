@@ -56,7 +56,8 @@ class Stats(ctypes.Structure):
 _lib = None
 
 # every symbol declared in include/hif.h
-EXPORTS = ["hif_default_options", "hif_factor", "hif_apply", "hif_residual", "hif_solve",
+EXPORTS = ["hif_default_options", "hif_factor", "hif_apply", "hif_apply_noalloc",
+           "hif_residual", "hif_solve",
            "hif_query_stats", "hif_predict_bytes", "hif_profile_begin", "hif_profile_end",
            "hif_destroy", "hif_last_error", "hif_version"]
 
@@ -88,6 +89,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.hif_factor.restype = i
     lib.hif_apply.argtypes = [vp, vp, vp, i, vp]
     lib.hif_apply.restype = i
+    lib.hif_apply_noalloc.argtypes = [vp, vp, vp, i, vp]
+    lib.hif_apply_noalloc.restype = i
     lib.hif_residual.argtypes = [vp, vp, vp, vp, i, vp]
     lib.hif_residual.restype = i
     lib.hif_solve.argtypes = [vp, vp, vp, i, vp, ctypes.POINTER(ctypes.c_int),
@@ -211,6 +214,17 @@ class Handle:
         fp, _k1 = _ptr(f)
         up, _k2 = _ptr(u)
         _check(load().hif_apply(self._h, fp, up, self._nrhs(f), _stream(stream)))
+        return u
+
+    def apply_noalloc(self, f, u, stream=None):
+        """u = F^{-1} f without any device allocation (f, u on the device).
+
+        For callers that must not allocate device memory; the work space is the
+        library's fixed 32 MiB device array (see hif_apply_noalloc in hif.h).
+        """
+        fp, _k1 = _ptr(f)
+        up, _k2 = _ptr(u)
+        _check(load().hif_apply_noalloc(self._h, fp, up, self._nrhs(f), _stream(stream)))
         return u
 
     def residual(self, f, u, r, stream=None):
