@@ -6,7 +6,10 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <future>
 #include <memory>
 #include <mutex>
 #include <numeric>
@@ -25,7 +28,8 @@ namespace hif {
 template <typename T>
 void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* Garena,
                                  int32_t* perm, T* Farena, double* scratch, int32_t* stepAr,
-                                 double eps, cudaStream_t st);
+                                 T* Fscratch, double eps, cudaStream_t st);
+size_t id_fscratch_elems(int64_t total_front_dofs);
 
 namespace {
 thread_local std::string g_last_error;
@@ -41,6 +45,18 @@ using Clock = std::chrono::steady_clock;
 double seconds_since(Clock::time_point t0) {
   return std::chrono::duration<double>(Clock::now() - t0).count();
 }
+
+// HIF_TRACE=1 prints the wall time of each host phase of hif_factor to stderr.
+struct Trace {
+  bool on = std::getenv("HIF_TRACE") != nullptr;
+  Clock::time_point t = Clock::now();
+  void mark(int level, const char* what) {
+    if (!on) return;
+    const double ms = 1e3 * seconds_since(t);
+    std::fprintf(stderr, "[hif] level %d %-28s %9.2f ms\n", level, what, ms);
+    t = Clock::now();
+  }
+};
 
 // ---- device memory --------------------------------------------------------------
 
@@ -71,13 +87,30 @@ class DevBuf {
       ms_->peak = std::max(ms_->peak, ms_->cur);
     }
   }
+  // Stream-ordered: allocated and later freed in order on `st` (no device
+  // synchronisation); for the temporaries of one factorization.
+  void alloc_async(size_t bytes, MemStats* ms, cudaStream_t st) {
+    release();
+    ms_ = ms;
+    if (bytes == 0) return;
+    HIF_CUDA_TRY(cudaMallocAsync(&p_, bytes, st));
+    st_ = st;
+    async_ = true;
+    bytes_ = bytes;
+    if (ms_) {
+      ms_->cur += bytes;
+      ms_->peak = std::max(ms_->peak, ms_->cur);
+    }
+  }
   void release() {
     if (p_) {
-      cudaFree(p_);
+      if (async_) cudaFreeAsync(p_, st_);
+      else cudaFree(p_);
       if (ms_) ms_->cur -= bytes_;
     }
     p_ = nullptr;
     bytes_ = 0;
+    async_ = false;
   }
   template <typename U>
   U* as() const { return static_cast<U*>(p_); }
@@ -88,11 +121,23 @@ class DevBuf {
     std::swap(p_, o.p_);
     std::swap(bytes_, o.bytes_);
     std::swap(ms_, o.ms_);
+    std::swap(st_, o.st_);
+    std::swap(async_, o.async_);
   }
   void* p_ = nullptr;
   size_t bytes_ = 0;
   MemStats* ms_ = nullptr;
+  cudaStream_t st_ = nullptr;
+  bool async_ = false;
 };
+
+template <typename U>
+void upload_async(DevBuf& b, const std::vector<U>& h, MemStats* ms, cudaStream_t st) {
+  b.alloc_async(h.size() * sizeof(U), ms, st);
+  if (!h.empty())
+    HIF_CUDA_TRY(cudaMemcpyAsync(b.as<void>(), h.data(), h.size() * sizeof(U),
+                                 cudaMemcpyHostToDevice, st));
+}
 
 template <typename U>
 void upload(DevBuf& b, const std::vector<U>& h, MemStats* ms, cudaStream_t st) {
@@ -233,7 +278,7 @@ class Builder {
   void cell_step(CellPlan& cp, DevBuf& Kar, DevBuf& cdesc_d, std::vector<CellDesc>& cdesc,
                  DevBuf& lists_d);
   void skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& alive, DevBuf& Kar,
-                 DevBuf& cdesc_d);
+                 DevBuf& cdesc_d, SkelPlan* plan = nullptr);
   void gemv_list(GemvList& gl, std::vector<GemvOp>&& ops, int trans, int mat) {
     gl.h = std::move(ops);
     gl.trans = trans;
@@ -246,6 +291,12 @@ class Builder {
   Symbolic sym_;
   DevBuf flags_;
   int level_ = 0;
+  Trace tr_;
+  // next level's symbolic plan built ahead of time
+  bool have_spec_ = false;
+  CellPlan spec_cells_;
+  std::vector<int64_t> spec_mapOff_;
+  std::vector<int32_t> spec_map_;
 };
 
 template <typename T>
@@ -264,10 +315,22 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
   const int n = F_.n;
   const int64_t N = (int64_t)n * n * n;
   auto t0 = Clock::now();
+  {
+    // keep the stream-ordered pool's memory between levels instead of
+    // returning it to the driver at every synchronisation
+    int dev = 0;
+    cudaMemPool_t pool;
+    HIF_CUDA_TRY(cudaGetDevice(&dev));
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+  }
   F_.cpl.alloc(sizeof(double) * 3 * N, &F_.mem);
   F_.diag.alloc(sizeof(double) * N, &F_.mem);
   DevBuf bad;
-  bad.alloc(sizeof(int), &F_.mem);
+  bad.alloc_async(sizeof(int), &F_.mem, st_);
   HIF_CUDA_TRY(cudaMemsetAsync(bad.as<int>(), 0, sizeof(int), st_));
   stencil_coefficients(a_dev, b_dev, b_const, n, F_.cpl.template as<double>(), F_.diag.template as<double>(),
                        bad.as<int>(), st_);
@@ -275,7 +338,7 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
   HIF_CUDA_TRY(cudaMemcpyAsync(&hbad, bad.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st_));
   HIF_CUDA_TRY(cudaStreamSynchronize(st_));
   if (hbad) throw Error{HIF_ERR_INVALID_ARG, "a must be finite and > 0, b finite and >= 0"};
-  flags_.alloc(sizeof(int) * FLAG_COUNT, &F_.mem);
+  flags_.alloc_async(sizeof(int) * FLAG_COUNT, &F_.mem, st_);
   HIF_CUDA_TRY(cudaMemsetAsync(flags_.as<int>(), 0xff, sizeof(int) * FLAG_COUNT, st_));
 
   const int L = F_.L;
@@ -285,7 +348,19 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
     level_ = level;
     auto tl = Clock::now();
     CellPlan cp;
-    sym_.build_cells(level, cp);
+    tr_.mark(level, "start");
+    std::vector<int64_t> mapOff;
+    std::vector<int32_t> map;
+    if (have_spec_) {
+      cp = std::move(spec_cells_);
+      mapOff = std::move(spec_mapOff_);
+      map = std::move(spec_map_);
+      have_spec_ = false;
+    } else {
+      sym_.build_cells(level, cp);
+      if (level > 0) sym_.merge_maps(prev, cp, mapOff, map);
+    }
+    tr_.mark(level, "symbolic cells + merge maps");
     // frontal matrices of the level's cells
     std::vector<CellDesc> cdesc(cp.ncell);
     int64_t koff = 0;
@@ -295,8 +370,8 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
       koff += (int64_t)nc * nc;
     }
     DevBuf Kar, cdesc_d, lists_d;
-    Kar.alloc(sizeof(T) * std::max<int64_t>(1, koff), &F_.mem);
-    upload(cdesc_d, cdesc, &F_.mem, st_);
+    Kar.alloc_async(sizeof(T) * std::max<int64_t>(1, koff), &F_.mem, st_);
+    upload_async(cdesc_d, cdesc, &F_.mem, st_);
     upload(lists_d, cp.dofs, &F_.mem, st_);
     if (level == 0) {
       HIF_CUDA_TRY(cudaMemsetAsync(Kar.as<T>(), 0, sizeof(T) * koff, st_));
@@ -304,11 +379,8 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
       assemble_level0<T>(cdesc_d.as<CellDesc>(), cp.ncell, lists_d.as<int32_t>(), n, cp.s,
                          F_.cpl.template as<double>(), F_.diag.template as<double>(), Kar.as<T>(), maxbox, st_);
     } else {
-      std::vector<int64_t> mapOff;
-      std::vector<int32_t> map;
-      sym_.merge_maps(prev, cp, mapOff, map);
       DevBuf map_d, mdesc_d;
-      upload(map_d, map, &F_.mem, st_);
+      upload_async(map_d, map, &F_.mem, st_);
       std::vector<MergeDesc> md(cp.ncell);
       const int C = cp.C, Cc = prev.C;
       for (int c = 0; c < cp.ncell; ++c) {
@@ -321,14 +393,15 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
           md[c].child[q] = (cx < Cc && cy < Cc && cz < Cc) ? cx + Cc * (cy + Cc * cz) : -1;
         }
       }
-      upload(mdesc_d, md, &F_.mem, st_);
+      upload_async(mdesc_d, md, &F_.mem, st_);
       merge_children<T>(mdesc_d.as<MergeDesc>(), md.data(), cp.ncell, prevDesc.as<CellDesc>(),
                         map_d.as<int32_t>(), prevK.as<T>(), Kar.as<T>(), st_);
-      HIF_CUDA_TRY(cudaStreamSynchronize(st_));
       prevK.release();
       prevDesc.release();
     }
+    tr_.mark(level, "frontal matrices");
     cell_step(cp, Kar, cdesc_d, cdesc, lists_d);
+    tr_.mark(level, "cell elimination");
     F_.stats.fronts[level][0] = cp.ncell;
     if (level == L) {
       F_.stats.root_size = (int)cp.dofs.size();
@@ -343,7 +416,25 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
       for (int64_t t = cp.off[c]; t < cp.off[c] + cp.p[c]; ++t) alive[cp.dofs[t]] = 0;
     if (F_.eps > 0.0) {
       skel_step(cp, 1, alive, Kar, cdesc_d);
-      skel_step(cp, 2, alive, Kar, cdesc_d);
+      tr_.mark(level, "faces");
+      SkelPlan ep;
+      sym_.build_skel(cp, 2, alive, ep);
+      // the next level's cells, assuming the edges keep every DOF (they
+      // usually do), are planned on a host thread while the edges run;
+      // rebuilt at the next level if an edge lost DOFs
+      std::vector<int32_t> spec_act;
+      spec_act.reserve(cp.active.size());
+      for (int32_t g : cp.active)
+        if (alive[g]) spec_act.push_back(g);
+      const std::vector<uint8_t> alive_faces = alive;
+      auto spec = std::async(std::launch::async, [&, act = std::move(spec_act)]() {
+        sym_.build_cells_from(level + 1, act, spec_cells_);
+        sym_.merge_maps(cp, spec_cells_, spec_mapOff_, spec_map_);
+      });
+      skel_step(cp, 2, alive, Kar, cdesc_d, &ep);
+      spec.get();
+      have_spec_ = (alive == alive_faces);
+      tr_.mark(level, "edges");
     }
     check_flags("level factorization");
     std::vector<int32_t> next;
@@ -387,7 +478,7 @@ void Builder<T>::cell_step(CellPlan& cp, DevBuf& Kar, DevBuf& cdesc_d, std::vect
   s.panels.alloc(sizeof(T) * std::max<int64_t>(1, pcur), &F_.mem);
   s.entries = pcur;
   DevBuf fr_d;
-  upload(fr_d, fr, &F_.mem, st_);
+  upload_async(fr_d, fr, &F_.mem, st_);
   partial_cholesky<T>(fr_d.as<DFront>(), fr.data(), (int)fr.size(), Kar.as<T>(), s.panels.as<T>(),
                       flags_.as<int>(), st_);
   // apply stage: gather the whole frontal list of every cell
@@ -454,15 +545,16 @@ void Builder<T>::cell_step(CellPlan& cp, DevBuf& Kar, DevBuf& cdesc_d, std::vect
     upload(s.acc_src, src, &F_.mem, st_);
   }
   F_.work_stride = std::max(F_.work_stride, 2 * s.nidx);
-  HIF_CUDA_TRY(cudaStreamSynchronize(st_));
   F_.stages.push_back(std::move(s));
 }
 
 template <typename T>
 void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& alive, DevBuf& Kar,
-                           DevBuf& cdesc_d) {
-  SkelPlan sp;
-  sym_.build_skel(cp, kind, alive, sp);
+                           DevBuf& cdesc_d, SkelPlan* plan) {
+  SkelPlan own;
+  if (!plan) sym_.build_skel(cp, kind, alive, own);
+  SkelPlan& sp = plan ? *plan : own;
+  tr_.mark(level_, kind == 1 ? " symbolic faces" : " symbolic edges");
   const int nf = sp.nfront;
   if (nf == 0) return;
   const int ncp = sp.ncellPer;
@@ -483,27 +575,30 @@ void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& a
     toff += (int64_t)(d.nF / 2) * (d.nF - d.nF / 2);
     F_.stats.flops += 2.0 * d.nR * (double)d.nF * d.nF;
   }
-  DevBuf rowpos_d, sd_d, G, perm_d, scratch, steps, tm;
-  upload(rowpos_d, sp.rowPos, &F_.mem, st_);
-  upload(sd_d, sd, &F_.mem, st_);
-  G.alloc(sizeof(T) * std::max<int64_t>(1, goff), &F_.mem);
-  perm_d.alloc(sizeof(int32_t) * poff, &F_.mem);
-  scratch.alloc(sizeof(double) * 2 * poff, &F_.mem);
-  steps.alloc(sizeof(int32_t) * poff, &F_.mem);
+  DevBuf rowpos_d, sd_d, G, perm_d, scratch, steps, fsc, tm;
+  upload_async(rowpos_d, sp.rowPos, &F_.mem, st_);
+  upload_async(sd_d, sd, &F_.mem, st_);
+  G.alloc_async(sizeof(T) * std::max<int64_t>(1, goff), &F_.mem, st_);
+  perm_d.alloc_async(sizeof(int32_t) * poff, &F_.mem, st_);
+  scratch.alloc_async(sizeof(double) * 2 * poff, &F_.mem, st_);
+  steps.alloc_async(sizeof(int32_t) * poff, &F_.mem, st_);
+  fsc.alloc_async(sizeof(T) * id_fscratch_elems(poff), &F_.mem, st_);
   tm.alloc(sizeof(T) * std::max<int64_t>(1, toff), &F_.mem);
   skel_gather<T>(sd_d.as<SkelDesc>(), sd.data(), nf, ncp, rowpos_d.as<int32_t>(),
                  cdesc_d.as<CellDesc>(), Kar.as<T>(), G.as<T>(), st_);
   interpolative_decomposition<T>(sd_d.as<SkelDesc>(), sd.data(), nf, G.as<T>(),
                                  perm_d.as<int32_t>(), tm.as<T>(), scratch.as<double>(),
-                                 steps.as<int32_t>(), F_.eps, st_);
+                                 steps.as<int32_t>(), fsc.as<T>(), F_.eps, st_);
   std::vector<int32_t> perm(poff);
   HIF_CUDA_TRY(cudaMemcpyAsync(sd.data(), sd_d.as<void>(), sizeof(SkelDesc) * nf,
                                cudaMemcpyDeviceToHost, st_));
   HIF_CUDA_TRY(cudaMemcpyAsync(perm.data(), perm_d.as<void>(), sizeof(int32_t) * poff,
                                cudaMemcpyDeviceToHost, st_));
   HIF_CUDA_TRY(cudaStreamSynchronize(st_));
+  tr_.mark(level_, " gather + ID");
   scratch.release();
   steps.release();
+  fsc.release();
   if (prof_enabled()) {
     // unblocked CPQR: each of the k steps reads and writes the trailing
     // (nR - i) x (nF - i - 1) block once and spends 4 flops per entry on it
@@ -541,14 +636,14 @@ void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& a
     F_.stats.flops += 4.0 * d.nF * (double)d.k * p + std::pow((double)p, 3) / 3.0 +
                       (double)p * p * d.k + (double)d.k * d.k * p;
   }
-  upload(sd_d, sd, &F_.mem, st_);
+  upload_async(sd_d, sd, &F_.mem, st_);
   DevBuf Z;
-  Z.alloc(sizeof(T) * std::max<int64_t>(1, zoff), &F_.mem);
+  Z.alloc_async(sizeof(T) * std::max<int64_t>(1, zoff), &F_.mem, st_);
   // permute only the active fronts: build a compact descriptor list
   std::vector<SkelDesc> sda;
   for (int f : act) sda.push_back(sd[f]);
   DevBuf sda_d;
-  upload(sda_d, sda, &F_.mem, st_);
+  upload_async(sda_d, sda, &F_.mem, st_);
   skel_permute<T>(sda_d.as<SkelDesc>(), sda.data(), (int)sda.size(), perm_d.as<int32_t>(),
                   G.as<T>(), Z.as<T>(), st_);
   // B_{F^F~} = A_{F^F~} - A_{F^F^} T ;  B_{F~F~} = A_{F~F~} - A_{F~F^} T - T^T B_{F^F~}
@@ -561,9 +656,9 @@ void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& a
     g3.push_back(GemmOp{d.Tm, d.Z + p, d.Z, p, p, k, k, nF, nF, 1, 0, -1.f, 1.f});
   }
   DevBuf g1d, g2d, g3d;
-  upload(g1d, g1, &F_.mem, st_);
-  upload(g2d, g2, &F_.mem, st_);
-  upload(g3d, g3, &F_.mem, st_);
+  upload_async(g1d, g1, &F_.mem, st_);
+  upload_async(g2d, g2, &F_.mem, st_);
+  upload_async(g3d, g3, &F_.mem, st_);
   gemm_batched<T>(g1d.as<GemmOp>(), g1.data(), (int)g1.size(), Z.as<T>(), tm.as<T>(), Z.as<T>(), st_);
   gemm_batched<T>(g2d.as<GemmOp>(), g2.data(), (int)g2.size(), Z.as<T>(), tm.as<T>(), Z.as<T>(), st_);
   gemm_batched<T>(g3d.as<GemmOp>(), g3.data(), (int)g3.size(), tm.as<T>(), Z.as<T>(), Z.as<T>(), st_);
@@ -575,7 +670,7 @@ void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& a
   std::vector<DFront> frs = fr;
   std::stable_sort(frs.begin(), frs.end(), [](const DFront& x, const DFront& y) { return x.p > y.p; });
   DevBuf fr_d;
-  upload(fr_d, frs, &F_.mem, st_);
+  upload_async(fr_d, frs, &F_.mem, st_);
   partial_cholesky<T>(fr_d.as<DFront>(), frs.data(), (int)frs.size(), Z.as<T>(), s.panels.as<T>(),
                       flags_.as<int>(), st_);
   skel_writeback<T>(sda_d.as<SkelDesc>(), sda.data(), (int)sda.size(), ncp, rowpos_d.as<int32_t>(),
@@ -629,7 +724,6 @@ void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& a
   upload(s.set_g, sg, &F_.mem, st_);
   upload(s.set_p, spos, &F_.mem, st_);
   F_.work_stride = std::max(F_.work_stride, 2 * s.nidx);
-  HIF_CUDA_TRY(cudaStreamSynchronize(st_));
   F_.stages.push_back(std::move(s));
 }
 

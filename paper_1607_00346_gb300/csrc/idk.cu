@@ -3,19 +3,30 @@
 // T_F = R11^{-1} R12.
 //
 // One thread-block cluster per front (1 to 16 CTAs, chosen from the front's
-// size).  Column j of the gather buffer belongs to CTA j % CS of the cluster
-// and never moves: the pivot order is kept as a permutation.  Each step
-//   1. every CTA proposes the largest remaining column norm among its columns;
-//      the proposals meet in distributed shared memory and every CTA picks the
-//      same winner (largest norm, lowest column index on ties);
-//   2. the owner of the pivot column builds the Householder reflector in place;
-//   3. every CTA applies it to its own remaining columns and downdates their
-//      norms.
+// size and the batch).  Column j of the gather buffer belongs to CTA j % CS of
+// the cluster and never moves: the pivot order is kept as a permutation.
+//
+// Blocked with deferred updates (the xLAQPS scheme of LAPACK's pivoted QR):
+// within a block of NBK steps the remaining columns keep their block-start
+// values; with V the block's reflectors and F(c,:) = tau-weighted products of
+// column c with them, the current column is a_c - V F(c,:)^T.  Each step
+//   1. every CTA proposes the largest remaining (downdated) column norm among
+//      its columns; the proposals meet in distributed shared memory and every
+//      CTA picks the same winner (largest norm, lowest column index on ties);
+//   2. the owner of the pivot column brings it up to date, builds the
+//      Householder reflector in place and the products g_l = v_l^T v_j;
+//   3. every CTA computes F(c, j) = tau_j (v_j^T a_c - sum_l g_l F(c,l)) for
+//      its remaining columns (one read of each column), updates row i of them
+//      (their R entries) and downdates their norms.
+// After the block, each CTA applies a_c -= V F(c,:)^T below the block to its
+// columns (one read and one write per column).  So each step reads the
+// trailing columns once instead of reading them twice and writing them.
+//
 // Reflectors and products run in the factor precision T.  Column norms are
 // kept in double and downdated after every step (|a_j|^2 -= R_ij^2); when the
-// downdate has lost most of the value the norm is recomputed from the column
-// (the LAPACK xGEQP3 safeguard).  Rows are never permuted, so R_{l,j} sits in
-// row l of column j.
+// downdate has lost most of the value the norm is recomputed from the current
+// column (the LAPACK xGEQP3 safeguard).  Rows are never permuted, so R_{l,j}
+// sits in row l of column j.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -32,8 +43,9 @@ namespace {
 
 constexpr int ID_THREADS = 512;
 constexpr int ID_WARPS = ID_THREADS / 32;
-
-constexpr int UNR = 8;   // independent loads in flight per lane in the column passes
+constexpr int NBK = 16;   // steps per block of deferred updates
+constexpr int RC = 128;   // rows of V staged in shared memory by the block update
+constexpr int UNR = 8;    // independent loads in flight per lane in the column passes
 
 // sum_{r in [r0, r1)} a[r] b[r] over one warp (result in every lane)
 template <typename T>
@@ -41,12 +53,30 @@ __device__ __forceinline__ T warp_dot(const T* __restrict__ a, const T* __restri
                                       int r1, int lane) {
   T acc[4] = {T(0), T(0), T(0), T(0)};
   int r = r0 + lane;
-  for (; r + 32 * (UNR - 1) < r1; r += 32 * UNR) {
+  if (r + 32 * (UNR - 1) < r1) {
+    // two chunks in flight: the next chunk's loads are issued before this
+    // chunk's products wait on theirs
     T x[UNR], y[UNR];
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
       x[u] = a[r + 32 * u];
       y[u] = b[r + 32 * u];
+    }
+    r += 32 * UNR;
+    for (; r + 32 * (UNR - 1) < r1; r += 32 * UNR) {
+      T xn[UNR], yn[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        xn[u] = a[r + 32 * u];
+        yn[u] = b[r + 32 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) acc[u & 3] = fma(x[u], y[u], acc[u & 3]);
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        x[u] = xn[u];
+        y[u] = yn[u];
+      }
     }
 #pragma unroll
     for (int u = 0; u < UNR; ++u) acc[u & 3] = fma(x[u], y[u], acc[u & 3]);
@@ -55,24 +85,6 @@ __device__ __forceinline__ T warp_dot(const T* __restrict__ a, const T* __restri
   T s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
-}
-
-// b[r] -= t a[r] for r in [r0, r1), one warp
-template <typename T>
-__device__ __forceinline__ void warp_axpy(T t, const T* __restrict__ a, T* __restrict__ b, int r0,
-                                          int r1, int lane) {
-  int r = r0 + lane;
-  for (; r + 32 * (UNR - 1) < r1; r += 32 * UNR) {
-    T x[UNR], y[UNR];
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      x[u] = a[r + 32 * u];
-      y[u] = b[r + 32 * u];
-    }
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) b[r + 32 * u] = fma(-t, x[u], y[u]);
-  }
-  for (; r < r1; r += 32) b[r] = fma(-t, a[r], b[r]);
 }
 
 // sum of squares (double) of a[r0:r1], one warp
@@ -94,9 +106,10 @@ __device__ __forceinline__ double warp_sumsq(const T* __restrict__ a, int r0, in
 }
 
 template <typename T>
-__global__ void __launch_bounds__(ID_THREADS) k_cpqr(SkelDesc* fr, const int* __restrict__ list,
+__global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int* __restrict__ list,
                                                      T* Gar, int32_t* permAr, T* Far,
-                                                     double* scratch, int32_t* stepAr, double eps) {
+                                                     double* scratch, int32_t* stepAr, T* Fsc,
+                                                     double eps) {
   cg::cluster_group cl = cg::this_cluster();
   const int CS = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -109,16 +122,23 @@ __global__ void __launch_bounds__(ID_THREADS) k_cpqr(SkelDesc* fr, const int* __
   int32_t* stepOf = stepAr + f.perm;
   double* nrm = scratch + 2 * f.perm;
   double* ref = nrm + nF;
+  T* Fm = Fsc + f.perm * NBK;       // F(c, l) at Fm[c*NBK + l]
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   __shared__ double s_val[ID_WARPS];
   __shared__ int s_idx[ID_WARPS];
   __shared__ double s_cand_val;
   __shared__ int s_cand_idx;
-  __shared__ double s_tau, s_v0;
+  __shared__ double s_tau_own, s_v0_own;     // written by the pivot's owner
+  __shared__ T s_g_own[NBK];                 // g_l = v_l^T v_j, written by the owner
+  __shared__ T s_g[NBK];
+  __shared__ T s_vrow[NBK];                  // V[i, l] of the current step
+  __shared__ int s_pl[NBK];                  // pivot columns of the block
+  __shared__ T s_v0[NBK], s_tau[NBK];
   __shared__ int s_piv, s_stop;
   __shared__ double s_r11;
+  __shared__ T s_V[RC][NBK + 1];
+  __shared__ T s_fp[NBK];
 
-  // initial norms of my columns
   for (int c = rank + CS * warp; c < nF; c += CS * ID_WARPS) {
     const double s = warp_sumsq(M + (int64_t)c * ld, 0, m, lane);
     if (lane == 0) {
@@ -130,117 +150,213 @@ __global__ void __launch_bounds__(ID_THREADS) k_cpqr(SkelDesc* fr, const int* __
   __syncthreads();
   const int kmax = min(m, nF);
   int k = kmax;
-  for (int i = 0; i < kmax; ++i) {
-    // 1. local proposal
-    double bv = -1.0;
-    int bi = nF;
-    for (int c = rank + CS * tid; c < nF; c += CS * ID_THREADS) {
-      if (stepOf[c] >= 0) continue;
-      const double v = nrm[c];
-      if (v > bv || (v == bv && c < bi)) {
-        bv = v;
-        bi = c;
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > bv || (ov == bv && oi < bi)) {
-        bv = ov;
-        bi = oi;
-      }
-    }
-    if (lane == 0) {
-      s_val[warp] = bv;
-      s_idx[warp] = bi;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double v = s_val[0];
-      int ix = s_idx[0];
-      for (int w = 1; w < ID_WARPS; ++w)
-        if (s_val[w] > v || (s_val[w] == v && s_idx[w] < ix)) {
-          v = s_val[w];
-          ix = s_idx[w];
-        }
-      s_cand_val = v;
-      s_cand_idx = ix;
-    }
-    cl.sync();
-    // 2. the cluster-wide winner (same in every CTA)
-    if (tid == 0) {
-      double v = -1.0;
-      int ix = nF;
-      for (int q = 0; q < CS; ++q) {
-        const double ov = *cl.map_shared_rank(&s_cand_val, q);
-        const int oi = *cl.map_shared_rank(&s_cand_idx, q);
-        if (ov > v || (ov == v && oi < ix)) {
-          v = ov;
-          ix = oi;
+  int i = 0;
+  bool stopped = false;
+  while (i < kmax && !stopped) {
+    int jdone = 0;
+    for (int j = 0; j < NBK && i < kmax; ++j) {
+      // 1. proposals
+      double bv = -1.0;
+      int bi = nF;
+      for (int c = rank + CS * tid; c < nF; c += CS * ID_THREADS) {
+        if (stepOf[c] >= 0) continue;
+        const double v = nrm[c];
+        if (v > bv || (v == bv && c < bi)) {
+          bv = v;
+          bi = c;
         }
       }
-      const double nv = sqrt(fmax(v, 0.0));
-      if (i == 0) s_r11 = nv;
-      s_stop = (ix >= nF) || ((i == 0) ? (nv == 0.0) : !(nv > eps * s_r11));
-      s_piv = ix;
-    }
-    __syncthreads();
-    if (s_stop) {
-      k = i;
-      break;
-    }
-    const int piv = s_piv;
-    const int owner = piv % CS;
-    T* cp = M + (int64_t)piv * ld;
-    if (owner == rank) {
-      double s = 0.0;
-      for (int r = i + 1 + tid; r < m; r += ID_THREADS) {
-        const double v = (double)cp[r];
-        s += v * v;
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) {
+          bv = ov;
+          bi = oi;
+        }
       }
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) s_val[warp] = s;
+      if (lane == 0) {
+        s_val[warp] = bv;
+        s_idx[warp] = bi;
+      }
       __syncthreads();
       if (tid == 0) {
-        double tail = 0.0;
-        for (int w = 0; w < ID_WARPS; ++w) tail += s_val[w];
-        const double x0 = (double)cp[i];
-        const double nx = sqrt(x0 * x0 + tail);
-        const double alpha = x0 >= 0.0 ? -nx : nx;
-        const double v0 = x0 - alpha;
-        const double vtv = v0 * v0 + tail;
-        s_tau = vtv > 0.0 ? 2.0 / vtv : 0.0;
-        s_v0 = v0;
-        cp[i] = (T)alpha;    // R_ii; v0 lives in shared memory
-        pv[i] = piv;
-        stepOf[piv] = i;
+        double v = s_val[0];
+        int ix = s_idx[0];
+        for (int w = 1; w < ID_WARPS; ++w)
+          if (s_val[w] > v || (s_val[w] == v && s_idx[w] < ix)) {
+            v = s_val[w];
+            ix = s_idx[w];
+          }
+        s_cand_val = v;
+        s_cand_idx = ix;
+      }
+      cl.sync();
+      if (warp == 0) {
+        // lane q reads CTA q's proposal; a shuffle reduction picks the winner
+        double v = -1.0;
+        int ix = nF;
+        if (lane < CS) {
+          v = *cl.map_shared_rank(&s_cand_val, lane);
+          ix = *cl.map_shared_rank(&s_cand_idx, lane);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
+          if (ov > v || (ov == v && oi < ix)) {
+            v = ov;
+            ix = oi;
+          }
+        }
+        if (lane == 0) {
+          const double nv = sqrt(fmax(v, 0.0));
+          if (i == 0) s_r11 = nv;
+          s_stop = (ix >= nF) || ((i == 0) ? (nv == 0.0) : !(nv > eps * s_r11));
+          s_piv = ix;
+        }
+      }
+      __syncthreads();
+      if (s_stop) {
+        k = i;
+        stopped = true;
+        break;
+      }
+      const int piv = s_piv;
+      const int owner = piv % CS;
+      T* cp = M + (int64_t)piv * ld;
+      // 2. the owner: bring the pivot column up to date, build the reflector
+      if (owner == rank) {
+        if (j > 0) {
+          if (tid < NBK) s_fp[tid] = tid < j ? Fm[(int64_t)piv * NBK + tid] : T(0);
+          __syncthreads();
+          for (int r = i + tid; r < m; r += ID_THREADS) {
+            T vv[NBK];
+#pragma unroll
+            for (int l = 0; l < NBK; ++l) vv[l] = l < j ? M[r + (int64_t)s_pl[l] * ld] : T(0);
+            T a = cp[r];
+#pragma unroll
+            for (int l = 0; l < NBK; ++l) a = fma(-vv[l], s_fp[l], a);
+            cp[r] = a;
+          }
+          __syncthreads();
+        }
+        double s = 0.0;
+        for (int r = i + 1 + tid; r < m; r += ID_THREADS) {
+          const double v = (double)cp[r];
+          s += v * v;
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) s_val[warp] = s;
+        __syncthreads();
+        if (tid == 0) {
+          double tail = 0.0;
+          for (int w = 0; w < ID_WARPS; ++w) tail += s_val[w];
+          const double x0 = (double)cp[i];
+          const double nx = sqrt(x0 * x0 + tail);
+          const double alpha = x0 >= 0.0 ? -nx : nx;
+          const double v0 = x0 - alpha;
+          const double vtv = v0 * v0 + tail;
+          s_tau_own = vtv > 0.0 ? 2.0 / vtv : 0.0;
+          s_v0_own = v0;
+          cp[i] = (T)alpha;    // R_ii; v0 lives in shared memory
+          pv[i] = piv;
+          stepOf[piv] = i;
+        }
+        __syncthreads();
+        // g_l = v_l^T v_j over rows i..m-1 (v_l is nonzero there, v_j starts at row i)
+        const T v0 = (T)s_v0_own;
+        for (int l = warp; l < j; l += ID_WARPS) {
+          const T* vl = M + (int64_t)s_pl[l] * ld;
+          T g = warp_dot(vl, cp, i + 1, m, lane);
+          g = fma(vl[i], v0, g);
+          if (lane == 0) s_g_own[l] = g;
+        }
+      }
+      cl.sync();
+      // 3. every CTA: the step's reflector scalars, then its own columns
+      if (tid == 0) {
+        s_pl[j] = piv;
+        s_v0[j] = (T)*cl.map_shared_rank(&s_v0_own, owner);
+        s_tau[j] = (T)*cl.map_shared_rank(&s_tau_own, owner);
+      }
+      if (tid < j) {
+        s_g[tid] = *cl.map_shared_rank(&s_g_own[tid], owner);
+        s_vrow[tid] = M[i + (int64_t)s_pl[tid] * ld];
+      }
+      __syncthreads();
+      if (tid == 0) s_vrow[j] = s_v0[j];
+      __syncthreads();
+      const T v0 = s_v0[j], tau = s_tau[j];
+      for (int c = rank + CS * warp; c < nF; c += CS * ID_WARPS) {
+        if (stepOf[c] >= 0) continue;
+        T* cc = M + (int64_t)c * ld;
+        T* Fc = Fm + (int64_t)c * NBK;
+        T fl[NBK];
+#pragma unroll
+        for (int l = 0; l < NBK; ++l) fl[l] = l < j ? Fc[l] : T(0);
+        const T aci = cc[i];
+        T dot = warp_dot(cp, cc, i + 1, m, lane);
+        dot = fma(v0, aci, dot);
+        T corr = T(0), rv = aci;
+#pragma unroll
+        for (int l = 0; l < NBK; ++l) {
+          if (l < j) {
+            corr = fma(s_g[l], fl[l], corr);
+            rv = fma(-s_vrow[l], fl[l], rv);
+          }
+        }
+        const T fcj = tau * (dot - corr);
+        rv = fma(-s_vrow[j], fcj, rv);
+        __syncwarp();
+        if (lane == 0) {
+          Fc[j] = fcj;
+          cc[i] = rv;
+        }
+        // downdate |a_c|^2 by R_ic^2 in double; recompute when mostly cancelled
+        double nv = nrm[c] - (double)rv * (double)rv;
+        if (nv <= 1e-2 * ref[c]) {
+          double s = 0.0;
+          for (int r = i + 1 + lane; r < m; r += 32) {
+            T a = cc[r];
+            for (int l = 0; l < j; ++l) a = fma(-M[r + (int64_t)s_pl[l] * ld], fl[l], a);
+            a = fma(-cp[r], fcj, a);
+            s += (double)a * (double)a;
+          }
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          nv = s;
+          if (lane == 0) ref[c] = s;
+        }
+        if (lane == 0) nrm[c] = fmax(nv, 0.0);
+      }
+      __syncthreads();
+      ++i;
+      jdone = j + 1;
+    }
+    // block update of my remaining columns below the block: a_c -= V F(c,:)^T
+    if (!stopped && i < kmax && jdone > 0) {
+      for (int r0 = i; r0 < m; r0 += RC) {
+        const int rn = min(RC, m - r0);
+        for (int e = tid; e < RC * NBK; e += ID_THREADS) {
+          const int rr = e % RC, l = e / RC;
+          s_V[rr][l] = (rr < rn && l < jdone) ? M[r0 + rr + (int64_t)s_pl[l] * ld] : T(0);
+        }
+        __syncthreads();
+        for (int c = rank + CS * warp; c < nF; c += CS * ID_WARPS) {
+          if (stepOf[c] >= 0) continue;
+          T* cc = M + (int64_t)c * ld;
+          const T* Fc = Fm + (int64_t)c * NBK;
+          T fl[NBK];
+#pragma unroll
+          for (int l = 0; l < NBK; ++l) fl[l] = l < jdone ? Fc[l] : T(0);
+          for (int rr = lane; rr < rn; rr += 32) {
+            T a = cc[r0 + rr];
+#pragma unroll
+            for (int l = 0; l < NBK; ++l) a = fma(-s_V[rr][l], fl[l], a);
+            cc[r0 + rr] = a;
+          }
+        }
+        __syncthreads();
       }
     }
-    cl.sync();
-    // 3. apply the reflector v = [v0; cp[i+1:m]] to my remaining columns
-    const double tau_d = *cl.map_shared_rank(&s_tau, owner);
-    const T v0 = (T)*cl.map_shared_rank(&s_v0, owner);
-    const T tau = (T)tau_d;
-    for (int j = rank + CS * warp; j < nF; j += CS * ID_WARPS) {
-      if (stepOf[j] >= 0) continue;
-      T* cj = M + (int64_t)j * ld;
-      T w = warp_dot(cp, cj, i + 1, m, lane);
-      w = fma(v0, cj[i], w);
-      const T tw = tau * w;
-      warp_axpy(tw, cp, cj, i + 1, m, lane);
-      __syncwarp();
-      if (lane == 0) cj[i] = fma(-tw, v0, cj[i]);
-      __syncwarp();
-      // downdate |a_j|^2 by R_ij^2 in double; recompute when mostly cancelled
-      const double rij = (double)cj[i];
-      double nv = nrm[j] - rij * rij;
-      if (nv <= 1e-2 * ref[j]) {
-        nv = warp_sumsq(cj, i + 1, m, lane);
-        if (lane == 0) ref[j] = nv;
-      }
-      if (lane == 0) nrm[j] = fmax(nv, 0.0);
-    }
-    __syncthreads();
   }
   // redundant columns, in increasing column order, follow the pivots in pv
   cl.sync();
@@ -272,37 +388,55 @@ __global__ void __launch_bounds__(ID_THREADS) k_cpqr(SkelDesc* fr, const int* __
 
 }  // namespace
 
+size_t id_fscratch_elems(int64_t total_front_dofs) { return (size_t)total_front_dofs * NBK; }
+
 template <typename T>
 void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* Garena,
                                  int32_t* perm, T* Farena, double* scratch, int32_t* stepAr,
-                                 double eps, cudaStream_t st) {
+                                 T* Fscratch, double eps, cudaStream_t st) {
   if (nf == 0) return;
   int nsm = 0, dev = 0;
   HIF_CUDA_TRY(cudaGetDevice(&dev));
   HIF_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  // cluster size per front from its work per step (nF x nR), so that the
-  // large fronts of the upper levels spread over up to 16 SMs each
-  std::vector<std::vector<int>> bucket(5);
-  const int sizes[5] = {1, 2, 4, 8, 16};
+  // cluster size: small fronts get one CTA; large fronts (work per step
+  // nF x nR above ~1e6) spread their columns over as many SMs as the batch
+  // leaves free (two CTAs per SM), up to 16, so that one launch fills the GPU
+  std::vector<std::vector<int>> bucket(17);
+  int nbig = 0;
+  for (int f = 0; f < nf; ++f)
+    if ((double)h_f[f].nF * (h_f[f].nF + h_f[f].nR) > 1.0e6) ++nbig;
+  const int cs_big = std::max(1, std::min(16, 2 * nsm / std::max(1, nbig)));
   for (int f = 0; f < nf; ++f) {
     const double work = (double)h_f[f].nF * (h_f[f].nF + h_f[f].nR);
-    int b = 0;
-    if (work > 2.0e5) b = 1;
-    if (work > 1.0e6) b = 2;
-    if (work > 4.0e6) b = 3;
-    if (work > 1.6e7) b = 4;
-    // do not spread a few fronts wider than the GPU
-    while (b > 0 && (int64_t)nf * sizes[b] > 2 * nsm) --b;
-    bucket[b].push_back(f);
+    int cs = work > 1.0e6 ? cs_big : 1;
+    cs = std::min(cs, std::max(1, h_f[f].nF / 8));   // at least 8 columns per CTA
+    bucket[cs].push_back(f);
   }
   static bool attr_set[2] = {false, false};
   if (!attr_set[sizeof(T) == 8]) {
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_cpqr<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     attr_set[sizeof(T) == 8] = true;
   }
-  for (int b = 0; b < 5; ++b) {
+  for (int b = 1; b <= 16; ++b) {
     if (bucket[b].empty()) continue;
-    const int CS = sizes[b];
+    int CS = b;
+    // the largest cluster of at most b CTAs that the GPU can place
+    while (CS > 1) {
+      cudaLaunchConfig_t q = {};
+      q.gridDim = dim3((unsigned)CS);
+      q.blockDim = dim3(ID_THREADS);
+      cudaLaunchAttribute qa[1];
+      qa[0].id = cudaLaunchAttributeClusterDimension;
+      qa[0].val.clusterDim.x = CS;
+      qa[0].val.clusterDim.y = 1;
+      qa[0].val.clusterDim.z = 1;
+      q.attrs = qa;
+      q.numAttrs = 1;
+      int ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, k_cpqr<T>, &q) == cudaSuccess && ncl > 0) break;
+      cudaGetLastError();
+      --CS;
+    }
     int* d_list = nullptr;
     HIF_CUDA_TRY(cudaMallocAsync(&d_list, sizeof(int) * bucket[b].size(), st));
     HIF_CUDA_TRY(cudaMemcpyAsync(d_list, bucket[b].data(), sizeof(int) * bucket[b].size(),
@@ -322,7 +456,7 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
     {
       ProfScope ps("id_cpqr", st);
       HIF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_cpqr<T>, d_f, (const int*)d_list, Garena, perm,
-                                      Farena, scratch, stepAr, eps));
+                                      Farena, scratch, stepAr, Fscratch, eps));
       HIF_CHECK_LAUNCH();
     }
     HIF_CUDA_TRY(cudaFreeAsync(d_list, st));
@@ -330,9 +464,10 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
 }
 
 template void interpolative_decomposition<float>(SkelDesc*, const SkelDesc*, int, float*, int32_t*,
-                                                 float*, double*, int32_t*, double, cudaStream_t);
+                                                 float*, double*, int32_t*, float*, double,
+                                                 cudaStream_t);
 template void interpolative_decomposition<double>(SkelDesc*, const SkelDesc*, int, double*,
-                                                  int32_t*, double*, double*, int32_t*, double,
-                                                  cudaStream_t);
+                                                  int32_t*, double*, double*, int32_t*, double*,
+                                                  double, cudaStream_t);
 
 }  // namespace hif

@@ -3,7 +3,6 @@
 
 #include <algorithm>
 #include <thread>
-#include <unordered_map>
 
 namespace hif {
 
@@ -64,7 +63,38 @@ int32_t Symbolic::pos_in_cell(const CellPlan& cp, int32_t g, int cx, int cy, int
   return cp.posB[(int64_t)sl * 8 + q];
 }
 
-void Symbolic::build_cells(int level, CellPlan& cp) const {
+void Symbolic::build_cells(int level, CellPlan& cp) const { build_cells_from(level, active_, cp); }
+
+void Symbolic::filter_rows(SkelPlan& sp, const std::vector<uint8_t>& alive) const {
+  const int ncp = sp.ncellPer;
+  const int nf = sp.nfront;
+  std::vector<int64_t> kept(nf, 0);
+  parallel_for(nf, [&](int64_t f) {
+    int64_t k = 0;
+    for (int64_t r = sp.rowOff[f]; r < sp.rowOff[f + 1]; ++r)
+      if (r < sp.rowOff[f] + sp.nF[f] || alive[sp.rowDof[r]]) ++k;
+    kept[f] = k;
+  });
+  std::vector<int64_t> off(nf + 1, 0);
+  for (int f = 0; f < nf; ++f) off[f + 1] = off[f] + kept[f];
+  std::vector<int32_t> dof(off[nf]);
+  std::vector<int32_t> pos(off[nf] * ncp);
+  parallel_for(nf, [&](int64_t f) {
+    int64_t o = off[f];
+    for (int64_t r = sp.rowOff[f]; r < sp.rowOff[f + 1]; ++r) {
+      if (!(r < sp.rowOff[f] + sp.nF[f] || alive[sp.rowDof[r]])) continue;
+      dof[o] = sp.rowDof[r];
+      for (int i = 0; i < ncp; ++i) pos[o * ncp + i] = sp.rowPos[r * ncp + i];
+      ++o;
+    }
+    sp.nR[f] = (int32_t)(kept[f] - sp.nF[f]);
+  });
+  sp.rowOff.swap(off);
+  sp.rowDof.swap(dof);
+  sp.rowPos.swap(pos);
+}
+
+void Symbolic::build_cells_from(int level, const std::vector<int32_t>& active, CellPlan& cp) const {
   const int n = n_;
   const int s = m_ << level;
   const int C = n / s;
@@ -73,7 +103,7 @@ void Symbolic::build_cells(int level, CellPlan& cp) const {
   cp.s = s;
   cp.C = C;
   cp.ncell = C * C * C;
-  cp.active = active_;
+  cp.active = active;
   const int64_t na = (int64_t)cp.active.size();
   cp.slot.assign(N, -1);
   cp.packed.resize(na);
@@ -168,28 +198,34 @@ void Symbolic::build_skel(const CellPlan& cp, int kind, const std::vector<uint8_
     int64_t c0 = pk & 0xffff, c1 = (pk >> 16) & 0xffff, c2 = (pk >> 32) & 0xffff;
     return (pk >> 48) * (int64_t)C * C * C + c0 + C * (c1 + C * c2);
   };
-  std::unordered_map<int64_t, int32_t> fid;
+  // group id -> front number through a dense table (8 separator masks x C^3
+  // low cells); fronts are numbered in order of their lowest global index
+  const int64_t C3 = (int64_t)C * C * C;
+  std::vector<int32_t> fid(8 * C3, -1);
   std::vector<int64_t> keys;
-  std::vector<std::vector<int32_t>> members;
+  std::vector<int32_t> fcount;
+  std::vector<int32_t> front_of(na, -1);
   for (int64_t i = 0; i < na; ++i) {
     int32_t g = cp.active[i];
     if (!alive[g]) continue;
     int64_t pk = cp.packed[i];
     if (popc3((int)(pk >> 48)) != kind) continue;
-    int64_t k = gkey(pk);
-    auto it = fid.find(k);
-    int32_t f;
-    if (it == fid.end()) {
+    const int64_t k = gkey(pk);
+    int32_t f = fid[k];
+    if (f < 0) {
       f = (int32_t)keys.size();
-      fid.emplace(k, f);
+      fid[k] = f;
       keys.push_back(k);
-      members.emplace_back();
-    } else {
-      f = it->second;
+      fcount.push_back(0);
     }
-    members[f].push_back(g);
+    fcount[f]++;
+    front_of[i] = f;
   }
   const int nf = (int)keys.size();
+  std::vector<std::vector<int32_t>> members(nf);
+  for (int f = 0; f < nf; ++f) members[f].reserve(fcount[f]);
+  for (int64_t i = 0; i < na; ++i)
+    if (front_of[i] >= 0) members[front_of[i]].push_back(cp.active[i]);
   sp.nfront = nf;
   sp.cells.assign((size_t)nf * ncp, -1);
   sp.nF.assign(nf, 0);

@@ -64,6 +64,11 @@ class Symbolic {
   void build_skel(const CellPlan& cp, int kind, const std::vector<uint8_t>& alive,
                   SkelPlan& sp) const;
 
+  // Drop the R rows whose DOF is no longer alive (the plan keeps its order).
+  void filter_rows(SkelPlan& sp, const std::vector<uint8_t>& alive) const;
+  // build_cells from an explicit active list (sorted global ids).
+  void build_cells_from(int level, const std::vector<int32_t>& active, CellPlan& cp) const;
+
   // Position of global DOF g in the boundary list of cell (cx,cy,cz) of plan cp.
   int32_t pos_in_cell(const CellPlan& cp, int32_t g, int cx, int cy, int cz) const;
 

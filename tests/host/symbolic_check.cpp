@@ -124,6 +124,25 @@ int main(int argc, char** argv) {
         rows_total += sp.rowOff[f + 1] - sp.rowOff[f];
       }
     }
+    // an edge plan built before some face DOFs die, then filtered, equals a
+    // plan built afterwards
+    {
+      std::vector<uint8_t> alive_pre = alive, alive_post = alive;
+      int t = 0;
+      for (int32_t g : cp.active) {
+        const int x[3] = {g % n, (g / n) % n, g / (n * n)};
+        int ns = 0;
+        for (int d = 0; d < 3; ++d) ns += is_sep(x[d], s);
+        if (ns == 1 && alive_post[g] && (t++ % 3 == 0)) alive_post[g] = 0;
+      }
+      SkelPlan a, b;
+      sym.build_skel(cp, 2, alive_pre, a);
+      sym.filter_rows(a, alive_post);
+      sym.build_skel(cp, 2, alive_post, b);
+      CHECK(a.nfront == b.nfront && a.rowOff == b.rowOff && a.rowDof == b.rowDof &&
+                a.rowPos == b.rowPos && a.nR == b.nR && a.cells == b.cells,
+            "filtered edge plan differs at level %d", level);
+    }
     const int c = C;
     CHECK(counts[1] == 3 * (c - 1) * c * c, "face count");
     CHECK(counts[2] == 3 * (c - 1) * (c - 1) * c, "edge count");
@@ -131,6 +150,15 @@ int main(int argc, char** argv) {
     std::vector<int32_t> next;
     for (int32_t g : cp.active)
       if (alive[g]) next.push_back(g);
+    // building from an explicit list equals building from the stored set
+    {
+      CellPlan x, y;
+      sym.build_cells_from(level + 1, next, x);
+      sym.set_active(next);
+      sym.build_cells(level + 1, y);
+      CHECK(x.dofs == y.dofs && x.off == y.off && x.p == y.p && x.posB == y.posB,
+            "build_cells_from differs");
+    }
     sym.set_active(next);
     prev = std::move(cp);
   }
