@@ -48,6 +48,11 @@ struct SkelDesc {
   int nF, nR;
   int k;            // rank (skeleton count) found by the ID
   int cell[4];
+  // matrix the ID factors: idm x nF at offset idoff (ld = idld) of the arena
+  // given to the ID; either the R rows of the gather buffer (idm = nR) or the
+  // triangular factor of their unpivoted QR (idm = nF)
+  int64_t idoff;
+  int idm, idld;
 };
 template <typename T>
 void skel_gather(const SkelDesc* d_f, const SkelDesc* h_f, int nf, int ncp,

@@ -30,6 +30,9 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
                                  int32_t* perm, T* Farena, double* scratch, int32_t* stepAr,
                                  T* Fscratch, double eps, cudaStream_t st);
 size_t id_fscratch_elems(int64_t total_front_dofs);
+template <typename T>
+void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garena, T* Rout,
+                    const std::vector<int64_t>& rOff, cudaStream_t st);
 
 namespace {
 thread_local std::string g_last_error;
@@ -566,6 +569,9 @@ void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& a
     d.nF = sp.nF[f];
     d.nR = sp.nR[f];
     d.G = goff;
+    d.idoff = goff + sp.nF[f];
+    d.idm = sp.nR[f];
+    d.idld = sp.nF[f] + sp.nR[f];
     d.rows = sp.rowOff[f] * ncp;
     d.perm = poff;
     d.Tm = toff;
@@ -586,26 +592,59 @@ void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& a
   tm.alloc(sizeof(T) * std::max<int64_t>(1, toff), &F_.mem);
   skel_gather<T>(sd_d.as<SkelDesc>(), sd.data(), nf, ncp, rowpos_d.as<int32_t>(),
                  cdesc_d.as<CellDesc>(), Kar.as<T>(), G.as<T>(), st_);
-  interpolative_decomposition<T>(sd_d.as<SkelDesc>(), sd.data(), nf, G.as<T>(),
-                                 perm_d.as<int32_t>(), tm.as<T>(), scratch.as<double>(),
-                                 steps.as<int32_t>(), fsc.as<T>(), F_.eps, st_);
+  // fronts with many more coupled rows than DOFs: reduce the rows by an
+  // unpivoted QR first; their ID then runs on the square triangular factor
+  std::vector<int> sel[2];   // 0: ID on the gathered rows, 1: ID on R
+  for (int f = 0; f < nf; ++f)
+    sel[(sd[f].nR > 2 * sd[f].nF && sd[f].nF >= 96) ? 1 : 0].push_back(f);
+  DevBuf Rbuf;
+  if (!sel[1].empty()) {
+    std::vector<int64_t> roff(sel[1].size());
+    int64_t rtot = 0;
+    for (size_t i = 0; i < sel[1].size(); ++i) {
+      roff[i] = rtot;
+      rtot += (int64_t)sd[sel[1][i]].nF * sd[sel[1][i]].nF;
+    }
+    Rbuf.alloc_async(sizeof(T) * rtot, &F_.mem, st_);
+    reduce_rows_qr<T>(sd.data(), sel[1], G.as<T>(), Rbuf.as<T>(), roff, st_);
+    for (size_t i = 0; i < sel[1].size(); ++i) {
+      SkelDesc& d = sd[sel[1][i]];
+      d.idoff = roff[i];
+      d.idm = d.nF;
+      d.idld = d.nF;
+    }
+  }
+  std::vector<SkelDesc> sub[2];
+  DevBuf sub_d[2];
+  for (int g = 0; g < 2; ++g) {
+    if (sel[g].empty()) continue;
+    for (int f : sel[g]) sub[g].push_back(sd[f]);
+    upload_async(sub_d[g], sub[g], &F_.mem, st_);
+    interpolative_decomposition<T>(sub_d[g].as<SkelDesc>(), sub[g].data(), (int)sub[g].size(),
+                                   g == 0 ? G.as<T>() : Rbuf.as<T>(), perm_d.as<int32_t>(),
+                                   tm.as<T>(), scratch.as<double>(), steps.as<int32_t>(),
+                                   fsc.as<T>(), F_.eps, st_);
+    HIF_CUDA_TRY(cudaMemcpyAsync(sub[g].data(), sub_d[g].as<void>(),
+                                 sizeof(SkelDesc) * sub[g].size(), cudaMemcpyDeviceToHost, st_));
+  }
   std::vector<int32_t> perm(poff);
-  HIF_CUDA_TRY(cudaMemcpyAsync(sd.data(), sd_d.as<void>(), sizeof(SkelDesc) * nf,
-                               cudaMemcpyDeviceToHost, st_));
   HIF_CUDA_TRY(cudaMemcpyAsync(perm.data(), perm_d.as<void>(), sizeof(int32_t) * poff,
                                cudaMemcpyDeviceToHost, st_));
   HIF_CUDA_TRY(cudaStreamSynchronize(st_));
+  for (int g = 0; g < 2; ++g)
+    for (size_t i = 0; i < sel[g].size(); ++i) sd[sel[g][i]].k = sub[g][i].k;
   tr_.mark(level_, " gather + ID");
   scratch.release();
   steps.release();
   fsc.release();
+  Rbuf.release();
   if (prof_enabled()) {
-    // unblocked CPQR: each of the k steps reads and writes the trailing
-    // (nR - i) x (nF - i - 1) block once and spends 4 flops per entry on it
+    // pivoted QR: each of the k steps reads and writes the trailing
+    // (idm - i) x (nF - i - 1) block once and spends 4 flops per entry on it
     double fl = 0.0, by = 0.0;
     for (int f = 0; f < nf; ++f) {
       for (int i = 0; i < sd[f].k; ++i) {
-        const double e = (double)(sd[f].nR - i) * (sd[f].nF - i - 1);
+        const double e = (double)(sd[f].idm - i) * (sd[f].nF - i - 1);
         fl += 4.0 * e;
         by += 2.0 * sizeof(T) * e;
       }

@@ -34,6 +34,7 @@
 
 #include "common.cuh"
 #include "front.cuh"
+#include "warp.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -45,66 +46,6 @@ constexpr int ID_THREADS = 512;
 constexpr int ID_WARPS = ID_THREADS / 32;
 constexpr int NBK = 16;   // steps per block of deferred updates
 constexpr int RC = 128;   // rows of V staged in shared memory by the block update
-constexpr int UNR = 8;    // independent loads in flight per lane in the column passes
-
-// sum_{r in [r0, r1)} a[r] b[r] over one warp (result in every lane)
-template <typename T>
-__device__ __forceinline__ T warp_dot(const T* __restrict__ a, const T* __restrict__ b, int r0,
-                                      int r1, int lane) {
-  T acc[4] = {T(0), T(0), T(0), T(0)};
-  int r = r0 + lane;
-  if (r + 32 * (UNR - 1) < r1) {
-    // two chunks in flight: the next chunk's loads are issued before this
-    // chunk's products wait on theirs
-    T x[UNR], y[UNR];
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      x[u] = a[r + 32 * u];
-      y[u] = b[r + 32 * u];
-    }
-    r += 32 * UNR;
-    for (; r + 32 * (UNR - 1) < r1; r += 32 * UNR) {
-      T xn[UNR], yn[UNR];
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        xn[u] = a[r + 32 * u];
-        yn[u] = b[r + 32 * u];
-      }
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) acc[u & 3] = fma(x[u], y[u], acc[u & 3]);
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        x[u] = xn[u];
-        y[u] = yn[u];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) acc[u & 3] = fma(x[u], y[u], acc[u & 3]);
-  }
-  for (; r < r1; r += 32) acc[0] = fma(a[r], b[r], acc[0]);
-  T s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;
-}
-
-// sum of squares (double) of a[r0:r1], one warp
-template <typename T>
-__device__ __forceinline__ double warp_sumsq(const T* __restrict__ a, int r0, int r1, int lane) {
-  double acc[2] = {0.0, 0.0};
-  int r = r0 + lane;
-  for (; r + 32 * (UNR - 1) < r1; r += 32 * UNR) {
-    T x[UNR];
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) x[u] = a[r + 32 * u];
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) acc[u & 1] += (double)x[u] * (double)x[u];
-  }
-  for (; r < r1; r += 32) acc[0] += (double)a[r] * (double)a[r];
-  double s = acc[0] + acc[1];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int* __restrict__ list,
                                                      T* Gar, int32_t* permAr, T* Far,
@@ -116,8 +57,8 @@ __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int*
   const int fidx = list[blockIdx.x / CS];
   SkelDesc& fref = fr[fidx];
   const SkelDesc f = fref;
-  const int nF = f.nF, m = f.nR, ld = nF + m;
-  T* M = Gar + f.G + nF;            // the R rows; column c at M + c*ld
+  const int nF = f.nF, m = f.idm, ld = f.idld;
+  T* M = Gar + f.idoff;             // column c at M + c*ld
   int32_t* pv = permAr + f.perm;
   int32_t* stepOf = stepAr + f.perm;
   double* nrm = scratch + 2 * f.perm;
@@ -404,10 +345,10 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
   std::vector<std::vector<int>> bucket(17);
   int nbig = 0;
   for (int f = 0; f < nf; ++f)
-    if ((double)h_f[f].nF * (h_f[f].nF + h_f[f].nR) > 1.0e6) ++nbig;
+    if ((double)h_f[f].nF * (h_f[f].nF + h_f[f].idm) > 1.0e6) ++nbig;
   const int cs_big = std::max(1, std::min(16, 2 * nsm / std::max(1, nbig)));
   for (int f = 0; f < nf; ++f) {
-    const double work = (double)h_f[f].nF * (h_f[f].nF + h_f[f].nR);
+    const double work = (double)h_f[f].nF * (h_f[f].nF + h_f[f].idm);
     int cs = work > 1.0e6 ? cs_big : 1;
     cs = std::min(cs, std::max(1, h_f[f].nF / 8));   // at least 8 columns per CTA
     bucket[cs].push_back(f);
