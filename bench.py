@@ -161,6 +161,51 @@ def run_reference(args, w):
     return 0
 
 
+def run_serving(args):
+    """Config 4: Poisson request stream, resident operators, batched solves."""
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1607_00346_gb300 import serving
+
+    torch.cuda.set_device(0)
+    sizes = [32, 48, 64, 96, 128]
+    be = serving.HifBackend(eps=1e-6, precision=1, lo=-2.0, hi=2.0, b=0.0)
+    budget = int(args.serve_budget_gb * (1 << 30))
+    # capacity: mean service time of requests served one at a time
+    probe = serving.poisson_requests(len(sizes), 1.0, sizes, seed=20260104, nrhs_max=16)
+    for i, r in enumerate(probe):
+        r.n = sizes[i]
+        r.m = serving.leaf_size(r.n)
+        r.arrival = 0.0
+    warm = serving.Server(be, budget, workers=1)
+    warm.run(probe[:2], realtime=False)
+    warm.release_all()
+    t0 = time.perf_counter()
+    one = serving.Server(be, budget, workers=1)
+    one.run(probe, realtime=False)
+    one.release_all()
+    mean_service = (time.perf_counter() - t0) / len(probe)
+    capacity = 1.0 / mean_service
+    out = {"metric": "serving: p50/p99 request latency and solves/s (config 4)",
+           "unit": "ms / solves/s", "data": "synthetic", "n_gpus": 1,
+           "config": {"sizes": sizes, "a": "10^U(-2,2) iid per point, own seed per request",
+                      "b": 0.0, "eps": 1e-6, "precision": "fp32 factor, fp64 PCG to 1e-10",
+                      "rhs": "1-16 N(0,1) per request", "workers": args.serve_workers,
+                      "budget_gb": args.serve_budget_gb, "requests": args.serve_requests},
+           "capacity_req_per_s": capacity, "mean_service_s": mean_service, "loads": {}}
+    for load in (0.5, 0.8):
+        reqs = serving.poisson_requests(args.serve_requests, load * capacity, sizes,
+                                        seed=20260104 + int(load * 10), nrhs_max=16)
+        srv = serving.Server(be, budget, workers=args.serve_workers)
+        st = srv.run(reqs)
+        srv.release_all()
+        out["loads"][str(load)] = st
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -173,7 +218,13 @@ def main():
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=32)
+    ap.add_argument("--serve", action="store_true", help="run the serving benchmark instead")
+    ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=200.0)
     args = ap.parse_args()
+    if args.serve:
+        return run_serving(args)
     w = dict(WORKLOADS[args.workload])
     if args.nrhs:
         w["nrhs"] = args.nrhs

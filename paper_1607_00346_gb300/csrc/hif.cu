@@ -1117,10 +1117,13 @@ size_t hif_predict_bytes(const hif_grid* grid, const hif_options* opt) {
   const double N = (double)grid->n * grid->n * grid->n;
   const int prec = opt ? opt->precision : HIF_PREC_FP64;
   const double word = prec == HIF_PREC_FP32 ? 4.0 : 8.0;
-  // operator (4 doubles per DOF) + level-0 frontal matrices and factor panels
-  // (about 150 and 100 entries per DOF) + index lists; the upper levels add a
-  // comparable amount (O(N) in total, §3.3.1).
-  return (size_t)(N * (32.0 + 2.0 * 250.0 * word + 64.0));
+  // Peak device bytes of hif_factor: the operator (32 B per DOF) plus factor
+  // words per DOF growing with log2 n, fitted to measured peaks at eps = 1e-6
+  // (64^3: ~2000 words per DOF, 128^3: ~3000) with a 25% margin, and at
+  // least 400 words per DOF for small grids.
+  const double lg = std::log2((double)grid->n);
+  const double words = std::max(400.0, -3718.0 + 955.0 * lg);
+  return (size_t)(N * (32.0 + 1.25 * words * word) + (64u << 20));
 }
 
 void hif_destroy(hif_handle h) { delete h; }

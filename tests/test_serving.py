@@ -1,0 +1,138 @@
+"""Serving loop (§8 a10): admission by predicted footprint, resident operators,
+batching of right-hand sides per operator, concurrent workers.
+
+CPU tests drive the scheduler with a fake backend whose 'solution' is a known
+function of the operator and the right-hand side; the GPU test checks that a
+result is the same alone and in a concurrent mix.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_1607_00346_gb300 import inputs
+from paper_1607_00346_gb300.serving import Request, Server, leaf_size, poisson_requests
+
+
+class FakeHandle:
+    def __init__(self, n, seed):
+        self.n, self.seed, self.released = n, seed, False
+
+
+class FakeBackend:
+    """Factor = sleep; solve returns u = f / (1 + seed % 7) for checking."""
+
+    def __init__(self, per_dof=100, t_factor=0.01, t_solve=0.002):
+        self.per_dof, self.t_factor, self.t_solve = per_dof, t_factor, t_solve
+        self.mu = threading.Lock()
+        self.live = 0
+        self.peak = 0
+        self.factorizations = []
+        self.solve_batches = []
+
+    def new_stream(self):
+        return None
+
+    def predict_bytes(self, n, m):
+        return n ** 3 * self.per_dof
+
+    def factor(self, n, m, seed, stream):
+        with self.mu:
+            self.live += n ** 3 * self.per_dof
+            self.peak = max(self.peak, self.live)
+            self.factorizations.append((n, seed))
+        time.sleep(self.t_factor)
+        return FakeHandle(n, seed), n ** 3 * self.per_dof
+
+    def solve(self, h, n, rhs, stream):
+        assert not h.released
+        time.sleep(self.t_solve)
+        with self.mu:
+            self.solve_batches.append(rhs.shape[0])
+        return [1] * rhs.shape[0], [1e-12] * rhs.shape[0], rhs / (1.0 + h.seed % 7)
+
+    def release(self, h):
+        h.released = True
+        with self.mu:
+            self.live -= h.n ** 3 * self.per_dof
+
+
+def _check_results(done):
+    for r in done:
+        f = inputs.normal_rhs(r.n, r.nrhs, 10_000 + r.rid)
+        assert np.allclose(r.u, f / (1.0 + r.seed % 7))
+
+
+def test_all_served_and_split_back_correctly():
+    be = FakeBackend()
+    srv = Server(be, mem_budget=10 * 32 ** 3 * 100, workers=3)
+    reqs = poisson_requests(30, rate=400.0, sizes=[16, 24, 32], seed=1, nrhs_max=4,
+                            repeat_prob=0.5)
+    st = srv.run(reqs)
+    assert st["requests"] == 30 and st["failed"] == 0
+    _check_results(srv.done)
+    assert st["p50_ms"] <= st["p99_ms"]
+    assert st["solves"] == sum(r.nrhs for r in reqs)
+
+
+def test_budget_respected_and_lru_eviction():
+    be = FakeBackend()
+    budget = 2 * 32 ** 3 * 100          # two 32^3 operators at a time
+    srv = Server(be, mem_budget=budget, workers=4)
+    reqs = [Request(rid=i, n=32, m=4, seed=100 + i, nrhs=1, arrival=0.001 * i) for i in range(8)]
+    srv.run(reqs)
+    assert be.peak <= budget
+    assert len(be.factorizations) == 8
+    assert sum(1 for _ in srv.resident) <= 2
+
+
+def test_same_operator_batched_and_factored_once():
+    be = FakeBackend(t_factor=0.05)
+    srv = Server(be, mem_budget=10 ** 9, workers=2)
+    # eight requests for one operator arrive while its factorization runs
+    reqs = [Request(rid=i, n=16, m=4, seed=7, nrhs=2, arrival=0.0 + 0.002 * i) for i in range(8)]
+    srv.run(reqs)
+    assert len(be.factorizations) == 1
+    assert max(be.solve_batches) > 2          # several requests shared one solve
+    _check_results(srv.done)
+
+
+def test_oversized_request_is_refused_and_others_served():
+    be = FakeBackend()
+    srv = Server(be, mem_budget=16 ** 3 * 100, workers=2)
+    reqs = [Request(rid=0, n=32, m=4, seed=1, nrhs=1, arrival=0.0),     # too large
+            Request(rid=1, n=16, m=4, seed=2, nrhs=2, arrival=0.001)]
+    st = srv.run(reqs)
+    assert st["failed"] == 1 and st["requests"] == 1
+    assert srv.failed[0].rid == 0
+    _check_results(srv.done)
+
+
+def test_leaf_sizes():
+    assert [leaf_size(n) for n in (16, 32, 48, 64, 96, 128)] == [4, 4, 3, 4, 3, 4]
+
+
+@pytest.mark.gpu
+def test_gpu_result_same_alone_and_in_the_mix():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_00346_gb300 import build
+    from paper_1607_00346_gb300.serving import HifBackend
+    build.build_library()
+    be = HifBackend(eps=1e-6, precision=1, keep_u=True)
+    mix = poisson_requests(12, rate=50.0, sizes=[16, 24, 32], seed=5, nrhs_max=3,
+                           repeat_prob=0.3)
+    srv = Server(be, mem_budget=8 << 30, workers=4)
+    st = srv.run(mix)
+    assert st["requests"] == 12 and st["failed"] == 0
+    srv.release_all()
+    for r in srv.done:
+        assert max(r.relres) <= 1e-10
+        alone = Server(be, mem_budget=8 << 30, workers=1)
+        alone.run([Request(rid=r.rid, n=r.n, m=r.m, seed=r.seed, nrhs=r.nrhs, arrival=0.0)])
+        a = alone.done[0]
+        alone.release_all()
+        # the same factorization and the same solve: identical up to rounding
+        assert np.allclose(a.u, r.u, rtol=0, atol=1e-12 * np.abs(a.u).max())
