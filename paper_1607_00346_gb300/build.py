@@ -18,7 +18,7 @@ LIB = os.path.join(BUILD, "libhif.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["dense.cu", "front.cu", "idk.cu", "qr.cu", "solve.cu", "prof.cu", "hif.cu"]
+CU_SOURCES = ["dense.cu", "tc.cu", "front.cu", "idk.cu", "qr.cu", "solve.cu", "prof.cu", "hif.cu"]
 CXX_SOURCES = ["symbolic.cpp"]
 
 

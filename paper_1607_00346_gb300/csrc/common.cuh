@@ -61,9 +61,11 @@ class ProfScope {
 
 // ---- device-side error flags -------------------------------------------------
 // Kernels never trap.  A failed Cholesky pivot (not positive or not finite)
-// records the front index in flags[0] (first failure wins) and the kernel
-// carries on with a harmless value so that the launch finishes normally.
-enum : int { FLAG_NOT_SPD = 0, FLAG_COUNT = 4 };
+// records the front index in flags[FLAG_NOT_SPD] (first failure wins) and the
+// kernel carries on with a harmless value so that the launch finishes
+// normally; a bounded wait that ran out records the front in
+// flags[FLAG_TIMEOUT] and the kernel returns early.
+enum : int { FLAG_NOT_SPD = 0, FLAG_TIMEOUT = 1, FLAG_COUNT = 4 };
 
 // ---- work descriptors ---------------------------------------------------------
 
@@ -73,10 +75,10 @@ enum : int { FLAG_NOT_SPD = 0, FLAG_COUNT = 4 };
 struct DFront {
   int64_t K;     // element offset of K in the K arena
   int64_t P;     // element offset of P in the factor arena
-  int n;
+  int n;         // extent handled by the kernel (rows/columns 0..n-1)
   int p;
   int id;        // front number (reported on failure)
-  int pad;
+  int ld;        // leading dimension of K and P (the front's full size)
 };
 
 // Batched matrix product C (m x n) = beta C + alpha op(A) op(B) with k inner.
@@ -86,6 +88,8 @@ struct GemmOp {
   int lda, ldb, ldc;
   int transA, transB;
   float alpha, beta;
+  int lower;         // 1: C is symmetric, only tiles touching its lower triangle are computed
+  int pad;
 };
 
 // Batched matrix-vector product on a front of the apply (see apply kernels).

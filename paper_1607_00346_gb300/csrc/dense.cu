@@ -7,6 +7,8 @@
 // Fronts whose work is finished, and tiles outside a front, exit at once.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <type_traits>
 #include <vector>
 
 #include "dense.cuh"
@@ -60,6 +62,7 @@ __global__ void __launch_bounds__(PANEL_ROWS) k_panel(const DFront* __restrict__
   const int jb = min(NB, d.p - j0);
   const int j1 = j0 + jb;
   const int n = d.n;
+  const int64_t ld = d.ld;
   const int r0 = j1 + blockIdx.x * PANEL_ROWS;
   if (blockIdx.x > 0 && r0 >= n) return;
   T* K = Kar + d.K;
@@ -69,7 +72,7 @@ __global__ void __launch_bounds__(PANEL_ROWS) k_panel(const DFront* __restrict__
   for (int e = tid; e < NB * NB; e += PANEL_ROWS) {
     int r = e % NB, c = e / NB;
     T v = T(0);
-    if (r < jb && c < jb && r >= c) v = K[(int64_t)(j0 + r) + (int64_t)(j0 + c) * n];
+    if (r < jb && c < jb && r >= c) v = K[(int64_t)(j0 + r) + (int64_t)(j0 + c) * ld];
     D[r][c] = v;
   }
   __syncthreads();
@@ -96,14 +99,14 @@ __global__ void __launch_bounds__(PANEL_ROWS) k_panel(const DFront* __restrict__
   if (blockIdx.x == 0) {
     for (int e = tid; e < jb * jb; e += PANEL_ROWS) {
       int r = e % jb, c = e / jb;
-      P[(int64_t)(j0 + r) + (int64_t)(j0 + c) * n] = r >= c ? D[r][c] : T(0);
+      P[(int64_t)(j0 + r) + (int64_t)(j0 + c) * ld] = r >= c ? D[r][c] : T(0);
     }
   }
   const int r = r0 + tid;
   if (r >= n) return;
   T x[NB];
 #pragma unroll
-  for (int c = 0; c < NB; ++c) x[c] = c < jb ? K[(int64_t)r + (int64_t)(j0 + c) * n] : T(0);
+  for (int c = 0; c < NB; ++c) x[c] = c < jb ? K[(int64_t)r + (int64_t)(j0 + c) * ld] : T(0);
 #pragma unroll
   for (int c = 0; c < NB; ++c) {
     if (c < jb) {
@@ -117,7 +120,7 @@ __global__ void __launch_bounds__(PANEL_ROWS) k_panel(const DFront* __restrict__
 #pragma unroll
   for (int c = 0; c < NB; ++c) {
     if (c < jb) {
-      const int64_t o = (int64_t)r + (int64_t)(j0 + c) * n;
+      const int64_t o = (int64_t)r + (int64_t)(j0 + c) * ld;
       K[o] = x[c];
       if (toP) P[o] = x[c];
     }
@@ -140,6 +143,7 @@ __global__ void __launch_bounds__(256) k_syrk(const DFront* __restrict__ fr, T* 
   const int jb = min(NB, d.p - j0);
   const int j1 = j0 + jb;
   const int n = d.n;
+  const int64_t ld = d.ld;
   const int nt = (n - j1 + TILE - 1) / TILE;
   if ((int)blockIdx.x >= nt * (nt + 1) / 2) return;
   int ti, tj;
@@ -155,8 +159,8 @@ __global__ void __launch_bounds__(256) k_syrk(const DFront* __restrict__ fr, T* 
       int rr = e % TILE, kk = e / TILE;
       int col = j0 + k0 + kk;
       bool kin = k0 + kk < jb;
-      As[kk][rr] = (kin && rb + rr < n) ? K[(int64_t)(rb + rr) + (int64_t)col * n] : T(0);
-      Bs[kk][rr] = (kin && cb + rr < n) ? K[(int64_t)(cb + rr) + (int64_t)col * n] : T(0);
+      As[kk][rr] = (kin && rb + rr < n) ? K[(int64_t)(rb + rr) + (int64_t)col * ld] : T(0);
+      Bs[kk][rr] = (kin && cb + rr < n) ? K[(int64_t)(cb + rr) + (int64_t)col * ld] : T(0);
     }
     __syncthreads();
     acc.mma(As, Bs, KC);
@@ -170,7 +174,7 @@ __global__ void __launch_bounds__(256) k_syrk(const DFront* __restrict__ fr, T* 
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int r = rb + tr + i;
-      if (r < n && r >= c) K[(int64_t)r + (int64_t)c * n] -= acc.v[i][j];
+      if (r < n && r >= c) K[(int64_t)r + (int64_t)c * ld] -= acc.v[i][j];
     }
   }
 }
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(NB) k_trtri_diag(const DFront* __restrict__ fr
   const int i0 = blockIdx.x * NB;
   if (i0 >= d.p) return;
   const int ib = min(NB, d.p - i0);
-  const int n = d.n;
+  const int64_t n = d.ld;
   T* P = Par + d.P;
   __shared__ T Ls[NB][NB + 1];
   __shared__ T Zs[NB][NB + 1];
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(256) k_trtri_row(const DFront* __restrict__ fr
   const int bj = blockIdx.x;
   if (bj >= bi) return;
   const int ib = min(NB, d.p - i0);
-  const int n = d.n;
+  const int64_t n = d.ld;
   const T* K = Kar + d.K;
   T* P = Par + d.P;
   __shared__ T As[KC][TILE + 4];
@@ -280,6 +284,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, co
   const int tm = (o.m + TILE - 1) / TILE, tn = (o.n + TILE - 1) / TILE;
   if ((int)blockIdx.x >= tm * tn) return;
   const int rb = (blockIdx.x % tm) * TILE, cb = (blockIdx.x / tm) * TILE;
+  if (o.lower && cb >= rb + TILE) return;
   const T* A = Ab + o.A;
   const T* B = Bb + o.B;
   T* C = Cb + o.C;
@@ -408,23 +413,30 @@ __global__ void __launch_bounds__(256) k_gemv_t(const GemvOp* __restrict__ ops,
 
 // ---- host wrappers ---------------------------------------------------------------
 
+// products at least this large (rows of X^T) go to the tensor cores (FP32)
+constexpr int TC_MIN_ROWS = 256;
+
 template <typename T>
 void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront, T* Karena,
                       T* Parena, int* d_flags, cudaStream_t st) {
   if (nfront == 0) return;
+  // HIF_NO_TENSOR_CORES=1 keeps every product on the FMA units
+  static const bool tc_off = std::getenv("HIF_NO_TENSOR_CORES") != nullptr;
+  const bool use_tc = std::is_same<T, float>::value && !tc_off;
   const int pmax = h_fronts[0].p;
-  // prefix maxima of n (fronts are sorted by p, not by n)
-  std::vector<int> nmax(nfront);
-  int mx = 0;
-  for (int f = 0; f < nfront; ++f) {
-    mx = std::max(mx, h_fronts[f].n);
-    nmax[f] = mx;
-  }
+  // 1. Cholesky of the leading p x p block (right-looking, panels of NB):
+  //    the kernels see extent p, leading dimension n
+  std::vector<DFront> lead(h_fronts, h_fronts + nfront);
+  for (auto& f : lead) f.n = f.p;
+  DFront* d_lead = nullptr;
+  HIF_CUDA_TRY(cudaMallocAsync(&d_lead, sizeof(DFront) * nfront, st));
+  HIF_CUDA_TRY(cudaMemcpyAsync(d_lead, lead.data(), sizeof(DFront) * nfront,
+                               cudaMemcpyHostToDevice, st));
   for (int j0 = 0; j0 < pmax; j0 += NB) {
     int nact = 0;
-    while (nact < nfront && h_fronts[nact].p > j0) ++nact;
-    const int nm = nmax[nact - 1];
-    const int j1min = j0 + 1;  // smallest possible j1 among active fronts
+    while (nact < nfront && lead[nact].p > j0) ++nact;
+    const int nm = lead[0].p;   // fronts are sorted by p, largest first
+    const int j1min = j0 + 1;   // smallest possible j1 among active fronts
     const int chunks = std::max(1, ceil_div(std::max(0, nm - j1min), PANEL_ROWS));
     int ntile = ceil_div(std::max(0, nm - j1min), TILE);
     const int pairs = std::max(1, ntile * (ntile + 1) / 2);
@@ -432,8 +444,8 @@ void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront
     double pf = 0, pb = 0, sf = 0, sb = 0;
     if (prof_enabled()) {
       for (int f = 0; f < nact; ++f) {
-        const double jb = std::min(NB, h_fronts[f].p - j0);
-        const double rest = h_fronts[f].n - j0 - jb;
+        const double jb = std::min(NB, lead[f].p - j0);
+        const double rest = lead[f].p - j0 - jb;
         pf += jb * jb * jb / 3.0 + rest * jb * jb;
         pb += sizeof(T) * (jb * jb / 2.0 + 2.0 * rest * jb);
         sf += rest * (rest + 1.0) * jb;
@@ -444,24 +456,25 @@ void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront
       const int nb = std::min(MAX_GRID_Y, nact - f0);
       {
         ProfScope ps("chol_panel", st, pf, pb);
-        k_panel<T><<<dim3(chunks, nb), PANEL_ROWS, 0, st>>>(d_fronts + f0, Karena, Parena, j0,
+        k_panel<T><<<dim3(chunks, nb), PANEL_ROWS, 0, st>>>(d_lead + f0, Karena, Parena, j0,
                                                             d_flags);
         HIF_CHECK_LAUNCH();
       }
       {
         ProfScope ps("chol_trailing_update", st, sf, sb);
-        k_syrk<T><<<dim3(pairs, nb), 256, 0, st>>>(d_fronts + f0, Karena, j0);
+        k_syrk<T><<<dim3(pairs, nb), 256, 0, st>>>(d_lead + f0, Karena, j0);
         HIF_CHECK_LAUNCH();
       }
     }
   }
-  // Linv = L^{-1}: diagonal blocks, then block rows
+  HIF_CUDA_TRY(cudaFreeAsync(d_lead, st));
+  // 2. Linv = L^{-1}: diagonal blocks, then block rows
   const int nblk = ceil_div(pmax, NB);
   for (int f0 = 0; f0 < nfront; f0 += MAX_GRID_Y) {
     const int nb = std::min(MAX_GRID_Y, nfront - f0);
     double fl = 0;
     if (prof_enabled())
-      for (int f = f0; f < f0 + nb; ++f) fl += std::pow((double)h_fronts[f].p, 1) * NB * NB / 3.0;
+      for (int f = f0; f < f0 + nb; ++f) fl += (double)h_fronts[f].p * NB * NB / 3.0;
     ProfScope ps("trtri_diag", st, fl, 0.0);
     k_trtri_diag<T><<<dim3(nblk, nb), NB, 0, st>>>(d_fronts + f0, Parena);
     HIF_CHECK_LAUNCH();
@@ -476,7 +489,41 @@ void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront
       ProfScope ps("trtri_row", st, fl, 0.0);
       k_trtri_row<T><<<dim3(bi, nb), 256, 0, st>>>(d_fronts + f0, Karena, Parena, bi);
       HIF_CHECK_LAUNCH();
-      }
+    }
+  }
+  // 3. X^T = A_NI L^{-T} (into the panel below Linv) and 4. the Schur
+  //    complement A_NN -= X^T X (lower tiles), each one deep product per front
+  std::vector<GemmOp> xo, so;
+  int maxrows = 0;
+  for (int f = 0; f < nfront; ++f) {
+    const DFront& h = h_fronts[f];
+    const int nb = h.n - h.p;
+    if (nb <= 0 || h.p <= 0) continue;
+    const int ld = h.ld;
+    GemmOp x{h.K + h.p, h.P, h.P + h.p, nb, h.p, h.p, ld, ld, ld, 0, 1, 1.f, 0.f, 0, 0};
+    GemmOp s{h.P + h.p, h.P + h.p, h.K + h.p + (int64_t)h.p * ld, nb, nb, h.p, ld, ld, ld, 0, 1,
+             -1.f, 1.f, 1, 0};
+    xo.push_back(x);
+    so.push_back(s);
+    maxrows = std::max(maxrows, nb);
+  }
+  if (!xo.empty()) {
+    GemmOp* d_ops = nullptr;
+    const size_t cnt = xo.size();
+    HIF_CUDA_TRY(cudaMallocAsync(&d_ops, sizeof(GemmOp) * 2 * cnt, st));
+    HIF_CUDA_TRY(cudaMemcpyAsync(d_ops, xo.data(), sizeof(GemmOp) * cnt, cudaMemcpyHostToDevice, st));
+    HIF_CUDA_TRY(cudaMemcpyAsync(d_ops + cnt, so.data(), sizeof(GemmOp) * cnt,
+                                 cudaMemcpyHostToDevice, st));
+    if (use_tc && maxrows >= TC_MIN_ROWS) {
+      gemm_tc(d_ops, xo.data(), (int)cnt, reinterpret_cast<const float*>(Karena),
+              reinterpret_cast<const float*>(Parena), reinterpret_cast<float*>(Parena), d_flags, st);
+      gemm_tc(d_ops + cnt, so.data(), (int)cnt, reinterpret_cast<const float*>(Parena),
+              reinterpret_cast<const float*>(Parena), reinterpret_cast<float*>(Karena), d_flags, st);
+    } else {
+      gemm_batched<T>(d_ops, xo.data(), (int)cnt, Karena, Parena, Parena, st);
+      gemm_batched<T>(d_ops + cnt, so.data(), (int)cnt, Parena, Parena, Karena, st);
+    }
+    HIF_CUDA_TRY(cudaFreeAsync(d_ops, st));
   }
 }
 

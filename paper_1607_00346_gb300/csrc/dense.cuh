@@ -16,6 +16,11 @@ template <typename T>
 void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront, T* Karena,
                       T* Parena, int* d_flags, cudaStream_t st);
 
+// C = beta C + alpha op(A) op(B) on the tensor cores (tcgen05, 3xTF32; see
+// tc.cu): GemmOp semantics as gemm_batched, beta 0 or 1, FP32 data.
+void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Abase,
+             const float* Bbase, float* Cbase, int* d_flags, cudaStream_t st);
+
 // C = beta C + alpha op(A) op(B) for a batch of independent problems.
 template <typename T>
 void gemm_batched(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const T* Abase,

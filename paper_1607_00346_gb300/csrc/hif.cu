@@ -32,7 +32,7 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
 size_t id_fscratch_elems(int64_t total_front_dofs);
 template <typename T>
 void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garena, T* Rout,
-                    const std::vector<int64_t>& rOff, cudaStream_t st);
+                    const std::vector<int64_t>& rOff, int* d_flags, cudaStream_t st);
 
 namespace {
 thread_local std::string g_last_error;
@@ -307,6 +307,10 @@ void Builder<T>::check_flags(const char* where) {
   int h[FLAG_COUNT];
   HIF_CUDA_TRY(cudaMemcpyAsync(h, flags_.as<int>(), sizeof(h), cudaMemcpyDeviceToHost, st_));
   HIF_CUDA_TRY(cudaStreamSynchronize(st_));
+  if (h[FLAG_TIMEOUT] >= 0)
+    throw Error{HIF_ERR_TIMEOUT, std::string("a bounded device wait expired in ") + where +
+                                     " at level " + std::to_string(level_) + ", front " +
+                                     std::to_string(h[FLAG_TIMEOUT])};
   if (h[FLAG_NOT_SPD] >= 0)
     throw Error{HIF_ERR_NOT_SPD, std::string("non-positive Cholesky pivot in ") + where +
                                      " at level " + std::to_string(level_) + ", front " +
@@ -472,13 +476,15 @@ void Builder<T>::cell_step(CellPlan& cp, DevBuf& Kar, DevBuf& cdesc_d, std::vect
   int64_t pcur = 0;
   for (int c : order) {
     poff[c] = pcur;
-    fr.push_back(DFront{cdesc[c].K, pcur, cdesc[c].n, cdesc[c].p, c, 0});
+    fr.push_back(DFront{cdesc[c].K, pcur, cdesc[c].n, cdesc[c].p, c, cdesc[c].n});
     pcur += (int64_t)cdesc[c].n * cdesc[c].p;
     F_.stats.flops += std::pow((double)cdesc[c].p, 3) / 3.0 +
                       (double)cdesc[c].p * cdesc[c].p * (cdesc[c].n - cdesc[c].p) +
                       (double)(cdesc[c].n - cdesc[c].p) * (cdesc[c].n - cdesc[c].p) * cdesc[c].p;
   }
   s.panels.alloc(sizeof(T) * std::max<int64_t>(1, pcur), &F_.mem);
+  // zero: the products read L^{-1} as a dense block (zeros above the diagonal)
+  HIF_CUDA_TRY(cudaMemsetAsync(s.panels.as<void>(), 0, sizeof(T) * std::max<int64_t>(1, pcur), st_));
   s.entries = pcur;
   DevBuf fr_d;
   upload_async(fr_d, fr, &F_.mem, st_);
@@ -606,7 +612,7 @@ void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& a
       rtot += (int64_t)sd[sel[1][i]].nF * sd[sel[1][i]].nF;
     }
     Rbuf.alloc_async(sizeof(T) * rtot, &F_.mem, st_);
-    reduce_rows_qr<T>(sd.data(), sel[1], G.as<T>(), Rbuf.as<T>(), roff, st_);
+    reduce_rows_qr<T>(sd.data(), sel[1], G.as<T>(), Rbuf.as<T>(), roff, flags_.as<int>(), st_);
     for (size_t i = 0; i < sel[1].size(); ++i) {
       SkelDesc& d = sd[sel[1][i]];
       d.idoff = roff[i];
@@ -669,7 +675,7 @@ void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& a
     d.Z = zoff;
     d.P = pnl;
     const int p = d.nF - d.k;
-    fr.push_back(DFront{d.Z, d.P, d.nF, p, f, 0});
+    fr.push_back(DFront{d.Z, d.P, d.nF, p, f, d.nF});
     zoff += (int64_t)d.nF * d.nF;
     pnl += (int64_t)d.nF * p;
     F_.stats.flops += 4.0 * d.nF * (double)d.k * p + std::pow((double)p, 3) / 3.0 +
@@ -706,6 +712,7 @@ void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& a
   s.kind = 1;
   s.level = level_;
   s.panels.alloc(sizeof(T) * std::max<int64_t>(1, pnl), &F_.mem);
+  HIF_CUDA_TRY(cudaMemsetAsync(s.panels.as<void>(), 0, sizeof(T) * std::max<int64_t>(1, pnl), st_));
   std::vector<DFront> frs = fr;
   std::stable_sort(frs.begin(), frs.end(), [](const DFront& x, const DFront& y) { return x.p > y.p; });
   DevBuf fr_d;

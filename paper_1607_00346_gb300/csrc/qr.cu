@@ -16,6 +16,8 @@
 //     accumulation: T_{j+1} = [T_j, -tau_j T_j V_j^T v_j; 0, tau_j]);
 //   * trailing columns: W = V^T A, W = T^T W, A -= V W (batched GEMMs).
 #include <algorithm>
+#include <cstdlib>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -145,9 +147,11 @@ __global__ void k_extract_r(const QRDesc* __restrict__ ds, const int64_t* __rest
 // arena); their n x n triangular factors go to Rout at rOff (ld = n).
 template <typename T>
 void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garena, T* Rout,
-                    const std::vector<int64_t>& rOff, cudaStream_t st) {
+                    const std::vector<int64_t>& rOff, int* d_flags, cudaStream_t st) {
   const int nq = (int)which.size();
   if (nq == 0) return;
+  static const bool tc_off = std::getenv("HIF_NO_TENSOR_CORES") != nullptr;
+  const bool use_tc = std::is_same<T, float>::value && !tc_off;
   // fronts sorted by n (largest first) so that the fronts still factoring a
   // panel are a prefix
   std::vector<int> ord(nq);
@@ -238,9 +242,22 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
     const int cnt = opCnt[pi];
     if (cnt == 0) continue;
     const int64_t o0 = opOff[pi];
-    gemm_batched<T>(d_ops + o0, ops.data() + o0, cnt, Var, Garena, War, st);
-    gemm_batched<T>(d_ops + o0 + cnt, ops.data() + o0 + cnt, cnt, Tar, War, War, st);
-    gemm_batched<T>(d_ops + o0 + 2 * cnt, ops.data() + o0 + 2 * cnt, cnt, Var, War, Garena, st);
+    // W1 = V^T A_t (deep K) goes to the tensor cores for FP32 fronts; the
+    // rank-QB update A_t -= V W2 is a read-modify-write of A_t with K = QB and
+    // runs faster on the SIMT kernel, which keeps more CTAs resident per SM
+    auto product = [&](int which_gemm, const T* A, const T* B, T* C) {
+      const int64_t oi = o0 + (int64_t)which_gemm * cnt;
+      if constexpr (std::is_same<T, float>::value) {
+        if (use_tc && which_gemm == 0) {
+          gemm_tc(d_ops + oi, ops.data() + oi, cnt, A, B, C, d_flags, st);
+          return;
+        }
+      }
+      gemm_batched<T>(d_ops + oi, ops.data() + oi, cnt, A, B, C, st);
+    };
+    product(0, Var, Garena, War);
+    product(1, Tar, War, War);
+    product(2, Var, War, Garena);
   }
   {
     ProfScope ps("id_rowreduce_extract", st);
@@ -257,8 +274,8 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
 }
 
 template void reduce_rows_qr<float>(const SkelDesc*, const std::vector<int>&, float*, float*,
-                                    const std::vector<int64_t>&, cudaStream_t);
+                                    const std::vector<int64_t>&, int*, cudaStream_t);
 template void reduce_rows_qr<double>(const SkelDesc*, const std::vector<int>&, double*, double*,
-                                     const std::vector<int64_t>&, cudaStream_t);
+                                     const std::vector<int64_t>&, int*, cudaStream_t);
 
 }  // namespace hif

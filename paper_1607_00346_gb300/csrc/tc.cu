@@ -1,0 +1,277 @@
+// Batched matrix products on the sm_103a tensor cores: the Schur complements
+// of the partial Cholesky (A_NN -= X^T X, §2.2 / §2.3: the only dense
+// contraction of the method) and X^T = A_NI L^{-T}.  FP32 accuracy from TF32
+// tensor cores by the 3xTF32 split: x = hi + lo with hi = tf32(x),
+// lo = tf32(x - hi), and A B^T ~= hi_A hi_B^T + hi_A lo_B^T + lo_A hi_B^T
+// (FP32 accumulation in tensor memory).
+//
+// Per CTA (128 threads, one 128 x 128 output tile):
+//   * the operand rows are staged in shared memory in the K-major, no-swizzle
+//     core-matrix layout (8 rows x 16 bytes per core matrix; LBO = 128 B
+//     between K-adjacent core matrices, SBO = 1024 B between 8-row groups);
+//   * one thread issues tcgen05.mma.cta_group::1.kind::tf32 (M = N = 128,
+//     K = 8 per instruction) into a 128-column TMEM accumulator and commits
+//     to an mbarrier; the wait on it has an iteration limit (on expiry the
+//     kernel records FLAG_TIMEOUT, frees its TMEM and returns);
+//   * four warps read the accumulator back with tcgen05.ld (warp w owns TMEM
+//     lanes 32w..32w+31 = tile rows) and write alpha times it to C (added to
+//     C when beta = 1).
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "dense.cuh"
+
+namespace hif {
+
+namespace {
+
+constexpr int TC_M = 128;        // tile rows (TMEM lanes)
+constexpr int TC_N = 128;        // tile columns (TMEM columns)
+constexpr int TC_KC = 32;        // K elements staged per chunk
+constexpr int TC_THREADS = 256;   // 128 stage A rows, 128 stage B rows
+constexpr int TILE_BYTES = TC_M * TC_KC * 4;   // one operand, one split: 16 KB
+constexpr long long WAIT_LIMIT = 20000000;     // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared memory matrix descriptor: no swizzle, K-major core matrices
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
+  d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
+  d |= (uint64_t)1 << 46;          // descriptor version of this architecture
+  return d;                        // base offset 0, swizzle mode 0 (none)
+}
+
+// instruction descriptor: D = F32, A = B = TF32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// byte offset of element (row, k) of a TC_M x TC_KC K-major operand
+__device__ __forceinline__ int core_off(int row, int k) {
+  return ((row >> 3) * (TC_KC / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// C (M x N) = beta C + alpha op(A) op(B) for a batch of problems (GemmOp
+// semantics: op(A)[r][k] = transA ? A[k + r lda] : A[r + k lda],
+// op(B)[k][c] = transB ? B[c + k ldb] : B[k + c ldb]).  Operands are read in
+// K chunks of TC_KC, split into TF32 hi/lo parts and staged in one of two
+// shared-memory buffers while the tensor cores work on the other.  beta is 0
+// or 1.  `lower` skips tiles strictly above the diagonal of a symmetric C.
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmOp* __restrict__ ops,
+                                                        const float* __restrict__ Ab,
+                                                        const float* __restrict__ Bb, float* Cb,
+                                                        int* flags) {
+  const GemmOp o = ops[blockIdx.y];
+  const int tm_n = (o.m + TC_M - 1) / TC_M, tn_n = (o.n + TC_N - 1) / TC_N;
+  if ((int)blockIdx.x >= tm_n * tn_n) return;
+  const int rb = (blockIdx.x % tm_n) * TC_M, cb = (blockIdx.x / tm_n) * TC_N;
+  if (o.lower && cb >= rb + TC_M) return;
+  const float* A = Ab + o.A;
+  const float* B = Bb + o.B;
+  float* C = Cb + o.C;
+
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(TC_N));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;\n");
+    s_fail = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  const uint32_t tmem = s_tmem;
+  const uint32_t idesc = idesc_tf32(TC_M, TC_N);
+  const int nchunk = (o.k + TC_KC - 1) / TC_KC;
+  uint32_t phase[2] = {0u, 0u};
+  bool ok = true;
+
+  // bounded wait for the products issued on buffer s
+  auto wait_buf = [&](int s) {
+    long long it = 0;
+    uint32_t done = 0;
+    while (!done) {
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          " selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(smem_u32(&mbar[s])), "r"(phase[s]));
+      if (++it > WAIT_LIMIT) break;
+    }
+    phase[s] ^= 1u;
+    return done != 0;
+  };
+
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int s = ch & 1;
+    unsigned char* buf = smem + s * 4 * TILE_BYTES;
+    if (ch >= 2 && !wait_buf(s)) s_fail = 1;   // buffer s is free again
+    __syncthreads();
+    if (s_fail) {
+      ok = false;
+      break;
+    }
+    const int k0 = ch * TC_KC;
+    {
+      // stage: thread t loads the TC_KC values of one row of A (t < 128) or
+      // of B (t >= 128), splits them and stores 16-byte groups of 4 k
+      const bool isA = tid < TC_M;
+      const int row = tid % TC_M;
+      const float* X = isA ? A : B;
+      const int base = isA ? rb : cb;
+      const int lim = isA ? o.m : o.n;
+      const int ldx = isA ? o.lda : o.ldb;
+      const bool kfast = isA ? (o.transA != 0) : (o.transB == 0);   // k contiguous in memory
+      float v[TC_KC];
+      const bool rin = base + row < lim;
+#pragma unroll
+      for (int k = 0; k < TC_KC; ++k) {
+        const int kk = k0 + k;
+        v[k] = (rin && kk < o.k)
+                   ? (kfast ? X[(int64_t)kk + (int64_t)(base + row) * ldx]
+                            : X[(int64_t)(base + row) + (int64_t)kk * ldx])
+                   : 0.f;
+      }
+      unsigned char* hi = buf + (isA ? 0 : 2 * TILE_BYTES);
+      unsigned char* lo = hi + TILE_BYTES;
+#pragma unroll
+      for (int k = 0; k < TC_KC; k += 4) {
+        float4 h, l;
+        h.x = tf32_hi(v[k]);
+        h.y = tf32_hi(v[k + 1]);
+        h.z = tf32_hi(v[k + 2]);
+        h.w = tf32_hi(v[k + 3]);
+        l.x = tf32_hi(v[k] - h.x);
+        l.y = tf32_hi(v[k + 1] - h.y);
+        l.z = tf32_hi(v[k + 2] - h.z);
+        l.w = tf32_hi(v[k + 3] - h.w);
+        const int off = core_off(row, k);
+        *reinterpret_cast<float4*>(hi + off) = h;
+        *reinterpret_cast<float4*>(lo + off) = l;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+      const uint32_t ah = smem_u32(buf), al = ah + TILE_BYTES, bh = ah + 2 * TILE_BYTES,
+                     bl = ah + 3 * TILE_BYTES;
+      for (int ks = 0; ks < TC_KC / 8; ++ks) {
+        const uint32_t off = ks * 256;   // two core matrices of K per instruction
+        const uint32_t acc0 = (ch > 0 || ks > 0) ? 1u : 0u;
+        mma_tf32(tmem, sdesc(ah + off, 128, 1024), sdesc(bh + off, 128, 1024), idesc, acc0);
+        mma_tf32(tmem, sdesc(ah + off, 128, 1024), sdesc(bl + off, 128, 1024), idesc, 1u);
+        mma_tf32(tmem, sdesc(al + off, 128, 1024), sdesc(bh + off, 128, 1024), idesc, 1u);
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              smem_u32(&mbar[s])));
+    }
+  }
+  // the last one or two chunks are still in flight
+  if (ok) {
+    for (int ch = max(0, nchunk - 2); ch < nchunk; ++ch)
+      if (!wait_buf(ch & 1)) ok = false;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  if (ok && nchunk > 0) {
+    // warp w reads TMEM lanes 32 (w % 4) .. (tile rows) and half w / 4 of the columns
+    const int r = rb + (warp % 4) * 32 + lane;
+    const float al = o.alpha;
+    const int ch0 = (warp / 4) * (TC_N / 2);
+    for (int c0 = ch0; c0 < ch0 + TC_N / 2; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)((warp % 4) * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+          "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+            "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+            "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+            "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+      if (r < o.m) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int c = cb + c0 + j;
+          if (c < o.n) {
+            float* cp = &C[(int64_t)r + (int64_t)c * o.ldc];
+            const float x = al * __uint_as_float(v[j]);
+            *cp = o.beta != 0.f ? *cp + x : x;
+          }
+        }
+      }
+    }
+  } else if (!ok && tid == 0) {
+    atomicCAS(&flags[FLAG_TIMEOUT], -1, (int)blockIdx.y);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_N));
+}
+
+}  // namespace
+
+void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Abase,
+             const float* Bbase, float* Cbase, int* d_flags, cudaStream_t st) {
+  if (nops == 0) return;
+  int mt = 1;
+  double fl = 0;
+  for (int i = 0; i < nops; ++i) {
+    mt = std::max(mt, ceil_div(h_ops[i].m, TC_M) * ceil_div(h_ops[i].n, TC_N));
+    fl += 2.0 * h_ops[i].m * (double)h_ops[i].n * h_ops[i].k * (h_ops[i].lower ? 0.5 : 1.0);
+  }
+  const size_t smem = 2 * 4 * TILE_BYTES;
+  static bool attr = false;
+  if (!attr) {
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    attr = true;
+  }
+  ProfScope ps("gemm_tc", st, fl, 0.0);
+  for (int f0 = 0; f0 < nops; f0 += 65535) {
+    const int nb = std::min(65535, nops - f0);
+    k_gemm_tc<<<dim3(mt, nb), TC_THREADS, smem, st>>>(d_ops + f0, Abase, Bbase, Cbase, d_flags);
+    HIF_CHECK_LAUNCH();
+  }
+}
+
+}  // namespace hif
