@@ -418,11 +418,9 @@ constexpr int TC_MIN_ROWS = 256;
 
 template <typename T>
 void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront, T* Karena,
-                      T* Parena, int* d_flags, cudaStream_t st) {
+                      T* Parena, int* d_flags, bool tensor_cores, cudaStream_t st) {
   if (nfront == 0) return;
-  // HIF_NO_TENSOR_CORES=1 keeps every product on the FMA units
-  static const bool tc_off = std::getenv("HIF_NO_TENSOR_CORES") != nullptr;
-  const bool use_tc = std::is_same<T, float>::value && !tc_off;
+  const bool use_tc = std::is_same<T, float>::value && tensor_cores;
   const int pmax = h_fronts[0].p;
   // 1. Cholesky of the leading p x p block (right-looking, panels of NB):
   //    the kernels see extent p, leading dimension n
@@ -583,7 +581,7 @@ void gemv_batched(const GemvOp* d_ops, const GemvOp* h_ops, int nops, int trans,
 }
 
 #define HIF_INST(T)                                                                          \
-  template void partial_cholesky<T>(const DFront*, const DFront*, int, T*, T*, int*,        \
+  template void partial_cholesky<T>(const DFront*, const DFront*, int, T*, T*, int*, bool,  \
                                     cudaStream_t);                                           \
   template void gemm_batched<T>(const GemmOp*, const GemmOp*, int, const T*, const T*, T*,  \
                                 cudaStream_t);                                               \

@@ -11,10 +11,11 @@ constexpr int TILE = 64;    // output tile of the trailing update / batched GEMM
 // Partial Cholesky of a batch of fronts (§2.2 and §2.3: A_II = L L^T,
 // X = L^{-1} A_IN, A_NN -= X^T X).  Fronts must be sorted by p, largest first.
 // On return: trailing blocks of K hold the Schur complements, P holds
-// [Linv; X^T] (Linv = L^{-1}, lower triangular) for each front.
+// [Linv; X^T] (Linv = L^{-1}, lower triangular) for each front.  With
+// tensor_cores (FP32 only) the deep products run on gemm_tc.
 template <typename T>
 void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront, T* Karena,
-                      T* Parena, int* d_flags, cudaStream_t st);
+                      T* Parena, int* d_flags, bool tensor_cores, cudaStream_t st);
 
 // C = beta C + alpha op(A) op(B) on the tensor cores (tcgen05, 3xTF32; see
 // tc.cu): GemmOp semantics as gemm_batched, beta 0 or 1, FP32 data.

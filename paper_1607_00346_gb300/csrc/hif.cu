@@ -32,7 +32,8 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
 size_t id_fscratch_elems(int64_t total_front_dofs);
 template <typename T>
 void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garena, T* Rout,
-                    const std::vector<int64_t>& rOff, int* d_flags, cudaStream_t st);
+                    const std::vector<int64_t>& rOff, int* d_flags, bool tensor_cores,
+                    cudaStream_t st);
 
 namespace {
 thread_local std::string g_last_error;
@@ -280,7 +281,8 @@ class Builder {
   void check_flags(const char* where);
   void cell_step(CellPlan& cp, DevBuf& Kar, DevBuf& cdesc_d, std::vector<CellDesc>& cdesc,
                  DevBuf& lists_d);
-  void skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& alive, DevBuf& Kar,
+  // returns the number of DOFs the step eliminated (marked dead in alive)
+  int64_t skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& alive, DevBuf& Kar,
                  DevBuf& cdesc_d, SkelPlan* plan = nullptr);
   void gemv_list(GemvList& gl, std::vector<GemvOp>&& ops, int trans, int mat) {
     gl.h = std::move(ops);
@@ -407,6 +409,23 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
       prevDesc.release();
     }
     tr_.mark(level, "frontal matrices");
+    // after the cell step the interiors are gone; the face and edge plans
+    // depend only on that set, so a host thread builds them while the cells
+    // are eliminated on the GPU (the edge rows are filtered again once the
+    // faces have dropped their redundant DOFs)
+    std::vector<uint8_t> alive(N, 0);
+    for (int32_t g : cp.active) alive[g] = 1;
+    for (int c = 0; c < cp.ncell; ++c)
+      for (int64_t t = cp.off[c]; t < cp.off[c] + cp.p[c]; ++t) alive[cp.dofs[t]] = 0;
+    SkelPlan fplan, ep;
+    std::future<void> planning;
+    if (level < L && F_.eps > 0.0) {
+      planning = std::async(std::launch::async, [&]() {
+        auto edges = std::async(std::launch::async, [&]() { sym_.build_skel(cp, 2, alive, ep); });
+        sym_.build_skel(cp, 1, alive, fplan);
+        edges.get();
+      });
+    }
     cell_step(cp, Kar, cdesc_d, cdesc, lists_d);
     tr_.mark(level, "cell elimination");
     F_.stats.fronts[level][0] = cp.ncell;
@@ -416,16 +435,12 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
       F_.stats.level_seconds[level] = seconds_since(tl);
       break;
     }
-    // interiors are eliminated; faces then edges are skeletonized
-    std::vector<uint8_t> alive(N, 0);
-    for (int32_t g : cp.active) alive[g] = 1;
-    for (int c = 0; c < cp.ncell; ++c)
-      for (int64_t t = cp.off[c]; t < cp.off[c] + cp.p[c]; ++t) alive[cp.dofs[t]] = 0;
     if (F_.eps > 0.0) {
-      skel_step(cp, 1, alive, Kar, cdesc_d);
+      planning.get();
+      tr_.mark(level, "plans joined");
+      const int64_t dropped = skel_step(cp, 1, alive, Kar, cdesc_d, &fplan);
       tr_.mark(level, "faces");
-      SkelPlan ep;
-      sym_.build_skel(cp, 2, alive, ep);
+      if (dropped) sym_.filter_rows(ep, alive);
       // the next level's cells, assuming the edges keep every DOF (they
       // usually do), are planned on a host thread while the edges run;
       // rebuilt at the next level if an edge lost DOFs
@@ -489,7 +504,7 @@ void Builder<T>::cell_step(CellPlan& cp, DevBuf& Kar, DevBuf& cdesc_d, std::vect
   DevBuf fr_d;
   upload_async(fr_d, fr, &F_.mem, st_);
   partial_cholesky<T>(fr_d.as<DFront>(), fr.data(), (int)fr.size(), Kar.as<T>(), s.panels.as<T>(),
-                      flags_.as<int>(), st_);
+                      flags_.as<int>(), F_.opt.tensor_cores != 0, st_);
   // apply stage: gather the whole frontal list of every cell
   s.nidx = (int64_t)cp.dofs.size();
   s.idx = std::move(lists_d);
@@ -558,14 +573,14 @@ void Builder<T>::cell_step(CellPlan& cp, DevBuf& Kar, DevBuf& cdesc_d, std::vect
 }
 
 template <typename T>
-void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& alive, DevBuf& Kar,
-                           DevBuf& cdesc_d, SkelPlan* plan) {
+int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& alive,
+                              DevBuf& Kar, DevBuf& cdesc_d, SkelPlan* plan) {
   SkelPlan own;
   if (!plan) sym_.build_skel(cp, kind, alive, own);
   SkelPlan& sp = plan ? *plan : own;
   tr_.mark(level_, kind == 1 ? " symbolic faces" : " symbolic edges");
   const int nf = sp.nfront;
-  if (nf == 0) return;
+  if (nf == 0) return 0;
   const int ncp = sp.ncellPer;
   std::vector<SkelDesc> sd(nf);
   int64_t goff = 0, poff = 0, toff = 0;
@@ -612,7 +627,8 @@ void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& a
       rtot += (int64_t)sd[sel[1][i]].nF * sd[sel[1][i]].nF;
     }
     Rbuf.alloc_async(sizeof(T) * rtot, &F_.mem, st_);
-    reduce_rows_qr<T>(sd.data(), sel[1], G.as<T>(), Rbuf.as<T>(), roff, flags_.as<int>(), st_);
+    reduce_rows_qr<T>(sd.data(), sel[1], G.as<T>(), Rbuf.as<T>(), roff, flags_.as<int>(),
+                      F_.opt.tensor_cores != 0, st_);
     for (size_t i = 0; i < sel[1].size(); ++i) {
       SkelDesc& d = sd[sel[1][i]];
       d.idoff = roff[i];
@@ -662,11 +678,13 @@ void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& a
   for (int f = 0; f < nf; ++f)
     if (sd[f].k < sd[f].nF) act.push_back(f);
   F_.stats.fronts[level_][kind] = (int64_t)act.size();
+  int64_t dropped = 0;
   for (int f : act) {
     const int32_t* pm = &perm[sd[f].perm];
     for (int i = sd[f].k; i < sd[f].nF; ++i) alive[sp.rowDof[sp.rowOff[f] + pm[i]]] = 0;
+    dropped += sd[f].nF - sd[f].k;
   }
-  if (act.empty()) return;
+  if (act.empty()) return 0;
   // frontal matrices Z = Q^T A_FF Q in (redundant, skeleton) order
   int64_t zoff = 0, pnl = 0;
   std::vector<DFront> fr;
@@ -718,7 +736,7 @@ void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& a
   DevBuf fr_d;
   upload_async(fr_d, frs, &F_.mem, st_);
   partial_cholesky<T>(fr_d.as<DFront>(), frs.data(), (int)frs.size(), Z.as<T>(), s.panels.as<T>(),
-                      flags_.as<int>(), st_);
+                      flags_.as<int>(), F_.opt.tensor_cores != 0, st_);
   skel_writeback<T>(sda_d.as<SkelDesc>(), sda.data(), (int)sda.size(), ncp, rowpos_d.as<int32_t>(),
                     perm_d.as<int32_t>(), cdesc_d.as<CellDesc>(), Z.as<T>(), Kar.as<T>(), st_);
   // apply stage
@@ -771,6 +789,7 @@ void Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& a
   upload(s.set_p, spos, &F_.mem, st_);
   F_.work_stride = std::max(F_.work_stride, 2 * s.nidx);
   F_.stages.push_back(std::move(s));
+  return dropped;
 }
 
 // ---- PCG ------------------------------------------------------------------------
@@ -968,6 +987,7 @@ void hif_default_options(hif_options* o) {
   o->use_graphs = 1;
   o->pcg_tol = 1e-10;
   o->max_iter = 200;
+  o->tensor_cores = 1;
 }
 
 const char* hif_version(void) { return "hif-gb300 0.1"; }
@@ -990,6 +1010,8 @@ hif_status hif_factor(const hif_grid* grid, const double* a, const double* b, do
   if (!(o.eps >= 0.0) || !(o.eps < 1.0)) throw Error{HIF_ERR_INVALID_ARG, "eps must be in [0, 1)"};
   if (o.precision != HIF_PREC_FP64 && o.precision != HIF_PREC_FP32)
     throw Error{HIF_ERR_INVALID_ARG, "precision must be HIF_PREC_FP64 or HIF_PREC_FP32"};
+  if (o.tensor_cores != 0 && o.tensor_cores != 1)
+    throw Error{HIF_ERR_INVALID_ARG, "tensor_cores must be 0 or 1"};
   if (!std::isfinite(b_const) || b_const < 0) throw Error{HIF_ERR_INVALID_ARG, "b_const must be finite and >= 0"};
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int64_t N = (int64_t)n * n * n;

@@ -147,11 +147,11 @@ __global__ void k_extract_r(const QRDesc* __restrict__ ds, const int64_t* __rest
 // arena); their n x n triangular factors go to Rout at rOff (ld = n).
 template <typename T>
 void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garena, T* Rout,
-                    const std::vector<int64_t>& rOff, int* d_flags, cudaStream_t st) {
+                    const std::vector<int64_t>& rOff, int* d_flags, bool tensor_cores,
+                    cudaStream_t st) {
   const int nq = (int)which.size();
   if (nq == 0) return;
-  static const bool tc_off = std::getenv("HIF_NO_TENSOR_CORES") != nullptr;
-  const bool use_tc = std::is_same<T, float>::value && !tc_off;
+  const bool use_tc = std::is_same<T, float>::value && tensor_cores;
   // fronts sorted by n (largest first) so that the fronts still factoring a
   // panel are a prefix
   std::vector<int> ord(nq);
@@ -274,8 +274,8 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
 }
 
 template void reduce_rows_qr<float>(const SkelDesc*, const std::vector<int>&, float*, float*,
-                                    const std::vector<int64_t>&, int*, cudaStream_t);
+                                    const std::vector<int64_t>&, int*, bool, cudaStream_t);
 template void reduce_rows_qr<double>(const SkelDesc*, const std::vector<int>&, double*, double*,
-                                     const std::vector<int64_t>&, int*, cudaStream_t);
+                                     const std::vector<int64_t>&, int*, bool, cudaStream_t);
 
 }  // namespace hif

@@ -222,10 +222,15 @@ void Symbolic::build_skel(const CellPlan& cp, int kind, const std::vector<uint8_
     front_of[i] = f;
   }
   const int nf = (int)keys.size();
-  std::vector<std::vector<int32_t>> members(nf);
-  for (int f = 0; f < nf; ++f) members[f].reserve(fcount[f]);
-  for (int64_t i = 0; i < na; ++i)
-    if (front_of[i] >= 0) members[front_of[i]].push_back(cp.active[i]);
+  // members of each front (ascending global index), CSR
+  std::vector<int64_t> moff(nf + 1, 0);
+  for (int f = 0; f < nf; ++f) moff[f + 1] = moff[f] + fcount[f];
+  std::vector<int32_t> mem(moff[nf]);
+  {
+    std::vector<int64_t> cur(moff.begin(), moff.end() - 1);
+    for (int64_t i = 0; i < na; ++i)
+      if (front_of[i] >= 0) mem[cur[front_of[i]]++] = cp.active[i];
+  }
   sp.nfront = nf;
   sp.cells.assign((size_t)nf * ncp, -1);
   sp.nF.assign(nf, 0);
@@ -233,7 +238,7 @@ void Symbolic::build_skel(const CellPlan& cp, int kind, const std::vector<uint8_
   // cells of each front: corners over its separator dimensions
   std::vector<int32_t> cellxyz((size_t)nf * ncp * 3);
   for (int f = 0; f < nf; ++f) {
-    int64_t pk = cp.packed[cp.slot[members[f][0]]];
+    int64_t pk = cp.packed[cp.slot[mem[moff[f]]]];
     int sep = (int)(pk >> 48);
     int lc[3] = {(int)(pk & 0xffff), (int)((pk >> 16) & 0xffff), (int)((pk >> 32) & 0xffff)};
     int j = 0;
@@ -246,52 +251,60 @@ void Symbolic::build_skel(const CellPlan& cp, int kind, const std::vector<uint8_
     }
   }
   // rows: the front's DOFs, then the alive boundary DOFs of its cells not in
-  // the front, each once (first cell in corner order that holds it)
-  auto for_rows = [&](int f, auto&& emit) {
+  // the front, each once (first cell in corner order that holds it).
+  // emit(g, pos) gets the row's position in each of the front's cells
+  // (-1 = not in that cell); it is called with pos = nullptr when only the
+  // count is wanted, which skips the positions after the first cell.
+  auto for_rows = [&](int f, bool want_pos, auto&& emit) {
     const int64_t fk = keys[f];
-    for (int32_t g : members[f]) emit(g, -1, -1);
+    const int32_t* cx = &cellxyz[(size_t)f * ncp * 3];
+    int32_t pos[4];
+    for (int64_t u = moff[f]; u < moff[f + 1]; ++u) {
+      const int32_t g = mem[u];
+      if (want_pos)
+        for (int j = 0; j < ncp; ++j)
+          pos[j] = pos_in_cell(cp, g, cx[3 * j], cx[3 * j + 1], cx[3 * j + 2]);
+      emit(g, pos);
+    }
     for (int i = 0; i < ncp; ++i) {
-      int cell = sp.cells[(size_t)f * ncp + i];
-      int64_t o = cp.off[cell] + cp.p[cell], e = cp.off[cell + 1];
+      const int cell = sp.cells[(size_t)f * ncp + i];
+      const int64_t o = cp.off[cell] + cp.p[cell], e = cp.off[cell + 1];
       for (int64_t t = o; t < e; ++t) {
-        int32_t g = cp.dofs[t];
+        const int32_t g = cp.dofs[t];
         if (!alive[g]) continue;
         if (gkey(cp.packed[cp.slot[g]]) == fk) continue;
         bool earlier = false;
         for (int j = 0; j < i && !earlier; ++j) {
-          const int32_t* cj = &cellxyz[((size_t)f * ncp + j) * 3];
-          earlier = pos_in_cell(cp, g, cj[0], cj[1], cj[2]) >= 0;
+          pos[j] = pos_in_cell(cp, g, cx[3 * j], cx[3 * j + 1], cx[3 * j + 2]);
+          earlier = pos[j] >= 0;
         }
-        if (!earlier) emit(g, i, (int32_t)(t - o));
+        if (earlier) continue;
+        if (want_pos) {
+          pos[i] = (int32_t)(t - o);
+          for (int j = i + 1; j < ncp; ++j)
+            pos[j] = pos_in_cell(cp, g, cx[3 * j], cx[3 * j + 1], cx[3 * j + 2]);
+        }
+        emit(g, pos);
       }
     }
   };
   std::vector<int64_t> cnt(nf, 0);
   parallel_for(nf, [&](int64_t f) {
     int64_t c = 0;
-    for_rows((int)f, [&](int32_t, int, int32_t) { ++c; });
+    for_rows((int)f, false, [&](int32_t, const int32_t*) { ++c; });
     cnt[f] = c;
-    sp.nF[f] = (int32_t)members[f].size();
+    sp.nF[f] = (int32_t)(moff[f + 1] - moff[f]);
     sp.nR[f] = (int32_t)(c - sp.nF[f]);
   });
   sp.rowOff.assign(nf + 1, 0);
   for (int f = 0; f < nf; ++f) sp.rowOff[f + 1] = sp.rowOff[f] + cnt[f];
-  sp.rowDof.assign(sp.rowOff[nf], -1);
-  sp.rowPos.assign(sp.rowOff[nf] * ncp, -1);
+  sp.rowDof.resize(sp.rowOff[nf]);
+  sp.rowPos.resize(sp.rowOff[nf] * ncp);
   parallel_for(nf, [&](int64_t f) {
     int64_t r = sp.rowOff[f];
-    for_rows((int)f, [&](int32_t g, int src, int32_t srcpos) {
+    for_rows((int)f, true, [&](int32_t g, const int32_t* pos) {
       sp.rowDof[r] = g;
-      for (int i = 0; i < ncp; ++i) {
-        int32_t pos;
-        if (i == src) {
-          pos = srcpos;
-        } else {
-          const int32_t* ci = &cellxyz[((size_t)f * ncp + i) * 3];
-          pos = pos_in_cell(cp, g, ci[0], ci[1], ci[2]);
-        }
-        sp.rowPos[r * ncp + i] = pos;
-      }
+      for (int i = 0; i < ncp; ++i) sp.rowPos[r * ncp + i] = pos[i];
       ++r;
     });
   });

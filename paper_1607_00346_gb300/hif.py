@@ -34,7 +34,7 @@ class Grid(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("precision", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("pcg_tol", ctypes.c_double),
-                ("max_iter", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -262,10 +262,11 @@ class Handle:
 
 def factor(n: int, m: int, a, b=None, b_const: float = 0.0, eps: float = 1e-6,
            precision: int = PREC_FP64, pcg_tol: float = 1e-10, max_iter: int = 200,
-           stream=None) -> Handle:
+           stream=None, tensor_cores: bool = True) -> Handle:
     """hif_factor: a (and b) are n^3 float64 arrays, host or device."""
     g = Grid(n, m, 0)
-    o = default_options(eps=eps, precision=precision, pcg_tol=pcg_tol, max_iter=max_iter)
+    o = default_options(eps=eps, precision=precision, pcg_tol=pcg_tol, max_iter=max_iter,
+                        tensor_cores=int(bool(tensor_cores)))
     ap, _ka = _ptr(a)
     bp, _kb = _ptr(b)
     out = ctypes.c_void_p()

@@ -39,6 +39,7 @@ def test_host_only_entry_points(lib):
     hif.load()
     o = hif.default_options()
     assert o.eps == 1e-6 and o.pcg_tol == 1e-10 and o.max_iter == 200
+    assert o.tensor_cores == 1 and o.use_graphs == 1 and o.precision == hif.PREC_FP64
     assert hif.predict_bytes(64, 4) > 0
     assert hif.predict_bytes(60, 4) == 0        # 60 is not 4 * 2^L
     assert hif.load().hif_version().startswith(b"hif-gb300")
@@ -53,3 +54,10 @@ def test_invalid_grid_rejected_before_any_device_work():
     with pytest.raises(hif.HifError) as e:
         hif.factor(16, 4, np.ones(16 ** 3), eps=-1.0)
     assert e.value.status == 1
+    o = hif.default_options(tensor_cores=2)
+    g = hif.Grid(16, 4, 0)
+    out = ctypes.c_void_p()
+    a = np.ones(16 ** 3)
+    st = hif.load().hif_factor(ctypes.byref(g), a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               None, 0.0, ctypes.byref(o), None, ctypes.byref(out))
+    assert st == 1 and not out.value
