@@ -5,17 +5,23 @@
 // lo = tf32(x - hi), and A B^T ~= hi_A hi_B^T + hi_A lo_B^T + lo_A hi_B^T
 // (FP32 accumulation in tensor memory).
 //
-// Per CTA (128 threads, one 128 x 128 output tile):
-//   * the operand rows are staged in shared memory in the K-major, no-swizzle
-//     core-matrix layout (8 rows x 16 bytes per core matrix; LBO = 128 B
-//     between K-adjacent core matrices, SBO = 1024 B between 8-row groups);
+// Per CTA (256 threads, one 128 x 128 output tile):
+//   * K is walked in chunks of KC (16, or 32 for products with few rows):
+//     thread t loads one row of the chunk of A (t < 128) or of B (t >= 128)
+//     into registers two chunks ahead, splits it and stores it in the K-major,
+//     no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix;
+//     LBO = 128 B between K-adjacent core matrices, SBO = 8 KC bytes between
+//     8-row groups) of one of two shared buffers;
 //   * one thread issues tcgen05.mma.cta_group::1.kind::tf32 (M = N = 128,
 //     K = 8 per instruction) into a 128-column TMEM accumulator and commits
-//     to an mbarrier; the wait on it has an iteration limit (on expiry the
-//     kernel records FLAG_TIMEOUT, frees its TMEM and returns);
-//   * four warps read the accumulator back with tcgen05.ld (warp w owns TMEM
-//     lanes 32w..32w+31 = tile rows) and write alpha times it to C (added to
-//     C when beta = 1).
+//     to the buffer's mbarrier; the wait on it has an iteration limit (on
+//     expiry the kernel records FLAG_TIMEOUT, frees its TMEM and returns);
+//   * with KC = 16 a CTA holds 64 KB of shared memory and three CTAs share an
+//     SM (384 of its 512 TMEM columns), so one CTA's loads overlap the others'
+//     products;
+//   * eight warps read the accumulator back with tcgen05.ld (warp w owns TMEM
+//     lanes 32 (w % 4) .. = tile rows, and half w / 4 of the columns) and
+//     write alpha times it to C (added to C when beta = 1).
 #include <stdint.h>
 
 #include <algorithm>
@@ -29,9 +35,7 @@ namespace {
 
 constexpr int TC_M = 128;        // tile rows (TMEM lanes)
 constexpr int TC_N = 128;        // tile columns (TMEM columns)
-constexpr int TC_KC = 32;        // K elements staged per chunk
 constexpr int TC_THREADS = 256;   // 128 stage A rows, 128 stage B rows
-constexpr int TILE_BYTES = TC_M * TC_KC * 4;   // one operand, one split: 16 KB
 constexpr long long WAIT_LIMIT = 20000000;     // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -60,9 +64,10 @@ __device__ __forceinline__ float tf32_hi(float x) {
   return __uint_as_float(r);
 }
 
-// byte offset of element (row, k) of a TC_M x TC_KC K-major operand
+// byte offset of element (row, k) of a TC_M x KC K-major operand
+template <int KC>
 __device__ __forceinline__ int core_off(int row, int k) {
-  return ((row >> 3) * (TC_KC / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4;
+  return ((row >> 3) * (KC / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4;
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
@@ -76,13 +81,14 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b,
 // C (M x N) = beta C + alpha op(A) op(B) for a batch of problems (GemmOp
 // semantics: op(A)[r][k] = transA ? A[k + r lda] : A[r + k lda],
 // op(B)[k][c] = transB ? B[c + k ldb] : B[k + c ldb]).  Operands are read in
-// K chunks of TC_KC, split into TF32 hi/lo parts and staged in one of two
+// K chunks of KC, split into TF32 hi/lo parts and staged in one of two
 // shared-memory buffers while the tensor cores work on the other.  beta is 0
 // or 1.  `lower` skips tiles strictly above the diagonal of a symmetric C.
-__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmOp* __restrict__ ops,
-                                                        const float* __restrict__ Ab,
-                                                        const float* __restrict__ Bb, float* Cb,
-                                                        int* flags) {
+template <int KC>
+__global__ void __launch_bounds__(TC_THREADS, KC == 16 ? 3 : 1)
+    k_gemm_tc(const GemmOp* __restrict__ ops, const float* __restrict__ Ab,
+              const float* __restrict__ Bb, float* Cb, int* flags) {
+  constexpr int TILE_BYTES = TC_M * KC * 4;   // one operand, one split
   const GemmOp o = ops[blockIdx.y];
   const int tm_n = (o.m + TC_M - 1) / TC_M, tn_n = (o.n + TC_N - 1) / TC_N;
   if ((int)blockIdx.x >= tm_n * tn_n) return;
@@ -115,7 +121,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmOp* __restrict
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   const uint32_t tmem = s_tmem;
   const uint32_t idesc = idesc_tf32(TC_M, TC_N);
-  const int nchunk = (o.k + TC_KC - 1) / TC_KC;
+  const int nchunk = (o.k + KC - 1) / KC;
   uint32_t phase[2] = {0u, 0u};
   bool ok = true;
 
@@ -135,40 +141,37 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmOp* __restrict
     return done != 0;
   };
 
-  for (int ch = 0; ch < nchunk; ++ch) {
+  // staging registers of two chunks: chunk c lives in va (c even) or vb (c
+  // odd); the loads of chunk c + 2 are issued as soon as chunk c is stored
+  const bool isA = tid < TC_M;
+  const int row = tid % TC_M;
+  const float* X = isA ? A : B;
+  const int base = isA ? rb : cb;
+  const int lim = isA ? o.m : o.n;
+  const int64_t ldx = isA ? o.lda : o.ldb;
+  const bool kfast = isA ? (o.transA != 0) : (o.transB == 0);   // k contiguous in memory
+  const bool rin = base + row < lim;
+  auto load = [&](int ch, float (&v)[KC]) {
+    const int k0 = ch * KC;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      const int kk = k0 + k;
+      v[k] = (rin && kk < o.k) ? (kfast ? X[(int64_t)kk + (int64_t)(base + row) * ldx]
+                                        : X[(int64_t)(base + row) + (int64_t)kk * ldx])
+                               : 0.f;
+    }
+  };
+  auto step = [&](int ch, float (&v)[KC]) -> bool {
     const int s = ch & 1;
     unsigned char* buf = smem + s * 4 * TILE_BYTES;
     if (ch >= 2 && !wait_buf(s)) s_fail = 1;   // buffer s is free again
     __syncthreads();
-    if (s_fail) {
-      ok = false;
-      break;
-    }
-    const int k0 = ch * TC_KC;
+    if (s_fail) return false;
     {
-      // stage: thread t loads the TC_KC values of one row of A (t < 128) or
-      // of B (t >= 128), splits them and stores 16-byte groups of 4 k
-      const bool isA = tid < TC_M;
-      const int row = tid % TC_M;
-      const float* X = isA ? A : B;
-      const int base = isA ? rb : cb;
-      const int lim = isA ? o.m : o.n;
-      const int ldx = isA ? o.lda : o.ldb;
-      const bool kfast = isA ? (o.transA != 0) : (o.transB == 0);   // k contiguous in memory
-      float v[TC_KC];
-      const bool rin = base + row < lim;
-#pragma unroll
-      for (int k = 0; k < TC_KC; ++k) {
-        const int kk = k0 + k;
-        v[k] = (rin && kk < o.k)
-                   ? (kfast ? X[(int64_t)kk + (int64_t)(base + row) * ldx]
-                            : X[(int64_t)(base + row) + (int64_t)kk * ldx])
-                   : 0.f;
-      }
       unsigned char* hi = buf + (isA ? 0 : 2 * TILE_BYTES);
       unsigned char* lo = hi + TILE_BYTES;
 #pragma unroll
-      for (int k = 0; k < TC_KC; k += 4) {
+      for (int k = 0; k < KC; k += 4) {
         float4 h, l;
         h.x = tf32_hi(v[k]);
         h.y = tf32_hi(v[k + 1]);
@@ -178,28 +181,38 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmOp* __restrict
         l.y = tf32_hi(v[k + 1] - h.y);
         l.z = tf32_hi(v[k + 2] - h.z);
         l.w = tf32_hi(v[k + 3] - h.w);
-        const int off = core_off(row, k);
+        const int off = core_off<KC>(row, k);
         *reinterpret_cast<float4*>(hi + off) = h;
         *reinterpret_cast<float4*>(lo + off) = l;
       }
     }
+    if (ch + 2 < nchunk) load(ch + 2, v);
     asm volatile("fence.proxy.async.shared::cta;\n");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;\n");
       const uint32_t ah = smem_u32(buf), al = ah + TILE_BYTES, bh = ah + 2 * TILE_BYTES,
                      bl = ah + 3 * TILE_BYTES;
-      for (int ks = 0; ks < TC_KC / 8; ++ks) {
+      for (int ks = 0; ks < KC / 8; ++ks) {
         const uint32_t off = ks * 256;   // two core matrices of K per instruction
         const uint32_t acc0 = (ch > 0 || ks > 0) ? 1u : 0u;
-        mma_tf32(tmem, sdesc(ah + off, 128, 1024), sdesc(bh + off, 128, 1024), idesc, acc0);
-        mma_tf32(tmem, sdesc(ah + off, 128, 1024), sdesc(bl + off, 128, 1024), idesc, 1u);
-        mma_tf32(tmem, sdesc(al + off, 128, 1024), sdesc(bh + off, 128, 1024), idesc, 1u);
+        constexpr uint32_t SBO = KC * 32;   // 8 rows x KC floats
+        mma_tf32(tmem, sdesc(ah + off, 128, SBO), sdesc(bh + off, 128, SBO), idesc, acc0);
+        mma_tf32(tmem, sdesc(ah + off, 128, SBO), sdesc(bl + off, 128, SBO), idesc, 1u);
+        mma_tf32(tmem, sdesc(al + off, 128, SBO), sdesc(bh + off, 128, SBO), idesc, 1u);
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
               smem_u32(&mbar[s])));
     }
+    return true;
+  };
+  float va[KC], vb[KC];
+  if (nchunk > 0) load(0, va);
+  if (nchunk > 1) load(1, vb);
+  for (int ch = 0; ch < nchunk && ok; ch += 2) {
+    if (!step(ch, va)) ok = false;
+    else if (ch + 1 < nchunk && !step(ch + 1, vb)) ok = false;
   }
   // the last one or two chunks are still in flight
   if (ok) {
@@ -253,23 +266,31 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmOp* __restrict
 void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Abase,
              const float* Bbase, float* Cbase, int* d_flags, cudaStream_t st) {
   if (nops == 0) return;
-  int mt = 1;
+  int mt = 1, mmax = 0;
   double fl = 0;
   for (int i = 0; i < nops; ++i) {
     mt = std::max(mt, ceil_div(h_ops[i].m, TC_M) * ceil_div(h_ops[i].n, TC_N));
+    mmax = std::max(mmax, h_ops[i].m);
     fl += 2.0 * h_ops[i].m * (double)h_ops[i].n * h_ops[i].k * (h_ops[i].lower ? 0.5 : 1.0);
   }
-  const size_t smem = 2 * 4 * TILE_BYTES;
+  // few rows (one tile, mostly padding): fewer, longer chunks
+  const bool wide = mmax <= 64;
+  const size_t smem = 2 * 4 * (size_t)TC_M * (wide ? 32 : 16) * 4;
   static bool attr = false;
   if (!attr) {
-    HIF_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      2 * 4 * TC_M * 16 * 4));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      2 * 4 * TC_M * 32 * 4));
     attr = true;
   }
   ProfScope ps("gemm_tc", st, fl, 0.0);
   for (int f0 = 0; f0 < nops; f0 += 65535) {
     const int nb = std::min(65535, nops - f0);
-    k_gemm_tc<<<dim3(mt, nb), TC_THREADS, smem, st>>>(d_ops + f0, Abase, Bbase, Cbase, d_flags);
+    if (wide)
+      k_gemm_tc<32><<<dim3(mt, nb), TC_THREADS, smem, st>>>(d_ops + f0, Abase, Bbase, Cbase, d_flags);
+    else
+      k_gemm_tc<16><<<dim3(mt, nb), TC_THREADS, smem, st>>>(d_ops + f0, Abase, Bbase, Cbase, d_flags);
     HIF_CHECK_LAUNCH();
   }
 }
