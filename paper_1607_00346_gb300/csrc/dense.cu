@@ -212,69 +212,6 @@ __global__ void __launch_bounds__(NB) k_trtri_diag(const DFront* __restrict__ fr
   }
 }
 
-// ---- block row i of Linv: Z_ij = -Z_ii sum_{k=j}^{i-1} L_ik Z_kj  (j < i) -------
-template <typename T>
-__global__ void __launch_bounds__(256) k_trtri_row(const DFront* __restrict__ fr, const T* Kar,
-                                                   T* Par, int bi) {
-  const DFront d = fr[blockIdx.y];
-  const int i0 = bi * NB;
-  if (i0 >= d.p) return;
-  const int bj = blockIdx.x;
-  if (bj >= bi) return;
-  const int ib = min(NB, d.p - i0);
-  const int64_t n = d.ld;
-  const T* K = Kar + d.K;
-  T* P = Par + d.P;
-  __shared__ T As[KC][TILE + 4];
-  __shared__ T Bs[KC][TILE + 4];
-  __shared__ T Ss[TILE][TILE + 4];
-  TileAcc<T> acc;
-  acc.zero();
-  const int j0 = bj * NB;
-  for (int kb = bj; kb < bi; ++kb) {
-    const int k0b = kb * NB;
-    for (int k0 = 0; k0 < NB; k0 += KC) {
-      for (int e = threadIdx.x; e < KC * TILE; e += 256) {
-        int rr = e % TILE, kk = e / TILE;
-        // A = L_ik (rows of block i, columns of block k) read from K
-        As[kk][rr] = rr < ib ? K[(int64_t)(i0 + rr) + (int64_t)(k0b + k0 + kk) * n] : T(0);
-        // B = Z_kj stored transposed: Bs[kk][c] = Z_kj[k0+kk][c]
-        Bs[kk][rr] = P[(int64_t)(k0b + k0 + kk) + (int64_t)(j0 + rr) * n];
-      }
-      __syncthreads();
-      acc.mma(As, Bs, KC);
-      __syncthreads();
-    }
-  }
-  // S -> shared, then Z_ij = -Z_ii S
-  const int tr = (threadIdx.x % 16) * 4, tc = (threadIdx.x / 16) * 4;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) Ss[tr + i][tc + j] = acc.v[i][j];
-  __syncthreads();
-  TileAcc<T> out;
-  out.zero();
-  for (int k0 = 0; k0 < NB; k0 += KC) {
-    for (int e = threadIdx.x; e < KC * TILE; e += 256) {
-      int rr = e % TILE, kk = e / TILE;
-      int kcol = k0 + kk;
-      As[kk][rr] = (rr < ib && kcol < ib && rr >= kcol)
-                       ? P[(int64_t)(i0 + rr) + (int64_t)(i0 + kcol) * n] : T(0);
-      Bs[kk][rr] = Ss[kcol][rr];
-    }
-    __syncthreads();
-    out.mma(As, Bs, KC);
-    __syncthreads();
-  }
-#pragma unroll
-  for (int j = 0; j < 4; ++j)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = tr + i;
-      if (r < ib) P[(int64_t)(i0 + r) + (int64_t)(j0 + tc + j) * n] = -out.v[i][j];
-    }
-}
 
 // ---- generic batched GEMM ------------------------------------------------------
 template <typename T>
@@ -466,7 +403,10 @@ void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront
     }
   }
   HIF_CUDA_TRY(cudaFreeAsync(d_lead, st));
-  // 2. Linv = L^{-1}: diagonal blocks, then block rows
+  // 2. Linv = L^{-1}: invert the NB x NB diagonal blocks, then merge
+  //    neighbouring inverted blocks pairwise up a binary tree of widths
+  //    s = NB, 2 NB, 4 NB, ...:  inv([A 0; B C]) = [A^-1 0; -C^-1 B A^-1  C^-1]
+  //    (two batched products per width: T = B A^-1, then -C^-1 T)
   const int nblk = ceil_div(pmax, NB);
   for (int f0 = 0; f0 < nfront; f0 += MAX_GRID_Y) {
     const int nb = std::min(MAX_GRID_Y, nfront - f0);
@@ -477,17 +417,45 @@ void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront
     k_trtri_diag<T><<<dim3(nblk, nb), NB, 0, st>>>(d_fronts + f0, Parena);
     HIF_CHECK_LAUNCH();
   }
-  for (int bi = 1; bi < nblk; ++bi) {
-    int nact = 0;
-    while (nact < nfront && h_fronts[nact].p > bi * NB) ++nact;
-    for (int f0 = 0; f0 < nact; f0 += MAX_GRID_Y) {
-      const int nb = std::min(MAX_GRID_Y, nact - f0);
-      double fl = 0;
-      if (prof_enabled()) fl = (double)nb * (bi * (bi + 1) / 2.0 + bi) * 2.0 * NB * NB * NB;
-      ProfScope ps("trtri_row", st, fl, 0.0);
-      k_trtri_row<T><<<dim3(bi, nb), 256, 0, st>>>(d_fronts + f0, Karena, Parena, bi);
-      HIF_CHECK_LAUNCH();
+  for (int s = NB; s < pmax; s *= 2) {
+    std::vector<GemmOp> tops, rops;
+    int64_t scr = 0;
+    for (int f = 0; f < nfront && h_fronts[f].p > s; ++f) {
+      const DFront& h = h_fronts[f];
+      const int ld = h.ld;
+      for (int i0 = 0; i0 + s < h.p; i0 += 2 * s) {
+        const int rs = std::min(2 * s, h.p - i0) - s;   // rows of the right part
+        const int64_t boff = (i0 + s) + (int64_t)i0 * ld;
+        const int64_t aoff = i0 + (int64_t)i0 * ld;
+        const int64_t coff = (i0 + s) + (int64_t)(i0 + s) * ld;
+        tops.push_back(GemmOp{h.K + boff, h.P + aoff, scr, rs, s, s, ld, ld, rs, 0, 0, 1.f, 0.f, 0, 0});
+        rops.push_back(GemmOp{h.P + coff, scr, h.P + boff, rs, s, rs, ld, rs, ld, 0, 0, -1.f, 0.f, 0, 0});
+        scr += (int64_t)rs * s;
+      }
     }
+    if (tops.empty()) break;
+    const size_t cnt = tops.size();
+    GemmOp* d_ops = nullptr;
+    T* d_scr = nullptr;
+    HIF_CUDA_TRY(cudaMallocAsync(&d_ops, sizeof(GemmOp) * 2 * cnt, st));
+    HIF_CUDA_TRY(cudaMallocAsync(&d_scr, sizeof(T) * scr, st));
+    HIF_CUDA_TRY(cudaMemcpyAsync(d_ops, tops.data(), sizeof(GemmOp) * cnt, cudaMemcpyHostToDevice, st));
+    HIF_CUDA_TRY(cudaMemcpyAsync(d_ops + cnt, rops.data(), sizeof(GemmOp) * cnt,
+                                 cudaMemcpyHostToDevice, st));
+    if constexpr (std::is_same<T, float>::value) {
+      if (use_tc && s >= 128) {
+        gemm_tc(d_ops, tops.data(), (int)cnt, Karena, Parena, d_scr, d_flags, st, "trtri_merge");
+        gemm_tc(d_ops + cnt, rops.data(), (int)cnt, Parena, d_scr, Parena, d_flags, st, "trtri_merge");
+      } else {
+        gemm_batched<T>(d_ops, tops.data(), (int)cnt, Karena, Parena, d_scr, st, "trtri_merge");
+        gemm_batched<T>(d_ops + cnt, rops.data(), (int)cnt, Parena, d_scr, Parena, st, "trtri_merge");
+      }
+    } else {
+      gemm_batched<T>(d_ops, tops.data(), (int)cnt, Karena, Parena, d_scr, st, "trtri_merge");
+      gemm_batched<T>(d_ops + cnt, rops.data(), (int)cnt, Parena, d_scr, Parena, st, "trtri_merge");
+    }
+    HIF_CUDA_TRY(cudaFreeAsync(d_scr, st));
+    HIF_CUDA_TRY(cudaFreeAsync(d_ops, st));
   }
   // 3. X^T = A_NI L^{-T} (into the panel below Linv) and 4. the Schur
   //    complement A_NN -= X^T X (lower tiles), each one deep product per front
@@ -527,7 +495,7 @@ void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront
 
 template <typename T>
 void gemm_batched(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const T* Abase,
-                  const T* Bbase, T* Cbase, cudaStream_t st) {
+                  const T* Bbase, T* Cbase, cudaStream_t st, const char* name) {
   if (nops == 0) return;
   int mt = 1;
   for (int i = 0; i < nops; ++i)
@@ -537,7 +505,7 @@ void gemm_batched(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const T* A
     double fl = 0;
     if (prof_enabled())
       for (int i = f0; i < f0 + nb; ++i) fl += 2.0 * h_ops[i].m * (double)h_ops[i].n * h_ops[i].k;
-    ProfScope ps("gemm_batched", st, fl, 0.0);
+    ProfScope ps(name, st, fl, 0.0);
     k_gemm<T><<<dim3(mt, nb), 256, 0, st>>>(d_ops + f0, Abase, Bbase, Cbase);
     HIF_CHECK_LAUNCH();
   }
@@ -584,7 +552,7 @@ void gemv_batched(const GemvOp* d_ops, const GemvOp* h_ops, int nops, int trans,
   template void partial_cholesky<T>(const DFront*, const DFront*, int, T*, T*, int*, bool,  \
                                     cudaStream_t);                                           \
   template void gemm_batched<T>(const GemmOp*, const GemmOp*, int, const T*, const T*, T*,  \
-                                cudaStream_t);                                               \
+                                cudaStream_t, const char*);                                  \
   template void gemv_batched<T>(const GemvOp*, const GemvOp*, int, int, const T*, T*,       \
                                 int64_t, int, cudaStream_t);
 HIF_INST(float)

@@ -19,13 +19,15 @@ void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront
 
 // C = beta C + alpha op(A) op(B) on the tensor cores (tcgen05, 3xTF32; see
 // tc.cu): GemmOp semantics as gemm_batched, beta 0 or 1, FP32 data.
+// `name` labels the launches in the kernel profile.
 void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Abase,
-             const float* Bbase, float* Cbase, int* d_flags, cudaStream_t st);
+             const float* Bbase, float* Cbase, int* d_flags, cudaStream_t st,
+             const char* name = "gemm_tc");
 
 // C = beta C + alpha op(A) op(B) for a batch of independent problems.
 template <typename T>
 void gemm_batched(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const T* Abase,
-                  const T* Bbase, T* Cbase, cudaStream_t st);
+                  const T* Bbase, T* Cbase, cudaStream_t st, const char* name = "gemm_batched");
 
 // y = alpha op(M) x (+ y), batched (see GemvOp).  trans = 0: y (rows) = M x;
 // trans = 1: y (cols) = M^T x.  nrhs vectors with stride `vstride` in `work`.

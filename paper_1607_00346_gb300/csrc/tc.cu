@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(TC_THREADS, KC == 16 ? 3 : 1)
 }  // namespace
 
 void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Abase,
-             const float* Bbase, float* Cbase, int* d_flags, cudaStream_t st) {
+             const float* Bbase, float* Cbase, int* d_flags, cudaStream_t st, const char* name) {
   if (nops == 0) return;
   int mt = 1, mmax = 0;
   double fl = 0;
@@ -284,7 +284,7 @@ void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Ab
                                       2 * 4 * TC_M * 32 * 4));
     attr = true;
   }
-  ProfScope ps("gemm_tc", st, fl, 0.0);
+  ProfScope ps(name, st, fl, 0.0);
   for (int f0 = 0; f0 < nops; f0 += 65535) {
     const int nb = std::min(65535, nops - f0);
     if (wide)
