@@ -636,6 +636,22 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
       d.idld = d.nF;
     }
   }
+  if (tr_.on) {
+    for (int g = 0; g < 2; ++g) {
+      if (sel[g].empty()) continue;
+      int64_t mxF = 0, mxM = 0, sF = 0, sM = 0;
+      for (int f : sel[g]) {
+        mxF = std::max<int64_t>(mxF, sd[f].nF);
+        mxM = std::max<int64_t>(mxM, sd[f].idm);
+        sF += sd[f].nF;
+        sM += sd[f].idm;
+      }
+      std::fprintf(stderr, "[hif] level %d %s ID%s: %zu fronts, nF max %lld mean %.1f, rows max %lld mean %.1f\n",
+                   level_, kind == 1 ? "faces" : "edges", g ? " on R" : "", sel[g].size(),
+                   (long long)mxF, (double)sF / sel[g].size(), (long long)mxM,
+                   (double)sM / sel[g].size());
+    }
+  }
   std::vector<SkelDesc> sub[2];
   DevBuf sub_d[2];
   for (int g = 0; g < 2; ++g) {

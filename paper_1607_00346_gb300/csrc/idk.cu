@@ -327,6 +327,179 @@ __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int*
   }
 }
 
+// ---- fronts whose ID matrix fits in shared memory ---------------------------------
+// One CTA per front: the idm x nF matrix is copied into shared memory and
+// factored there by unblocked Householder QR with column pivoting.  Columns
+// stay in place (ties go to the lowest column index, as in the cluster
+// kernel).  The pass that applies step i's reflector to a column also
+// recomputes, from the updated entries, the column's norm below row i + 1
+// and its row i + 1 entry, and every warp keeps the best candidate among its
+// columns; so each step needs a single barrier, and the norms involve no
+// downdating (no cancellation), which lets them run in the factor precision
+// (FP64 arithmetic is a small fraction of the FP32 rate on this part).
+constexpr int SMEM_ID_MAX = 220 * 1024;   // dynamic shared memory per CTA, bytes
+
+__host__ __device__ inline size_t smem_id_bytes(int m, int nF, int tsize) {
+  // tail norms (T), R diagonal (T), done flags (int) + the matrix
+  return (((size_t)nF * (2 * tsize + 4) + 15) / 16) * 16 + (size_t)m * nF * tsize;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_cpqr_smem(SkelDesc* fr, const int* __restrict__ list,
+                                                    const T* __restrict__ Gar, int32_t* permAr,
+                                                    T* Far, double eps) {
+  const int fidx = list[blockIdx.x];
+  SkelDesc& fref = fr[fidx];
+  const SkelDesc f = fref;
+  const int nF = f.nF, m = f.idm, ldg = f.idld;
+  const T* Mg = Gar + f.idoff;
+  int32_t* pv = permAr + f.perm;
+  T* Tm = Far + f.Tm;
+  extern __shared__ __align__(16) unsigned char sm[];
+  T* tail = reinterpret_cast<T*>(sm);          // |a_c[i+1:]|^2 before step i
+  T* rdiag = tail + nF;                        // R_ii
+  int* done = reinterpret_cast<int*>(rdiag + nF);
+  T* A = reinterpret_cast<T*>(sm + ((size_t)nF * (2 * sizeof(T) + 4) + 15) / 16 * 16);
+  // per-warp candidates for the next pivot, |a_c[i:]|^2 and the column;
+  // double-buffered by step parity so that one barrier per step suffices
+  __shared__ T s_cv[2][32];
+  __shared__ int s_ci[2][32];
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid / 32, lane = tid % 32, nw = nt / 32;
+
+  // copy, and the norms for step 0
+  {
+    T bv = T(-1);
+    int bc = nF;
+    for (int c = warp; c < nF; c += nw) {
+      const T* src = Mg + (int64_t)c * ldg;
+      T* dst = A + (int64_t)c * m;
+      T s = T(0), head = T(0);
+      for (int r = lane; r < m; r += 32) {
+        const T x = src[r];
+        dst[r] = x;
+        if (r == 0) head = x;
+        else s = fma(x, x, s);
+      }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      head = __shfl_sync(0xffffffffu, head, 0);
+      const T full = fma(head, head, s);
+      if (lane == 0) {
+        tail[c] = s;
+        done[c] = 0;
+      }
+      if (full > bv) {
+        bv = full;
+        bc = c;
+      }
+    }
+    if (lane == 0) {
+      s_cv[0][warp] = bv;
+      s_ci[0][warp] = bc;
+    }
+  }
+  __syncthreads();
+  const int kmax = min(m, nF);
+  int k = kmax;
+  T r11 = T(0);
+  for (int i = 0; i < kmax; ++i) {
+    // pivot: the best of the warps' candidates (largest norm, lowest column)
+    const int cur = i & 1;
+    T bv = s_cv[cur][0];
+    int p = s_ci[cur][0];
+    for (int w = 1; w < nw; ++w) {
+      const T v = s_cv[cur][w];
+      const int c = s_ci[cur][w];
+      if (v > bv || (v == bv && c < p)) {
+        bv = v;
+        p = c;
+      }
+    }
+    const T nv = sqrt(fmax(bv, T(0)));
+    if (i == 0) r11 = nv;
+    if (p >= nF || (i == 0 ? nv == T(0) : !((double)nv > eps * (double)r11))) {
+      k = i;
+      break;
+    }
+    // reflector of column p over rows i..m-1: v = (x0 - alpha, a_p[i+1:])
+    const T* ap = A + (int64_t)p * m;
+    const T x0 = ap[i], tl = tail[p];
+    const T nx = sqrt(fma(x0, x0, tl));
+    const T alpha = x0 >= T(0) ? -nx : nx;
+    const T v0 = x0 - alpha;
+    const T vtv = fma(v0, v0, tl);
+    const T tau = vtv > T(0) ? T(2) / vtv : T(0);
+    if (tid == 0) {
+      rdiag[i] = alpha;
+      pv[i] = p;
+    }
+    // the other remaining columns: a_c -= tau v (v^T a_c)
+    T cbv = T(-1);
+    int cbc = nF;
+    for (int c = warp; c < nF; c += nw) {
+      if (c == p || done[c]) continue;
+      T* ac = A + (int64_t)c * m;
+      T w0 = T(0), w1 = T(0);
+      int r = i + 1 + lane;
+      for (; r + 32 < m; r += 64) {
+        w0 = fma(ap[r], ac[r], w0);
+        w1 = fma(ap[r + 32], ac[r + 32], w1);
+      }
+      if (r < m) w0 = fma(ap[r], ac[r], w0);
+      T w = w0 + w1;
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      w = fma(v0, ac[i], w);
+      const T tw = tau * w;
+      T s = T(0), head = T(0);
+      for (int r2 = i + 1 + lane; r2 < m; r2 += 32) {
+        const T x = fma(-ap[r2], tw, ac[r2]);
+        ac[r2] = x;
+        if (r2 == i + 1) head = x;
+        else s = fma(x, x, s);
+      }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      head = __shfl_sync(0xffffffffu, head, 0);
+      const T full = fma(head, head, s);
+      __syncwarp();
+      if (lane == 0) {
+        ac[i] = fma(-v0, tw, ac[i]);   // R_ic
+        tail[c] = s;
+      }
+      if (full > cbv) {
+        cbv = full;
+        cbc = c;
+      }
+    }
+    if (lane == 0) {
+      s_cv[cur ^ 1][warp] = cbv;
+      s_ci[cur ^ 1][warp] = cbc;
+    }
+    if (tid == 0) done[p] = 1;
+    __syncthreads();
+  }
+  if (tid == 0) fref.k = k;
+  // T = R11^{-1} R12 (k x (nF-k), ld = k): one warp per redundant column,
+  // back substitution in place in shared memory; R_{l,j} sits in row l of
+  // column pv[j], R_jj in rdiag[j]; redundant columns follow the pivots in
+  // increasing column order
+  for (int c = warp; c < nF; c += nw) {
+    if (done[c]) continue;
+    int rk = 0;
+    for (int q2 = 0; q2 < c; ++q2) rk += done[q2] == 0;
+    T* b = A + (int64_t)c * m;
+    for (int ii = k - 1; ii >= 0; --ii) {
+      const T xi = b[ii] / rdiag[ii];
+      const T* rc = A + (int64_t)pv[ii] * m;
+      __syncwarp();
+      if (lane == 0) b[ii] = xi;
+      for (int r = lane; r < ii; r += 32) b[r] = fma(-xi, rc[r], b[r]);
+      __syncwarp();
+    }
+    T* out = Tm + (int64_t)rk * k;
+    for (int r = lane; r < k; r += 32) out[r] = b[r];
+    if (lane == 0) pv[k + rk] = c;
+  }
+}
+
 }  // namespace
 
 size_t id_fscratch_elems(int64_t total_front_dofs) { return (size_t)total_front_dofs * NBK; }
@@ -339,15 +512,55 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
   int nsm = 0, dev = 0;
   HIF_CUDA_TRY(cudaGetDevice(&dev));
   HIF_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  // fronts whose matrix fits in shared memory: one CTA each, in three size
+  // classes (128, 256 or 1024 threads; dynamic shared memory of the class's
+  // largest front)
+  static bool smem_attr[2] = {false, false};
+  if (!smem_attr[sizeof(T) == 8]) {
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_cpqr_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      SMEM_ID_MAX));
+    smem_attr[sizeof(T) == 8] = true;
+  }
+  constexpr size_t class_max[3] = {16 * 1024, 64 * 1024, (size_t)SMEM_ID_MAX};
+  constexpr int class_threads[3] = {128, 256, 1024};
+  std::vector<int> small[3], rest;
+  size_t small_bytes[3] = {0, 0, 0};
+  for (int f = 0; f < nf; ++f) {
+    const size_t by = smem_id_bytes(h_f[f].idm, h_f[f].nF, (int)sizeof(T));
+    int cl = 0;
+    while (cl < 3 && by > class_max[cl]) ++cl;
+    if (cl == 3) {
+      rest.push_back(f);
+    } else {
+      small[cl].push_back(f);
+      small_bytes[cl] = std::max(small_bytes[cl], by);
+    }
+  }
+  for (int cl = 0; cl < 3; ++cl) {
+    if (small[cl].empty()) continue;
+    int* d_list = nullptr;
+    HIF_CUDA_TRY(cudaMallocAsync(&d_list, sizeof(int) * small[cl].size(), st));
+    HIF_CUDA_TRY(cudaMemcpyAsync(d_list, small[cl].data(), sizeof(int) * small[cl].size(),
+                                 cudaMemcpyHostToDevice, st));
+    {
+      static const char* names[3] = {"id_cpqr_smem_c0", "id_cpqr_smem_c1", "id_cpqr_smem_c2"};
+      ProfScope ps(names[cl], st);
+      k_cpqr_smem<T><<<(unsigned)small[cl].size(), class_threads[cl], small_bytes[cl], st>>>(
+          d_f, d_list, Garena, perm, Farena, eps);
+      HIF_CHECK_LAUNCH();
+    }
+    HIF_CUDA_TRY(cudaFreeAsync(d_list, st));
+  }
+  if (rest.empty()) return;
   // cluster size: small fronts get one CTA; large fronts (work per step
   // nF x nR above ~1e6) spread their columns over as many SMs as the batch
   // leaves free (two CTAs per SM), up to 16, so that one launch fills the GPU
   std::vector<std::vector<int>> bucket(17);
   int nbig = 0;
-  for (int f = 0; f < nf; ++f)
+  for (int f : rest)
     if ((double)h_f[f].nF * (h_f[f].nF + h_f[f].idm) > 1.0e6) ++nbig;
   const int cs_big = std::max(1, std::min(16, 2 * nsm / std::max(1, nbig)));
-  for (int f = 0; f < nf; ++f) {
+  for (int f : rest) {
     const double work = (double)h_f[f].nF * (h_f[f].nF + h_f[f].idm);
     int cs = work > 1.0e6 ? cs_big : 1;
     cs = std::min(cs, std::max(1, h_f[f].nF / 8));   // at least 8 columns per CTA
