@@ -43,6 +43,17 @@ FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_ALU_PEAK_TFLOPS = 1.25
 
 
+# roofline of each profiled kernel: tensor-core products, FMA-unit dense
+# algebra, or HBM streams (the ID's trailing-matrix passes and the apply's
+# mat-vecs read each entry once per step / per sweep)
+KERNEL_BOUND = {
+    "gemm_tc": "tensor",
+    "id_cpqr": "hbm", "id_rowreduce_panel": "hbm", "apply_gemv_n": "hbm", "apply_gemv_t": "hbm",
+    "skel_gather": "hbm", "merge_children": "hbm", "spmv": "hbm", "residual": "hbm",
+    "chol_panel": "alu", "chol_trailing_update": "alu", "gemm_batched": "alu",
+    "trtri_merge": "alu", "id_cpqr_smem": "alu",
+}
+
 # nominal dense TF32 / bf16 tensor ratio (1.1 / 2.25 PFLOP/s)
 TF32_PER_BF16 = 1.1 / 2.25
 
@@ -345,29 +356,36 @@ def main():
 
     # roofline of the dominant kernel (largest share of the timed region)
     hbm_peak, bf16_peak, peak_src = _peaks()
+    total_prof_s = max(sum(p["seconds"] for p in prof), 1e-12)
+
+    def roofline(k):
+        per_launch_s = k["seconds"] / max(k["launches"], 1)
+        bound = KERNEL_BOUND.get(k["name"], "alu" if k["flops"] > 0 else "hbm")
+        if bound == "tensor":
+            # algorithmic flops 2mnk of the products (the 3xTF32 split issues
+            # three TF32 products per algorithmic one; that cost is the kernel's)
+            peak = bf16_peak * TF32_PER_BF16
+            ach = k["flops"] / max(k["launches"], 1) / per_launch_s / 1e12
+            src = f"{peak_src} bf16_tflops x nominal tf32/bf16 ratio"
+            unit = "TFLOP/s"
+        elif bound == "alu":
+            peak = FP32_ALU_PEAK_TFLOPS if prec == hif.PREC_FP32 else FP64_ALU_PEAK_TFLOPS
+            ach = k["flops"] / max(k["launches"], 1) / per_launch_s / 1e12
+            src = "unit counts x max clock"
+            unit = "TFLOP/s"
+        else:
+            peak = hbm_peak
+            ach = k["bytes"] / max(k["launches"], 1) / per_launch_s / 1e9
+            src = f"{peak_src} hbm_gbs"
+            unit = "GB/s"
+        return {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                "traffic": None, "kernel": k["name"], "peak_source": src,
+                "share": k["seconds"] / total_prof_s}
+
     dom = max(prof, key=lambda p: p["seconds"])
     launches = sum(p["launches"] for p in prof)
-    per_launch_s = dom["seconds"] / max(dom["launches"], 1)
-    if dom["name"] == "gemm_tc":
-        # algorithmic flops 2mnk of the products (the 3xTF32 split issues three
-        # TF32 products per algorithmic one; that cost is the kernel's)
-        peak = bf16_peak * TF32_PER_BF16
-        ach = dom["flops"] / max(dom["launches"], 1) / per_launch_s / 1e12
-        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None, "kernel": dom["name"],
-                "peak_source": f"{peak_src} bf16_tflops x nominal tf32/bf16 ratio"}
-    elif dom["flops"] > 0:
-        peak = FP32_ALU_PEAK_TFLOPS if prec == hif.PREC_FP32 else FP64_ALU_PEAK_TFLOPS
-        ach = dom["flops"] / max(dom["launches"], 1) / per_launch_s / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None, "kernel": dom["name"],
-                "peak_source": "unit counts x max clock"}
-    else:
-        ach = dom["bytes"] / max(dom["launches"], 1) / per_launch_s / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": None, "kernel": dom["name"],
-                "peak_source": f"{peak_src} hbm_gbs"}
-    roof["share"] = dom["seconds"] / max(sum(p["seconds"] for p in prof), 1e-12)
+    roof = roofline(dom)
+    roof_top = [roofline(k) for k in sorted(prof, key=lambda p: -p["seconds"])[:8]]
 
     # the plain FP64 GPU form of the same step (comparison point), one run
     fp64_form = None
@@ -416,7 +434,10 @@ def main():
             "clocks": clocks, "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N * (1 + nrhs),
                     "d2h_bytes_per_step": 8 * N * nrhs},
-            "roofline": roof, "cpu_baseline": cpu, "fp64_form": fp64_form,
+            "roofline": roof, "roofline_top": [
+                {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()
+                 if k in ("kernel", "bound", "achieved", "frac", "share", "unit")}
+                for r in roof_top], "cpu_baseline": cpu, "fp64_form": fp64_form,
             "kernels": {p["name"]: round(p["seconds"] / args.steps, 5) for p in
                         sorted(prof, key=lambda p: -p["seconds"])[:8]},
         }

@@ -269,48 +269,61 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, co
 }
 
 // ---- batched GEMV --------------------------------------------------------------
-constexpr int GEMV_ROWS = 128;
-constexpr int GEMV_XC = 64;
+constexpr int GEMV_ROWS = 128;   // rows of y per CTA (N form)
+constexpr int GEMV_WARPS = 8;    // column classes per CTA (N form)
 
+// y = alpha M x (+ y): a CTA owns 128 rows; its 8 warps take the columns
+// c = w, w + 8, ... (each warp reads 128 contiguous rows of a column, 4 per
+// lane), and the 8 partial sums are added in warp order in shared memory,
+// so the result does not depend on timing.
 template <typename T, int R>
-__global__ void __launch_bounds__(GEMV_ROWS) k_gemv_n(const GemvOp* __restrict__ ops,
-                                                      const T* __restrict__ Mar, T* work,
-                                                      int64_t vs) {
+__global__ void __launch_bounds__(GEMV_ROWS * 2) k_gemv_n(const GemvOp* __restrict__ ops,
+                                                          const T* __restrict__ Mar, T* work,
+                                                          int64_t vs) {
   const GemvOp o = ops[blockIdx.y];
   const int r0 = blockIdx.x * GEMV_ROWS;
   if (r0 >= o.rows) return;
-  const int r = r0 + threadIdx.x;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const T* M = Mar + o.M;
-  __shared__ T xs[GEMV_XC][R];
-  T acc[R];
+  __shared__ T red[GEMV_WARPS][GEMV_ROWS];
+  T acc[4][R];
 #pragma unroll
-  for (int q = 0; q < R; ++q) acc[q] = T(0);
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int q = 0; q < R; ++q) acc[j][q] = T(0);
   const int cend = o.tri ? min(o.cols, r0 + GEMV_ROWS) : o.cols;
-  for (int c0 = 0; c0 < cend; c0 += GEMV_XC) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < GEMV_XC * R; e += GEMV_ROWS) {
-      int cc = e % GEMV_XC, q = e / GEMV_XC;
-      xs[cc][q] = c0 + cc < cend ? work[o.x + q * vs + c0 + cc] : T(0);
-    }
-    __syncthreads();
-    if (r < o.rows) {
-      const int cl = min(GEMV_XC, cend - c0);
-      for (int cc = 0; cc < cl; ++cc) {
-        const int c = c0 + cc;
-        if (o.tri && c > r) break;
-        const T mv = M[(int64_t)r + (int64_t)c * o.ld];
+  for (int c = warp; c < cend; c += GEMV_WARPS) {
+    T xv[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) acc[q] = fma(mv, xs[cc][q], acc[q]);
+    for (int q = 0; q < R; ++q) xv[q] = work[o.x + q * vs + c];
+    const T* mc = M + (int64_t)c * o.ld;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = r0 + lane + 32 * j;
+      if (r < o.rows && (!o.tri || c <= r)) {
+        const T mv = mc[r];
+#pragma unroll
+        for (int q = 0; q < R; ++q) acc[j][q] = fma(mv, xv[q], acc[j][q]);
       }
     }
   }
-  if (r < o.rows) {
-    const T al = (T)o.alpha;
+  const T al = (T)o.alpha;
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
-      T* yp = &work[o.y + q * vs + r];
-      *yp = (o.beta_one ? *yp : T(0)) + al * acc[q];
+  for (int q = 0; q < R; ++q) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) red[warp][lane + 32 * j] = acc[j][q];
+    __syncthreads();
+    if (threadIdx.x < GEMV_ROWS) {
+      const int r = r0 + threadIdx.x;
+      T s = red[0][threadIdx.x];
+#pragma unroll
+      for (int w = 1; w < GEMV_WARPS; ++w) s += red[w][threadIdx.x];
+      if (r < o.rows) {
+        T* yp = &work[o.y + q * vs + r];
+        *yp = (o.beta_one ? *yp : T(0)) + al * s;
+      }
     }
+    __syncthreads();
   }
 }
 
@@ -539,8 +552,8 @@ void gemv_batched(const GemvOp* d_ops, const GemvOp* h_ops, int nops, int trans,
         if (R == 8) k_gemv_t<T, 8><<<grid, 256, 0, st>>>(d_ops + f0, Marena, w, vstride);
         else k_gemv_t<T, 1><<<grid, 256, 0, st>>>(d_ops + f0, Marena, w, vstride);
       } else {
-        if (R == 8) k_gemv_n<T, 8><<<grid, GEMV_ROWS, 0, st>>>(d_ops + f0, Marena, w, vstride);
-        else k_gemv_n<T, 1><<<grid, GEMV_ROWS, 0, st>>>(d_ops + f0, Marena, w, vstride);
+        if (R == 8) k_gemv_n<T, 8><<<grid, GEMV_ROWS * 2, 0, st>>>(d_ops + f0, Marena, w, vstride);
+        else k_gemv_n<T, 1><<<grid, GEMV_ROWS * 2, 0, st>>>(d_ops + f0, Marena, w, vstride);
       }
       HIF_CHECK_LAUNCH();
       }

@@ -30,6 +30,7 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
                                  int32_t* perm, T* Farena, double* scratch, int32_t* stepAr,
                                  T* Fscratch, double eps, cudaStream_t st);
 size_t id_fscratch_elems(int64_t total_front_dofs);
+bool id_in_shared_memory(int m, int nF, int tsize);
 template <typename T>
 void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garena, T* Rout,
                     const std::vector<int64_t>& rOff, int* d_flags, bool tensor_cores,
@@ -677,17 +678,24 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
   fsc.release();
   Rbuf.release();
   if (prof_enabled()) {
-    // pivoted QR: each of the k steps reads and writes the trailing
-    // (idm - i) x (nF - i - 1) block once and spends 4 flops per entry on it
-    double fl = 0.0, by = 0.0;
+    // pivoted QR: each of the k steps spends 4 flops per entry of the
+    // trailing (idm - i) x (nF - i - 1) block; the cluster kernel reads and
+    // writes that block in HBM once per step, the shared-memory kernel reads
+    // the matrix once and writes the pivots and T
+    double fl[2] = {0.0, 0.0}, by[2] = {0.0, 0.0};
     for (int f = 0; f < nf; ++f) {
+      const int sm = id_in_shared_memory(sd[f].idm, sd[f].nF, (int)sizeof(T)) ? 1 : 0;
       for (int i = 0; i < sd[f].k; ++i) {
         const double e = (double)(sd[f].idm - i) * (sd[f].nF - i - 1);
-        fl += 4.0 * e;
-        by += 2.0 * sizeof(T) * e;
+        fl[sm] += 4.0 * e;
+        if (!sm) by[sm] += 2.0 * sizeof(T) * e;
       }
+      if (sm)
+        by[sm] += sizeof(T) * ((double)sd[f].idm * sd[f].nF +
+                               (double)sd[f].k * (sd[f].nF - sd[f].k)) + 4.0 * sd[f].nF;
     }
-    prof_add("id_cpqr", fl, by);
+    prof_add("id_cpqr", fl[0], by[0]);
+    prof_add("id_cpqr_smem", fl[1], by[1]);
   }
   // fronts with redundant DOFs are eliminated; the others keep every DOF
   std::vector<int> act;

@@ -504,6 +504,10 @@ __global__ void __launch_bounds__(1024) k_cpqr_smem(SkelDesc* fr, const int* __r
 
 size_t id_fscratch_elems(int64_t total_front_dofs) { return (size_t)total_front_dofs * NBK; }
 
+bool id_in_shared_memory(int m, int nF, int tsize) {
+  return smem_id_bytes(m, nF, tsize) <= (size_t)SMEM_ID_MAX;
+}
+
 template <typename T>
 void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* Garena,
                                  int32_t* perm, T* Farena, double* scratch, int32_t* stepAr,
@@ -543,8 +547,7 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
     HIF_CUDA_TRY(cudaMemcpyAsync(d_list, small[cl].data(), sizeof(int) * small[cl].size(),
                                  cudaMemcpyHostToDevice, st));
     {
-      static const char* names[3] = {"id_cpqr_smem_c0", "id_cpqr_smem_c1", "id_cpqr_smem_c2"};
-      ProfScope ps(names[cl], st);
+      ProfScope ps("id_cpqr_smem", st);   // counts added by the caller (they need k)
       k_cpqr_smem<T><<<(unsigned)small[cl].size(), class_threads[cl], small_bytes[cl], st>>>(
           d_f, d_list, Garena, perm, Farena, eps);
       HIF_CHECK_LAUNCH();

@@ -235,7 +235,16 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
     int nact = 0;
     while (nact < nq && qd[nact].n > p) ++nact;
     {
-      ProfScope ps("id_rowreduce_panel", st);
+      // algorithmic counts: Householder QR of the (m - p) x jb panel
+      // (2 (m-p) jb^2 flops), read and written once, reflectors written to V
+      double pf = 0, pb = 0;
+      if (prof_enabled())
+        for (int i = 0; i < nact; ++i) {
+          const double mp = qd[i].m - p, jb = std::min(QB, qd[i].n - p);
+          pf += 2.0 * mp * jb * jb;
+          pb += 3.0 * sizeof(T) * mp * jb;
+        }
+      ProfScope ps("id_rowreduce_panel", st, pf, pb);
       k_qr_panel<T><<<nact, QR_THREADS, 0, st>>>(d_qd, Garena, Var, Tar, p);
       HIF_CHECK_LAUNCH();
     }
