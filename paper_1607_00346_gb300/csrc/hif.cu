@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <future>
 #include <memory>
 #include <mutex>
@@ -52,13 +53,24 @@ double seconds_since(Clock::time_point t0) {
 }
 
 // HIF_TRACE=1 prints the wall time of each host phase of hif_factor to stderr.
+// HIF_TRACE=2 also drains the stream at every mark and prints how long the
+// drain took: a phase whose drain is near zero left the GPU idle while the
+// host worked (the drains serialize host and GPU, so the total grows).
 struct Trace {
-  bool on = std::getenv("HIF_TRACE") != nullptr;
+  int mode = std::getenv("HIF_TRACE") ? std::atoi(std::getenv("HIF_TRACE")) : 0;
+  bool on = mode > 0;
+  cudaStream_t st = nullptr;
   Clock::time_point t = Clock::now();
   void mark(int level, const char* what) {
     if (!on) return;
     const double ms = 1e3 * seconds_since(t);
-    std::fprintf(stderr, "[hif] level %d %-28s %9.2f ms\n", level, what, ms);
+    double drain = 0.0;
+    if (mode >= 2) {
+      const auto t1 = Clock::now();
+      cudaStreamSynchronize(st);
+      drain = 1e3 * seconds_since(t1);
+    }
+    std::fprintf(stderr, "[hif] level %d %-28s %9.2f ms  drain %8.2f ms\n", level, what, ms, drain);
     t = Clock::now();
   }
 };
@@ -274,23 +286,54 @@ struct Factor : FactorBase {
 template <typename T>
 class Builder {
  public:
-  Builder(Factor<T>& F, cudaStream_t st) : F_(F), st_(st), sym_(F.n, F.m) {}
+  Builder(Factor<T>& F, cudaStream_t st) : F_(F), st_(st), sym_(F.n, F.m) { tr_.st = st; }
+  ~Builder() {
+    jobs_.clear();   // waits for the host workers
+    if (up_st_) {
+      cudaStreamSynchronize(up_st_);
+      cudaStreamDestroy(up_st_);
+    }
+  }
 
   void run(const double* a_dev, const double* b_dev, double b_const);
 
  private:
   void check_flags(const char* where);
-  void cell_step(CellPlan& cp, DevBuf& Kar, DevBuf& cdesc_d, std::vector<CellDesc>& cdesc,
-                 DevBuf& lists_d);
+  void cell_step(std::shared_ptr<const CellPlan> cpp, DevBuf& Kar, DevBuf& cdesc_d,
+                 std::vector<CellDesc>& cdesc, DevBuf& lists_d);
   // returns the number of DOFs the step eliminated (marked dead in alive)
   int64_t skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& alive, DevBuf& Kar,
-                 DevBuf& cdesc_d, SkelPlan* plan = nullptr);
-  void gemv_list(GemvList& gl, std::vector<GemvOp>&& ops, int trans, int mat) {
-    gl.h = std::move(ops);
-    gl.trans = trans;
-    gl.mat = mat;
-    upload(gl.d, gl.h, &F_.mem, st_);
+                    DevBuf& cdesc_d, SkelPlan* plan = nullptr);
+
+  // Host side of an apply stage (gather list, mat-vec lists, set and
+  // accumulate lists).  It depends only on the plan and, for faces and edges,
+  // on the ID's ranks and pivots, so a worker thread builds it while the GPU
+  // factors; finished stages are uploaded on a side stream whenever the host
+  // waits for the GPU anyway, and the rest when the factorization ends.
+  struct StageHost {
+    std::vector<int32_t> idx;        // empty: the list is already on the device
+    std::vector<GemvOp> fwd[3], bwd[3];
+    int nfwd = 0, nbwd = 0;
+    int fwd_trans[3] = {0, 0, 0}, fwd_mat[3] = {0, 0, 0};
+    int bwd_trans[3] = {0, 0, 0}, bwd_mat[3] = {0, 0, 0};
+    std::vector<int32_t> set_g, set_p;
+    std::vector<int32_t> acc_tgt, acc_src;
+    std::vector<int64_t> acc_ptr;
+    int64_t entries_add = 0;
+  };
+  std::vector<std::pair<size_t, std::future<StageHost>>> jobs_;
+  // cell stages wait until the level's plans are joined (they would compete
+  // with the planning threads for the host cores)
+  std::vector<std::pair<size_t, std::function<StageHost()>>> unstarted_;
+  void start_stage_jobs() {
+    for (auto& u : unstarted_) jobs_.emplace_back(u.first, std::async(std::launch::async, std::move(u.second)));
+    unstarted_.clear();
   }
+  cudaStream_t up_st_ = nullptr;
+  void upload_stages(bool all);
+  static StageHost cell_stage_host(std::shared_ptr<const CellPlan> cpp,
+                                   std::vector<CellDesc> cdesc, std::vector<int64_t> poff,
+                                   int64_t N, int64_t nidx);
 
   Factor<T>& F_;
   cudaStream_t st_;
@@ -351,13 +394,15 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
   flags_.alloc_async(sizeof(int) * FLAG_COUNT, &F_.mem, st_);
   HIF_CUDA_TRY(cudaMemsetAsync(flags_.as<int>(), 0xff, sizeof(int) * FLAG_COUNT, st_));
 
+  HIF_CUDA_TRY(cudaStreamCreateWithFlags(&up_st_, cudaStreamNonBlocking));
   const int L = F_.L;
-  CellPlan prev;
+  std::shared_ptr<CellPlan> prevp;
   DevBuf prevK, prevDesc;
   for (int level = 0; level <= L; ++level) {
     level_ = level;
     auto tl = Clock::now();
-    CellPlan cp;
+    auto cpp = std::make_shared<CellPlan>();
+    CellPlan& cp = *cpp;
     tr_.mark(level, "start");
     std::vector<int64_t> mapOff;
     std::vector<int32_t> map;
@@ -368,7 +413,7 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
       have_spec_ = false;
     } else {
       sym_.build_cells(level, cp);
-      if (level > 0) sym_.merge_maps(prev, cp, mapOff, map);
+      if (level > 0) sym_.merge_maps(*prevp, cp, mapOff, map);
     }
     tr_.mark(level, "symbolic cells + merge maps");
     // frontal matrices of the level's cells
@@ -392,7 +437,7 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
       DevBuf map_d, mdesc_d;
       upload_async(map_d, map, &F_.mem, st_);
       std::vector<MergeDesc> md(cp.ncell);
-      const int C = cp.C, Cc = prev.C;
+      const int C = cp.C, Cc = prevp->C;
       for (int c = 0; c < cp.ncell; ++c) {
         md[c].K = cdesc[c].K;
         md[c].map = mapOff[c];
@@ -411,9 +456,9 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
     }
     tr_.mark(level, "frontal matrices");
     // after the cell step the interiors are gone; the face and edge plans
-    // depend only on that set, so a host thread builds them while the cells
-    // are eliminated on the GPU (the edge rows are filtered again once the
-    // faces have dropped their redundant DOFs)
+    // depend only on that set, so two host threads build them while the
+    // cells are eliminated on the GPU (the edge rows are filtered again once
+    // the faces have dropped their redundant DOFs)
     std::vector<uint8_t> alive(N, 0);
     for (int32_t g : cp.active) alive[g] = 1;
     for (int c = 0; c < cp.ncell; ++c)
@@ -427,10 +472,11 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
         edges.get();
       });
     }
-    cell_step(cp, Kar, cdesc_d, cdesc, lists_d);
+    cell_step(cpp, Kar, cdesc_d, cdesc, lists_d);
     tr_.mark(level, "cell elimination");
     F_.stats.fronts[level][0] = cp.ncell;
     if (level == L) {
+      start_stage_jobs();
       F_.stats.root_size = (int)cp.dofs.size();
       check_flags("the root factorization");
       F_.stats.level_seconds[level] = seconds_since(tl);
@@ -438,6 +484,7 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
     }
     if (F_.eps > 0.0) {
       planning.get();
+      start_stage_jobs();
       tr_.mark(level, "plans joined");
       const int64_t dropped = skel_step(cp, 1, alive, Kar, cdesc_d, &fplan);
       tr_.mark(level, "faces");
@@ -458,6 +505,8 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
       spec.get();
       have_spec_ = (alive == alive_faces);
       tr_.mark(level, "edges");
+    } else {
+      start_stage_jobs();
     }
     check_flags("level factorization");
     std::vector<int32_t> next;
@@ -466,19 +515,23 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
       if (alive[g]) next.push_back(g);
     F_.stats.active_after[level] = (int64_t)next.size();
     sym_.set_active(std::move(next));
-    prev = std::move(cp);
+    prevp = std::move(cpp);
     prevK = std::move(Kar);
     prevDesc = std::move(cdesc_d);
     F_.stats.level_seconds[level] = seconds_since(tl);
   }
+  start_stage_jobs();
+  upload_stages(true);
+  HIF_CUDA_TRY(cudaStreamSynchronize(up_st_));
   HIF_CUDA_TRY(cudaStreamSynchronize(st_));
   F_.stats.factor_seconds = seconds_since(t0);
 }
 
 template <typename T>
-void Builder<T>::cell_step(CellPlan& cp, DevBuf& Kar, DevBuf& cdesc_d, std::vector<CellDesc>& cdesc,
-                           DevBuf& lists_d) {
+void Builder<T>::cell_step(std::shared_ptr<const CellPlan> cpp, DevBuf& Kar, DevBuf& cdesc_d,
+                           std::vector<CellDesc>& cdesc, DevBuf& lists_d) {
   (void)cdesc_d;
+  const CellPlan& cp = *cpp;
   Stage s;
   s.kind = 0;
   s.level = level_;
@@ -506,38 +559,46 @@ void Builder<T>::cell_step(CellPlan& cp, DevBuf& Kar, DevBuf& cdesc_d, std::vect
   upload_async(fr_d, fr, &F_.mem, st_);
   partial_cholesky<T>(fr_d.as<DFront>(), fr.data(), (int)fr.size(), Kar.as<T>(), s.panels.as<T>(),
                       flags_.as<int>(), F_.opt.tensor_cores != 0, st_);
-  // apply stage: gather the whole frontal list of every cell
+  tr_.mark(level_, " cells: partial Cholesky queued");
+  // apply stage: gather the whole frontal list of every cell (already on
+  // the device); the rest is built on a worker thread
   s.nidx = (int64_t)cp.dofs.size();
   s.idx = std::move(lists_d);
-  std::vector<GemvOp> f1, f2, b1, b2;
-  std::vector<int32_t> sg, sp;
+  const size_t si = F_.stages.size();
+  F_.stages.push_back(std::move(s));
+  const int64_t N = (int64_t)F_.n * F_.n * F_.n;
+  const int64_t nidx = (int64_t)cp.dofs.size();
+  unstarted_.emplace_back(si, [cpp, cdesc, poff = std::move(poff), N, nidx]() mutable {
+    return cell_stage_host(cpp, std::move(cdesc), std::move(poff), N, nidx);
+  });
+}
+
+template <typename T>
+typename Builder<T>::StageHost Builder<T>::cell_stage_host(std::shared_ptr<const CellPlan> cpp,
+                                                           std::vector<CellDesc> cdesc,
+                                                           std::vector<int64_t> poff, int64_t N,
+                                                           int64_t nidx) {
+  const CellPlan& cp = *cpp;
+  StageHost h;
   for (int c = 0; c < cp.ncell; ++c) {
     const int nc = cdesc[c].n, p = cdesc[c].p;
     if (p == 0) continue;
-    const int64_t vo = cp.off[c], to = s.nidx + cp.off[c], P = poff[c];
+    const int64_t vo = cp.off[c], to = nidx + cp.off[c], P = poff[c];
     // forward: t_I = Linv v_I ; t_B = X^T t_I
-    f1.push_back(GemvOp{P, vo, to, p, p, nc, 1, 1.0f, 0});
-    if (nc > p) f2.push_back(GemvOp{P + p, to, to + p, nc - p, p, nc, 0, 1.0f, 0});
+    h.fwd[0].push_back(GemvOp{P, vo, to, p, p, nc, 1, 1.0f, 0});
+    if (nc > p) h.fwd[1].push_back(GemvOp{P + p, to, to + p, nc - p, p, nc, 0, 1.0f, 0});
     // backward: v_I -= X v_B ; t_I = Linv^T v_I
-    if (nc > p) b1.push_back(GemvOp{P + p, vo + p, vo, nc - p, p, nc, 0, -1.0f, 1});
-    b2.push_back(GemvOp{P, vo, to, p, p, nc, 1, 1.0f, 0});
+    if (nc > p) h.bwd[0].push_back(GemvOp{P + p, vo + p, vo, nc - p, p, nc, 0, -1.0f, 1});
+    h.bwd[1].push_back(GemvOp{P, vo, to, p, p, nc, 1, 1.0f, 0});
     for (int a = 0; a < p; ++a) {
-      sg.push_back(cp.dofs[cp.off[c] + a]);
-      sp.push_back((int32_t)(to + a));
+      h.set_g.push_back(cp.dofs[cp.off[c] + a]);
+      h.set_p.push_back((int32_t)(to + a));
     }
   }
-  s.fwd.resize(2);
-  s.bwd.resize(2);
-  gemv_list(s.fwd[0], std::move(f1), 0, 0);
-  gemv_list(s.fwd[1], std::move(f2), 0, 0);
-  gemv_list(s.bwd[0], std::move(b1), 1, 0);
-  gemv_list(s.bwd[1], std::move(b2), 1, 0);
-  s.nset = (int64_t)sg.size();
-  upload(s.set_g, sg, &F_.mem, st_);
-  upload(s.set_p, sp, &F_.mem, st_);
+  h.nfwd = h.nbwd = 2;
+  h.bwd_trans[0] = h.bwd_trans[1] = 1;
   // deterministic accumulation of the boundary updates: per DOF, contributions
   // in cell order (counting sort on the global index)
-  const int64_t N = (int64_t)F_.n * F_.n * F_.n;
   std::vector<int64_t> cnt(N + 1, 0);
   int64_t npair = 0;
   for (int c = 0; c < cp.ncell; ++c) {
@@ -548,29 +609,62 @@ void Builder<T>::cell_step(CellPlan& cp, DevBuf& Kar, DevBuf& cdesc_d, std::vect
     }
   }
   if (npair) {
-    std::vector<int32_t> tgt;
-    std::vector<int64_t> ptr;
     for (int64_t g = 0; g < N; ++g)
-      if (cnt[g + 1]) tgt.push_back((int32_t)g);
+      if (cnt[g + 1]) h.acc_tgt.push_back((int32_t)g);
     std::vector<int64_t> start(N + 1, 0);
     for (int64_t g = 0; g < N; ++g) start[g + 1] = start[g] + cnt[g + 1];
-    std::vector<int32_t> src(npair);
+    h.acc_src.resize(npair);
     std::vector<int64_t> cur(start.begin(), start.end() - 1);
     for (int c = 0; c < cp.ncell; ++c) {
       if (cp.p[c] == 0) continue;
       for (int64_t t = cp.off[c] + cp.p[c]; t < cp.off[c + 1]; ++t)
-        src[cur[cp.dofs[t]]++] = (int32_t)(s.nidx + t);
+        h.acc_src[cur[cp.dofs[t]]++] = (int32_t)(nidx + t);
     }
-    ptr.reserve(tgt.size() + 1);
-    ptr.push_back(0);
-    for (int32_t g : tgt) ptr.push_back(start[g + 1]);
-    s.nacc = (int64_t)tgt.size();
-    upload(s.acc_tgt, tgt, &F_.mem, st_);
-    upload(s.acc_ptr, ptr, &F_.mem, st_);
-    upload(s.acc_src, src, &F_.mem, st_);
+    h.acc_ptr.reserve(h.acc_tgt.size() + 1);
+    h.acc_ptr.push_back(0);
+    for (int32_t g : h.acc_tgt) h.acc_ptr.push_back(start[g + 1]);
   }
-  F_.work_stride = std::max(F_.work_stride, 2 * s.nidx);
-  F_.stages.push_back(std::move(s));
+  return h;
+}
+
+template <typename T>
+void Builder<T>::upload_stages(bool all) {
+  for (size_t jj = 0; jj < jobs_.size();) {
+    auto& job = jobs_[jj];
+    if (!all && job.second.wait_for(std::chrono::seconds(0)) != std::future_status::ready) {
+      ++jj;
+      continue;
+    }
+    StageHost h = job.second.get();
+    Stage& s = F_.stages[job.first];
+    if (!h.idx.empty()) upload(s.idx, h.idx, &F_.mem, up_st_);
+    s.fwd.resize(h.nfwd);
+    s.bwd.resize(h.nbwd);
+    for (int i = 0; i < h.nfwd; ++i) {
+      s.fwd[i].h = std::move(h.fwd[i]);
+      s.fwd[i].trans = h.fwd_trans[i];
+      s.fwd[i].mat = h.fwd_mat[i];
+      upload(s.fwd[i].d, s.fwd[i].h, &F_.mem, up_st_);
+    }
+    for (int i = 0; i < h.nbwd; ++i) {
+      s.bwd[i].h = std::move(h.bwd[i]);
+      s.bwd[i].trans = h.bwd_trans[i];
+      s.bwd[i].mat = h.bwd_mat[i];
+      upload(s.bwd[i].d, s.bwd[i].h, &F_.mem, up_st_);
+    }
+    s.nset = (int64_t)h.set_g.size();
+    upload(s.set_g, h.set_g, &F_.mem, up_st_);
+    upload(s.set_p, h.set_p, &F_.mem, up_st_);
+    s.nacc = (int64_t)h.acc_tgt.size();
+    if (s.nacc) {
+      upload(s.acc_tgt, h.acc_tgt, &F_.mem, up_st_);
+      upload(s.acc_ptr, h.acc_ptr, &F_.mem, up_st_);
+      upload(s.acc_src, h.acc_src, &F_.mem, up_st_);
+    }
+    s.entries += h.entries_add;
+    F_.work_stride = std::max(F_.work_stride, 2 * s.nidx);
+    jobs_.erase(jobs_.begin() + (std::ptrdiff_t)jj);
+  }
 }
 
 template <typename T>
@@ -653,6 +747,7 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
                    (double)sM / sel[g].size());
     }
   }
+  tr_.mark(level_, " gather + row reduction queued");
   std::vector<SkelDesc> sub[2];
   DevBuf sub_d[2];
   for (int g = 0; g < 2; ++g) {
@@ -669,6 +764,7 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
   std::vector<int32_t> perm(poff);
   HIF_CUDA_TRY(cudaMemcpyAsync(perm.data(), perm_d.as<void>(), sizeof(int32_t) * poff,
                                cudaMemcpyDeviceToHost, st_));
+  upload_stages(false);   // while the GPU runs the ID
   HIF_CUDA_TRY(cudaStreamSynchronize(st_));
   for (int g = 0; g < 2; ++g)
     for (size_t i = 0; i < sel[g].size(); ++i) sd[sel[g][i]].k = sub[g][i].k;
@@ -761,58 +857,55 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
   upload_async(fr_d, frs, &F_.mem, st_);
   partial_cholesky<T>(fr_d.as<DFront>(), frs.data(), (int)frs.size(), Z.as<T>(), s.panels.as<T>(),
                       flags_.as<int>(), F_.opt.tensor_cores != 0, st_);
+  tr_.mark(level_, " Z products + Cholesky queued");
   skel_writeback<T>(sda_d.as<SkelDesc>(), sda.data(), (int)sda.size(), ncp, rowpos_d.as<int32_t>(),
                     perm_d.as<int32_t>(), cdesc_d.as<CellDesc>(), Z.as<T>(), Kar.as<T>(), st_);
-  // apply stage
-  std::vector<int32_t> gidx;
-  std::vector<GemvOp> f1, f2, f3, b1, b2, b3;
-  std::vector<int32_t> sg, spos;
-  int64_t vo = 0;
+  // apply stage: the lists are built on a worker thread
   int64_t totalF = 0;
   for (const SkelDesc& d : sda) totalF += d.nF;
-  for (const SkelDesc& d : sda) {
-    const int k = d.k, nF = d.nF, p = nF - k;
-    const int32_t* pm = &perm[d.perm];
-    const int f = (int)(&d - sda.data());
-    const int src = act[f];
-    for (int i = 0; i < p; ++i) gidx.push_back(sp.rowDof[sp.rowOff[src] + pm[k + i]]);
-    for (int i = 0; i < k; ++i) gidx.push_back(sp.rowDof[sp.rowOff[src] + pm[i]]);
-    const int64_t to = totalF + vo;
-    // forward: v_c -= T^T v_h ; t_c = Linv v_c ; v_h -= X^T t_c
-    if (k) f1.push_back(GemvOp{d.Tm, vo + p, vo, k, p, k, 0, -1.0f, 1});
-    f2.push_back(GemvOp{d.P, vo, to, p, p, nF, 1, 1.0f, 0});
-    if (k) f3.push_back(GemvOp{d.P + p, to, vo + p, k, p, nF, 0, -1.0f, 1});
-    // backward: v_c -= X v_h ; t_c = Linv^T v_c ; v_h -= T t_c
-    if (k) b1.push_back(GemvOp{d.P + p, vo + p, vo, k, p, nF, 0, -1.0f, 1});
-    b2.push_back(GemvOp{d.P, vo, to, p, p, nF, 1, 1.0f, 0});
-    if (k) b3.push_back(GemvOp{d.Tm, to, vo + p, k, p, k, 0, -1.0f, 1});
-    for (int i = 0; i < p; ++i) {
-      sg.push_back(gidx[vo + i]);
-      spos.push_back((int32_t)(to + i));
-    }
-    for (int i = 0; i < k; ++i) {
-      sg.push_back(gidx[vo + p + i]);
-      spos.push_back((int32_t)(vo + p + i));
-    }
-    s.entries += (int64_t)nF * p + (int64_t)k * p;
-    vo += nF;
-  }
-  s.nidx = vo;
+  s.nidx = totalF;
   s.tmats = std::move(tm);
-  upload(s.idx, gidx, &F_.mem, st_);
-  s.fwd.resize(3);
-  s.bwd.resize(3);
-  gemv_list(s.fwd[0], std::move(f1), 1, 1);
-  gemv_list(s.fwd[1], std::move(f2), 0, 0);
-  gemv_list(s.fwd[2], std::move(f3), 0, 0);
-  gemv_list(s.bwd[0], std::move(b1), 1, 0);
-  gemv_list(s.bwd[1], std::move(b2), 1, 0);
-  gemv_list(s.bwd[2], std::move(b3), 0, 1);
-  s.nset = (int64_t)sg.size();
-  upload(s.set_g, sg, &F_.mem, st_);
-  upload(s.set_p, spos, &F_.mem, st_);
-  F_.work_stride = std::max(F_.work_stride, 2 * s.nidx);
+  const size_t si = F_.stages.size();
   F_.stages.push_back(std::move(s));
+  auto job = [sda, perm = std::move(perm), act, rowDof = std::move(sp.rowDof),
+              rowOff = std::move(sp.rowOff), totalF]() {
+    StageHost h;
+    int64_t vo = 0;
+    for (const SkelDesc& d : sda) {
+      const int k = d.k, nF = d.nF, p = nF - k;
+      const int32_t* pm = &perm[d.perm];
+      const int src = act[&d - sda.data()];
+      const int64_t base = (int64_t)h.idx.size();
+      for (int i = 0; i < p; ++i) h.idx.push_back(rowDof[rowOff[src] + pm[k + i]]);
+      for (int i = 0; i < k; ++i) h.idx.push_back(rowDof[rowOff[src] + pm[i]]);
+      const int64_t to = totalF + vo;
+      // forward: v_c -= T^T v_h ; t_c = Linv v_c ; v_h -= X^T t_c
+      if (k) h.fwd[0].push_back(GemvOp{d.Tm, vo + p, vo, k, p, k, 0, -1.0f, 1});
+      h.fwd[1].push_back(GemvOp{d.P, vo, to, p, p, nF, 1, 1.0f, 0});
+      if (k) h.fwd[2].push_back(GemvOp{d.P + p, to, vo + p, k, p, nF, 0, -1.0f, 1});
+      // backward: v_c -= X v_h ; t_c = Linv^T v_c ; v_h -= T t_c
+      if (k) h.bwd[0].push_back(GemvOp{d.P + p, vo + p, vo, k, p, nF, 0, -1.0f, 1});
+      h.bwd[1].push_back(GemvOp{d.P, vo, to, p, p, nF, 1, 1.0f, 0});
+      if (k) h.bwd[2].push_back(GemvOp{d.Tm, to, vo + p, k, p, k, 0, -1.0f, 1});
+      for (int i = 0; i < p; ++i) {
+        h.set_g.push_back(h.idx[base + i]);
+        h.set_p.push_back((int32_t)(to + i));
+      }
+      for (int i = 0; i < k; ++i) {
+        h.set_g.push_back(h.idx[base + p + i]);
+        h.set_p.push_back((int32_t)(vo + p + i));
+      }
+      h.entries_add += (int64_t)nF * p + (int64_t)k * p;
+      vo += nF;
+    }
+    h.nfwd = h.nbwd = 3;
+    h.fwd_trans[0] = 1;
+    h.fwd_mat[0] = 1;
+    h.bwd_trans[0] = h.bwd_trans[1] = 1;
+    h.bwd_mat[2] = 1;
+    return h;
+  };
+  jobs_.emplace_back(si, std::async(std::launch::async, std::move(job)));
   return dropped;
 }
 
