@@ -25,7 +25,11 @@
 #include "front.cuh"
 #include "warp.cuh"
 
+#include <cooperative_groups.h>
+
 namespace hif {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -129,6 +133,190 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_panel(const QRDesc* __restric
   }
 }
 
+// The same panel factorization spread over a thread-block cluster: the
+// panel's active rows (p..m-1) are split into CS contiguous slices held in
+// the shared memory of the cluster's CTAs.  Per column: each CTA adds up its
+// slice's part of the tail norm, the parts meet in distributed shared memory
+// and every CTA forms the same reflector from them (summed in rank order);
+// then each CTA computes its slice's part of the reflector's products with
+// the remaining panel columns, the parts meet again, and each CTA updates its
+// slice.  Two cluster barriers per column; the panel is read and written
+// once.  Sums run in the factor precision (FP64 arithmetic is slow here).
+constexpr int QRC_THREADS = 256;
+constexpr int QRC_WARPS = QRC_THREADS / 32;
+
+template <typename T>
+__global__ void __launch_bounds__(QRC_THREADS) k_qr_panel_cluster(const QRDesc* __restrict__ ds,
+                                                                 T* Gar, T* Var, T* Tar, int p,
+                                                                 int rb) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const QRDesc d = ds[blockIdx.x / CS];
+  if (p >= d.n) return;   // the whole cluster returns (same front)
+  const int jb = min(QB, d.n - p);
+  const int m = d.m, ld = d.ld, mp = m - p;
+  const int r0 = rank * rb, r1 = min(mp, r0 + rb);   // this CTA's rows, relative to p
+  T* A = Gar + d.A;
+  T* V = Var + d.V;
+  extern __shared__ __align__(16) unsigned char qsm[];
+  T* P = reinterpret_cast<T*>(qsm);                  // slice: P[i + j rb], i = row - p - r0
+  __shared__ T s_nrm[2], s_x0[2];                    // this CTA's parts, by column parity
+  __shared__ T s_dot[2][QB];
+  __shared__ T s_red[QRC_WARPS][QB];
+  __shared__ T s_G[QB][QB + 1];                      // Gram matrix parts, then the sum
+  __shared__ double s_tau[QB], s_v0[QB];
+  __shared__ double s_T[QB][QB + 1];
+  __shared__ double s_Gsum[QB][QB + 1];
+  __shared__ T s_sc[3];                              // v0, tau, alpha of the current column
+  __shared__ T s_w[QB];                              // tau w_jj of the current column
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int nr = max(0, r1 - r0);
+  for (int e = tid; e < nr * jb; e += QRC_THREADS) {
+    const int i = e % nr, j = e / nr;
+    P[i + (int64_t)j * rb] = A[(p + r0 + i) + (int64_t)(p + j) * ld];
+  }
+  __syncthreads();
+  for (int j = 0; j < jb; ++j) {
+    const int par = j & 1;
+    // 1. tail norm part (rows below the diagonal) and x0 from its owner
+    T s = T(0);
+    for (int i = max(0, j + 1 - r0) + tid; i < nr; i += QRC_THREADS) {
+      const T x = P[i + (int64_t)j * rb];
+      s = fma(x, x, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) s_red[warp][0] = s;
+    __syncthreads();
+    if (tid == 0) {
+      T t = T(0);
+      for (int w = 0; w < QRC_WARPS; ++w) t += s_red[w][0];
+      s_nrm[par] = t;
+      if (j >= r0 && j < r1) s_x0[par] = P[(j - r0) + (int64_t)j * rb];
+    }
+    cl.sync();
+    if (tid == 0) {
+      T tail = T(0);
+      for (int q2 = 0; q2 < CS; ++q2) tail += *cl.map_shared_rank(&s_nrm[par], q2);
+      const T x0 = *cl.map_shared_rank(&s_x0[par], min(CS - 1, j / rb));
+      const T nx = sqrt(fma(x0, x0, tail));
+      const T alpha = x0 >= T(0) ? -nx : nx;
+      const T v0 = x0 - alpha;
+      const T vtv = fma(v0, v0, tail);
+      s_sc[0] = v0;
+      s_sc[1] = vtv > T(0) ? T(2) / vtv : T(0);
+      s_sc[2] = alpha;
+      s_tau[j] = (double)s_sc[1];
+      s_v0[j] = (double)v0;
+    }
+    __syncthreads();
+    const T v0 = s_sc[0], tau = s_sc[1];
+    // 2. parts of w_jj = v^T a_jj for the remaining panel columns (v = v0 at
+    //    row j, the column's entries below it)
+    const int nrem = jb - j - 1;
+    if (nrem > 0) {
+      T acc[QB];
+#pragma unroll
+      for (int jj = 0; jj < QB; ++jj) acc[jj] = T(0);
+      for (int i = max(0, j - r0) + tid; i < nr; i += QRC_THREADS) {
+        const int row = r0 + i;
+        const T vi = row == j ? v0 : P[i + (int64_t)j * rb];
+#pragma unroll
+        for (int jj = 0; jj < QB; ++jj)
+          if (jj > j && jj < jb) acc[jj] = fma(vi, P[i + (int64_t)jj * rb], acc[jj]);
+      }
+#pragma unroll
+      for (int jj = 0; jj < QB; ++jj) {
+        if (jj > j && jj < jb) {
+          T x = acc[jj];
+          for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+          if (lane == 0) s_red[warp][jj] = x;
+        }
+      }
+      __syncthreads();
+      if (tid < QB && tid > j && tid < jb) {
+        T t = T(0);
+        for (int w = 0; w < QRC_WARPS; ++w) t += s_red[w][tid];
+        s_dot[par][tid] = t;
+      }
+    }
+    cl.sync();
+    if (tid < QB && tid > j && tid < jb) {
+      T t = T(0);
+      for (int q2 = 0; q2 < CS; ++q2) t += *cl.map_shared_rank(&s_dot[par][tid], q2);
+      s_w[tid] = tau * t;
+    }
+    __syncthreads();
+    // 3. update the slice: a_jj -= (tau w_jj) v; the diagonal gets alpha
+    for (int e = tid; e < nr * nrem; e += QRC_THREADS) {
+      const int i = e % nr, jj = j + 1 + e / nr;
+      const int row = r0 + i;
+      if (row < j) continue;
+      const T vi = row == j ? v0 : P[i + (int64_t)j * rb];
+      P[i + (int64_t)jj * rb] = fma(-s_w[jj], vi, P[i + (int64_t)jj * rb]);
+    }
+    __syncthreads();
+    if (tid == 0 && j >= r0 && j < r1) P[(j - r0) + (int64_t)j * rb] = s_sc[2];
+    __syncthreads();
+  }
+  // reflectors to V (rows p..m-1, zeros above each diagonal), the slice back
+  // to A, and this slice's part of the Gram matrix V^T V
+  for (int e = tid; e < nr * QB; e += QRC_THREADS) {
+    const int i = e % nr, j = e / nr, row = r0 + i;
+    T v = T(0);
+    if (j < jb) {
+      if (row == j) v = (T)s_v0[j];
+      else if (row > j) v = P[i + (int64_t)j * rb];
+      A[(p + row) + (int64_t)(p + j) * ld] = P[i + (int64_t)j * rb];
+    }
+    V[row + (int64_t)j * m] = v;
+  }
+  for (int e = warp; e < jb * jb; e += QRC_WARPS) {
+    const int a = e % jb, b = e / jb;
+    if (a > b) continue;
+    T g = T(0);
+    for (int i = lane; i < nr; i += 32) {
+      const int row = r0 + i;
+      const T va = row == a ? (T)s_v0[a] : (row > a ? P[i + (int64_t)a * rb] : T(0));
+      const T vb = row == b ? (T)s_v0[b] : (row > b ? P[i + (int64_t)b * rb] : T(0));
+      g = fma(va, vb, g);
+    }
+    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+    if (lane == 0) {
+      s_G[a][b] = g;
+      s_G[b][a] = g;
+    }
+  }
+  cl.sync();
+  if (rank == 0) {
+    for (int e = tid; e < jb * jb; e += QRC_THREADS) {
+      const int a = e % jb, b = e / jb;
+      double t = 0.0;
+      for (int q2 = 0; q2 < CS; ++q2) t += (double)*cl.map_shared_rank(&s_G[a][b], q2);
+      s_Gsum[a][b] = t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int j = 0; j < jb; ++j) {
+        for (int i = 0; i < QB; ++i) s_T[i][j] = 0.0;
+        s_T[j][j] = s_tau[j];
+        for (int i = 0; i < j; ++i) {
+          double t = 0.0;
+          for (int l = i; l < j; ++l) t += s_T[i][l] * s_Gsum[l][j];
+          s_T[i][j] = -s_tau[j] * t;
+        }
+      }
+    }
+    __syncthreads();
+    T* Tt = Tar + d.Tt;
+    for (int e = tid; e < QB * QB; e += QRC_THREADS) {
+      const int i = e % QB, j = e / QB;
+      Tt[e] = (i < jb && j < jb) ? (T)s_T[i][j] : T(0);
+    }
+  }
+  cl.sync();   // no CTA leaves while others may still read its shared memory
+}
+
 // R (n x n, ld = n, zeros below the diagonal) from rows 0..n-1 of the factored matrix
 template <typename T>
 __global__ void k_extract_r(const QRDesc* __restrict__ ds, const int64_t* __restrict__ roff,
@@ -142,6 +330,46 @@ __global__ void k_extract_r(const QRDesc* __restrict__ ds, const int64_t* __rest
 }
 
 }  // namespace
+
+constexpr size_t QRC_SMEM_MAX = 160 * 1024;
+
+// Whether a cluster of cs CTAs with rb panel rows each can be placed (the
+// first call per precision also lifts the kernel's cluster-size and shared
+// memory limits).
+template <typename T>
+bool panel_cluster_fits_t(int cs, int rb) {
+  static bool attr = false;
+  if (!attr) {
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel_cluster<T>,
+                                      cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel_cluster<T>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)QRC_SMEM_MAX));
+    attr = true;
+  }
+  const size_t smem = (size_t)rb * QB * sizeof(T);
+  if (smem > QRC_SMEM_MAX) return false;
+  cudaLaunchConfig_t q = {};
+  q.gridDim = dim3((unsigned)cs);
+  q.blockDim = dim3(QRC_THREADS);
+  q.dynamicSmemBytes = smem;
+  cudaLaunchAttribute qa[1];
+  qa[0].id = cudaLaunchAttributeClusterDimension;
+  qa[0].val.clusterDim.x = cs;
+  qa[0].val.clusterDim.y = 1;
+  qa[0].val.clusterDim.z = 1;
+  q.attrs = qa;
+  q.numAttrs = 1;
+  int ncl = 0;
+  if (cudaOccupancyMaxActiveClusters(&ncl, k_qr_panel_cluster<T>, &q) == cudaSuccess && ncl > 0)
+    return true;
+  cudaGetLastError();
+  return false;
+}
+
+inline bool panel_cluster_fits(int cs, int rb, int tsize) {
+  return tsize == 8 ? panel_cluster_fits_t<double>(cs, rb) : panel_cluster_fits_t<float>(cs, rb);
+}
 
 // Unpivoted QR of the R rows of fronts `which` (in place in the gather
 // arena); their n x n triangular factors go to Rout at rOff (ld = n).
@@ -189,6 +417,9 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
   HIF_CUDA_TRY(cudaMemcpyAsync(d_qd, qd.data(), sizeof(QRDesc) * nq, cudaMemcpyHostToDevice, st));
   HIF_CUDA_TRY(cudaMemcpyAsync(d_ro, ro.data(), sizeof(int64_t) * nq, cudaMemcpyHostToDevice, st));
   const int nmax = qd[0].n;
+  int nsm = 0, dev = 0;
+  HIF_CUDA_TRY(cudaGetDevice(&dev));
+  HIF_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   // GEMM descriptors of every panel, uploaded once
   std::vector<GemmOp> ops;
   std::vector<int64_t> opOff;   // per panel: start of its 3 lists
@@ -238,6 +469,8 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
       // algorithmic counts: Householder QR of the (m - p) x jb panel
       // (2 (m-p) jb^2 flops), read and written once, reflectors written to V
       double pf = 0, pb = 0;
+      int maxmp = 0;
+      for (int i = 0; i < nact; ++i) maxmp = std::max(maxmp, qd[i].m - p);
       if (prof_enabled())
         for (int i = 0; i < nact; ++i) {
           const double mp = qd[i].m - p, jb = std::min(QB, qd[i].n - p);
@@ -245,7 +478,31 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
           pb += 3.0 * sizeof(T) * mp * jb;
         }
       ProfScope ps("id_rowreduce_panel", st, pf, pb);
-      k_qr_panel<T><<<nact, QR_THREADS, 0, st>>>(d_qd, Garena, Var, Tar, p);
+      // few fronts: spread each panel over a cluster that keeps it in shared
+      // memory (as many CTAs per front as fill two per SM, up to 16); many
+      // fronts already fill the GPU with one CTA each
+      int cs = std::min(16, 2 * nsm / std::max(1, nact));
+      while (cs > 1 && !panel_cluster_fits(cs, ceil_div(maxmp, cs), (int)sizeof(T))) --cs;
+      const int rb = ceil_div(maxmp, std::max(1, cs));
+      const size_t smem = (size_t)rb * QB * sizeof(T);
+      if (cs > 1 && smem <= QRC_SMEM_MAX) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(nact * cs));
+        cfg.blockDim = dim3(QRC_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        HIF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_qr_panel_cluster<T>, (const QRDesc*)d_qd, Garena,
+                                        Var, Tar, p, rb));
+      } else {
+        k_qr_panel<T><<<nact, QR_THREADS, 0, st>>>(d_qd, Garena, Var, Tar, p);
+      }
       HIF_CHECK_LAUNCH();
     }
     const int cnt = opCnt[pi];
