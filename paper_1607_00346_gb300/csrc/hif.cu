@@ -842,9 +842,12 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
   upload_async(g1d, g1, &F_.mem, st_);
   upload_async(g2d, g2, &F_.mem, st_);
   upload_async(g3d, g3, &F_.mem, st_);
-  gemm_batched<T>(g1d.as<GemmOp>(), g1.data(), (int)g1.size(), Z.as<T>(), tm.as<T>(), Z.as<T>(), st_);
-  gemm_batched<T>(g2d.as<GemmOp>(), g2.data(), (int)g2.size(), Z.as<T>(), tm.as<T>(), Z.as<T>(), st_);
-  gemm_batched<T>(g3d.as<GemmOp>(), g3.data(), (int)g3.size(), tm.as<T>(), Z.as<T>(), Z.as<T>(), st_);
+  gemm_batched<T>(g1d.as<GemmOp>(), g1.data(), (int)g1.size(), Z.as<T>(), tm.as<T>(), Z.as<T>(), st_,
+                  "skel_z_products");
+  gemm_batched<T>(g2d.as<GemmOp>(), g2.data(), (int)g2.size(), Z.as<T>(), tm.as<T>(), Z.as<T>(), st_,
+                  "skel_z_products");
+  gemm_batched<T>(g3d.as<GemmOp>(), g3.data(), (int)g3.size(), tm.as<T>(), Z.as<T>(), Z.as<T>(), st_,
+                  "skel_z_products");
   // partial Cholesky of Z: eliminate the redundant DOFs
   Stage s;
   s.kind = 1;

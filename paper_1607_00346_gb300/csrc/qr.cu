@@ -515,11 +515,12 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
       const int64_t oi = o0 + (int64_t)which_gemm * cnt;
       if constexpr (std::is_same<T, float>::value) {
         if (use_tc && which_gemm == 0) {
-          gemm_tc(d_ops + oi, ops.data() + oi, cnt, A, B, C, d_flags, st);
+          gemm_tc(d_ops + oi, ops.data() + oi, cnt, A, B, C, d_flags, st, "id_rowreduce_w1");
           return;
         }
       }
-      gemm_batched<T>(d_ops + oi, ops.data() + oi, cnt, A, B, C, st);
+      gemm_batched<T>(d_ops + oi, ops.data() + oi, cnt, A, B, C, st,
+                      which_gemm == 0 ? "id_rowreduce_w1" : "id_rowreduce_update");
     };
     product(0, Var, Garena, War);
     product(1, Tar, War, War);

@@ -5,21 +5,23 @@
 // lo = tf32(x - hi), and A B^T ~= hi_A hi_B^T + hi_A lo_B^T + lo_A hi_B^T
 // (FP32 accumulation in tensor memory).
 //
-// Per CTA (256 threads, one 128 x 128 output tile):
+// Per CTA (one 128 x TN output tile, TN = 128 or 256; 128 + TN threads):
 //   * K is walked in chunks of KC (16, or 32 for products with few rows):
 //     thread t loads one row of the chunk of A (t < 128) or of B (t >= 128)
 //     into registers two chunks ahead, splits it and stores it in the K-major,
 //     no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix;
 //     LBO = 128 B between K-adjacent core matrices, SBO = 8 KC bytes between
 //     8-row groups) of one of two shared buffers;
-//   * one thread issues tcgen05.mma.cta_group::1.kind::tf32 (M = N = 128,
-//     K = 8 per instruction) into a 128-column TMEM accumulator and commits
+//   * one thread issues tcgen05.mma.cta_group::1.kind::tf32 (M = 128, N = TN,
+//     K = 8 per instruction) into a TN-column TMEM accumulator and commits
 //     to the buffer's mbarrier; the wait on it has an iteration limit (on
 //     expiry the kernel records FLAG_TIMEOUT, frees its TMEM and returns);
-//   * with KC = 16 a CTA holds 64 KB of shared memory and three CTAs share an
-//     SM (384 of its 512 TMEM columns), so one CTA's loads overlap the others'
-//     products;
-//   * eight warps read the accumulator back with tcgen05.ld (warp w owns TMEM
+//   * with KC = 16 a 128 x 128 CTA holds 64 KB of shared memory and three
+//     share an SM (384 of its 512 TMEM columns); a 128 x 256 CTA holds 96 KB
+//     and two share an SM (all 512 columns), so one CTA's loads overlap the
+//     others' products, and no mix of resident CTAs can ask for more than
+//     512 columns;
+//   * warps 0-7 read the accumulator back with tcgen05.ld (warp w owns TMEM
 //     lanes 32 (w % 4) .. = tile rows, and half w / 4 of the columns) and
 //     write alpha times it to C (added to C when beta = 1).
 #include <stdint.h>
@@ -34,8 +36,6 @@ namespace hif {
 namespace {
 
 constexpr int TC_M = 128;        // tile rows (TMEM lanes)
-constexpr int TC_N = 128;        // tile columns (TMEM columns)
-constexpr int TC_THREADS = 256;   // 128 stage A rows, 128 stage B rows
 constexpr long long WAIT_LIMIT = 20000000;     // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -84,15 +84,17 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b,
 // K chunks of KC, split into TF32 hi/lo parts and staged in one of two
 // shared-memory buffers while the tensor cores work on the other.  beta is 0
 // or 1.  `lower` skips tiles strictly above the diagonal of a symmetric C.
-template <int KC>
-__global__ void __launch_bounds__(TC_THREADS, KC == 16 ? 3 : 1)
+template <int KC, int TN>
+__global__ void __launch_bounds__(TC_M + TN, KC == 16 ? (TN == 128 ? 3 : 2) : 1)
     k_gemm_tc(const GemmOp* __restrict__ ops, const float* __restrict__ Ab,
               const float* __restrict__ Bb, float* Cb, int* flags) {
-  constexpr int TILE_BYTES = TC_M * KC * 4;   // one operand, one split
+  constexpr int TILE_A = TC_M * KC * 4;   // A operand, one split
+  constexpr int TILE_B = TN * KC * 4;     // B operand, one split
+  constexpr int STAGE = 2 * TILE_A + 2 * TILE_B;
   const GemmOp o = ops[blockIdx.y];
-  const int tm_n = (o.m + TC_M - 1) / TC_M, tn_n = (o.n + TC_N - 1) / TC_N;
+  const int tm_n = (o.m + TC_M - 1) / TC_M, tn_n = (o.n + TN - 1) / TN;
   if ((int)blockIdx.x >= tm_n * tn_n) return;
-  const int rb = (blockIdx.x % tm_n) * TC_M, cb = (blockIdx.x / tm_n) * TC_N;
+  const int rb = (blockIdx.x % tm_n) * TC_M, cb = (blockIdx.x / tm_n) * TN;
   if (o.lower && cb >= rb + TC_M) return;
   const float* A = Ab + o.A;
   const float* B = Bb + o.B;
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(TC_THREADS, KC == 16 ? 3 : 1)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                      smem_u32(&s_tmem)),
-                 "r"(TC_N));
+                 "r"(TN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   if (tid == 0) {
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(TC_THREADS, KC == 16 ? 3 : 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   const uint32_t tmem = s_tmem;
-  const uint32_t idesc = idesc_tf32(TC_M, TC_N);
+  const uint32_t idesc = idesc_tf32(TC_M, TN);
   const int nchunk = (o.k + KC - 1) / KC;
   uint32_t phase[2] = {0u, 0u};
   bool ok = true;
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(TC_THREADS, KC == 16 ? 3 : 1)
   // staging registers of two chunks: chunk c lives in va (c even) or vb (c
   // odd); the loads of chunk c + 2 are issued as soon as chunk c is stored
   const bool isA = tid < TC_M;
-  const int row = tid % TC_M;
+  const int row = isA ? tid : tid - TC_M;
   const float* X = isA ? A : B;
   const int base = isA ? rb : cb;
   const int lim = isA ? o.m : o.n;
@@ -163,13 +165,13 @@ __global__ void __launch_bounds__(TC_THREADS, KC == 16 ? 3 : 1)
   };
   auto step = [&](int ch, float (&v)[KC]) -> bool {
     const int s = ch & 1;
-    unsigned char* buf = smem + s * 4 * TILE_BYTES;
+    unsigned char* buf = smem + s * STAGE;
     if (ch >= 2 && !wait_buf(s)) s_fail = 1;   // buffer s is free again
     __syncthreads();
     if (s_fail) return false;
     {
-      unsigned char* hi = buf + (isA ? 0 : 2 * TILE_BYTES);
-      unsigned char* lo = hi + TILE_BYTES;
+      unsigned char* hi = buf + (isA ? 0 : 2 * TILE_A);
+      unsigned char* lo = hi + (isA ? TILE_A : TILE_B);
 #pragma unroll
       for (int k = 0; k < KC; k += 4) {
         float4 h, l;
@@ -191,8 +193,8 @@ __global__ void __launch_bounds__(TC_THREADS, KC == 16 ? 3 : 1)
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;\n");
-      const uint32_t ah = smem_u32(buf), al = ah + TILE_BYTES, bh = ah + 2 * TILE_BYTES,
-                     bl = ah + 3 * TILE_BYTES;
+      const uint32_t ah = smem_u32(buf), al = ah + TILE_A, bh = ah + 2 * TILE_A,
+                     bl = bh + TILE_B;
       for (int ks = 0; ks < KC / 8; ++ks) {
         const uint32_t off = ks * 256;   // two core matrices of K per instruction
         const uint32_t acc0 = (ch > 0 || ks > 0) ? 1u : 0u;
@@ -221,12 +223,13 @@ __global__ void __launch_bounds__(TC_THREADS, KC == 16 ? 3 : 1)
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n");
-  if (ok && nchunk > 0) {
-    // warp w reads TMEM lanes 32 (w % 4) .. (tile rows) and half w / 4 of the columns
+  if (ok && nchunk > 0 && warp < 8) {
+    // warps 0-7: warp w reads TMEM lanes 32 (w % 4) .. (tile rows) and half
+    // w / 4 of the columns
     const int r = rb + (warp % 4) * 32 + lane;
     const float al = o.alpha;
-    const int ch0 = (warp / 4) * (TC_N / 2);
-    for (int c0 = ch0; c0 < ch0 + TC_N / 2; c0 += 32) {
+    const int ch0 = (warp / 4) * (TN / 2);
+    for (int c0 = ch0; c0 < ch0 + TN / 2; c0 += 32) {
       uint32_t v[32];
       const uint32_t taddr = tmem + ((uint32_t)((warp % 4) * 32) << 16) + (uint32_t)c0;
       asm volatile(
@@ -258,41 +261,50 @@ __global__ void __launch_bounds__(TC_THREADS, KC == 16 ? 3 : 1)
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_N));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TN));
 }
 
 }  // namespace
 
+template <int KC, int TN>
+void launch_tc(const GemmOp* d_ops, int nops, int mt, const float* Abase, const float* Bbase,
+               float* Cbase, int* d_flags, cudaStream_t st) {
+  constexpr size_t smem = 2 * (size_t)(2 * TC_M * KC * 4 + 2 * TN * KC * 4);
+  static bool attr = false;
+  if (!attr) {
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<KC, TN>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  for (int f0 = 0; f0 < nops; f0 += 65535) {
+    const int nb = std::min(65535, nops - f0);
+    k_gemm_tc<KC, TN><<<dim3(mt, nb), TC_M + TN, smem, st>>>(d_ops + f0, Abase, Bbase, Cbase,
+                                                             d_flags);
+    HIF_CHECK_LAUNCH();
+  }
+}
+
 void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Abase,
              const float* Bbase, float* Cbase, int* d_flags, cudaStream_t st, const char* name) {
   if (nops == 0) return;
-  int mt = 1, mmax = 0;
+  int mmax = 0, nmax = 0;
   double fl = 0;
   for (int i = 0; i < nops; ++i) {
-    mt = std::max(mt, ceil_div(h_ops[i].m, TC_M) * ceil_div(h_ops[i].n, TC_N));
     mmax = std::max(mmax, h_ops[i].m);
+    nmax = std::max(nmax, h_ops[i].n);
     fl += 2.0 * h_ops[i].m * (double)h_ops[i].n * h_ops[i].k * (h_ops[i].lower ? 0.5 : 1.0);
   }
-  // few rows (one tile, mostly padding): fewer, longer chunks
-  const bool wide = mmax <= 64;
-  const size_t smem = 2 * 4 * (size_t)TC_M * (wide ? 32 : 16) * 4;
-  static bool attr = false;
-  if (!attr) {
-    HIF_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      2 * 4 * TC_M * 16 * 4));
-    HIF_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      2 * 4 * TC_M * 32 * 4));
-    attr = true;
-  }
+  // few rows (one tile, mostly padding): fewer, longer chunks; wide
+  // products: 128 x 256 tiles (half the A staging per product)
+  const bool narrow = mmax <= 64;
+  const int tn = (!narrow && nmax >= 256) ? 256 : 128;
+  int mt = 1;
+  for (int i = 0; i < nops; ++i)
+    mt = std::max(mt, ceil_div(h_ops[i].m, TC_M) * ceil_div(h_ops[i].n, tn));
   ProfScope ps(name, st, fl, 0.0);
-  for (int f0 = 0; f0 < nops; f0 += 65535) {
-    const int nb = std::min(65535, nops - f0);
-    if (wide)
-      k_gemm_tc<32><<<dim3(mt, nb), TC_THREADS, smem, st>>>(d_ops + f0, Abase, Bbase, Cbase, d_flags);
-    else
-      k_gemm_tc<16><<<dim3(mt, nb), TC_THREADS, smem, st>>>(d_ops + f0, Abase, Bbase, Cbase, d_flags);
-    HIF_CHECK_LAUNCH();
-  }
+  if (narrow) launch_tc<32, 128>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st);
+  else if (tn == 256) launch_tc<16, 256>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st);
+  else launch_tc<16, 128>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st);
 }
 
 }  // namespace hif
