@@ -35,7 +35,29 @@ WORKLOADS = {
     "contrast64": dict(n=64, m=4, lo=-1.0, hi=1.0, b=0.0, eps=1e-6, nrhs=8),
     "laplace16": dict(n=16, m=4, lo=0.0, hi=0.0, b=0.0, eps=1e-6, nrhs=1),
     "contrast256": dict(n=256, m=4, lo=-3.0, hi=3.0, b=0.0, eps=1e-4, nrhs=1),
+    # the paper's Example 2 (smoothed thresholded noise) and Example 3
+    # (checkerboard of 7-point blocks) fields, {0.1, 1000}
+    "example2_64": dict(n=64, m=4, lo=0.0, hi=0.0, b=0.1, eps=1e-5, nrhs=1, field=("blur", 1.0)),
+    "example3_64": dict(n=64, m=4, lo=0.0, hi=0.0, b=0.1, eps=1e-4, nrhs=1, field=("checker", 7)),
 }
+
+
+def make_field(w: dict, n: int, seed: int):
+    from paper_1607_00346_gb300 import inputs
+    if "field" in w:
+        return inputs.make_coeff(n, w["field"], seed)
+    if w["hi"] > w["lo"]:
+        return inputs.coeff_log_uniform(n, w["lo"], w["hi"], seed)
+    return inputs.coeff_constant(n)
+
+
+def field_desc(w: dict) -> str:
+    if "field" in w:
+        return {"blur": "Example 2 field (U(0,1) smoothed by a unit Gaussian, 0.1 / 1000 at 0.5)",
+                "checker": "Example 3 checkerboard of 7-point blocks (1000 / 0.1)"}[w["field"][0]]
+    if w["hi"] > w["lo"]:
+        return f"a=10^U({w['lo']},{w['hi']}) iid per point"
+    return "a=1"
 
 # FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -139,8 +161,7 @@ def cpu_oracle_sample(w: dict, n_sample: int, seed: int):
     from oracle import krylov, stencil
     from paper_1607_00346_gb300 import inputs
 
-    a = inputs.coeff_log_uniform(n_sample, w["lo"], w["hi"], seed) if w["hi"] > w["lo"] \
-        else inputs.coeff_constant(n_sample)
+    a = make_field(w, n_sample, seed)
     f = inputs.normal_rhs(n_sample, 1, seed + 1)[0]
     t0 = time.perf_counter()
     A = stencil.assemble(a, w["b"], n_sample)
@@ -272,8 +293,7 @@ def main():
     N = n ** 3
     prec = hif.PREC_FP32 if args.precision == "fp32" else hif.PREC_FP64
     seed = inputs.SEED_BASE + 2
-    a_h = inputs.coeff_log_uniform(n, w["lo"], w["hi"], seed) if w["hi"] > w["lo"] \
-        else inputs.coeff_constant(n)
+    a_h = make_field(w, n, seed)
     f_h = inputs.normal_rhs(n, nrhs, seed + 1)
     a_d = torch.from_numpy(a_h).cuda()
     f_d = torch.from_numpy(f_h).cuda()
@@ -421,7 +441,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == hif.PREC_FP32 else "f64", "data": "synthetic",
             "config": {"workload": f"{args.workload}: n={n} (N={N}), m={m}, "
-                                   f"a=10^U({w['lo']},{w['hi']}) iid per point, b={w['b']}, "
+                                   f"{field_desc(w)}, b={w['b']}, "
                                    f"eps={w['eps']}, {args.precision} factor, FP64 PCG to 1e-10, "
                                    f"nrhs={nrhs}",
                        "l2": "inputs and factor larger than L2 (no flush needed)",

@@ -182,3 +182,23 @@ def test_invalid_coefficients(H):
     # the context is still usable afterwards
     h = H.factor(n, 4, _dev(np.ones(n ** 3)), eps=0.0)
     assert h.stats()["root_size"] == n ** 3 - (n - 1) ** 3
+
+
+@pytest.mark.parametrize("field,n,eps", [("blur", 32, 1e-5), ("checker", 32, 1e-4)])
+def test_paper_example_fields_within_2x_oracle(H, field, n, eps):
+    # the paper's Example 2 (smoothed thresholded noise) and Example 3
+    # (checkerboard) coefficient fields, b = 0.1: contrast 10^4
+    a = (inputs.coeff_blurred_quantized(n, 610 + n) if field == "blur"
+         else inputs.coeff_checkerboard(n))
+    A = stencil.assemble(a, 0.1, n)
+    x = inputs.normal_rhs(n, 1, 620 + n)[0]
+    h = H.factor(n, 4, _dev(a), b_const=0.1, eps=eps)
+    es_g = _es_gpu(h, A, x)
+    fac = ohif.hif_factor(A, n, 4, eps, check=False)
+    es_o = krylov.solve_error(A, fac, x)
+    assert es_g <= 2.0 * es_o + 1e-12, (es_g, es_o)
+    f = inputs.normal_rhs(n, 1, 630 + n)
+    u = torch.zeros(f.shape, dtype=torch.float64, device="cuda")
+    its, rel = h.solve(_dev(f), u)
+    r = f[0] - A @ u.cpu().numpy()[0]
+    assert rel[0] <= 1e-10 and np.linalg.norm(r) <= 1.0000001e-10 * np.linalg.norm(f[0])
