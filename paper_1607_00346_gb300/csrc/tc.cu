@@ -27,6 +27,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 #include "dense.cuh"
@@ -87,7 +88,8 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b,
 template <int KC, int TN>
 __global__ void __launch_bounds__(TC_M + TN, KC == 16 ? (TN == 128 ? 3 : 2) : 1)
     k_gemm_tc(const GemmOp* __restrict__ ops, const float* __restrict__ Ab,
-              const float* __restrict__ Bb, float* Cb, int* flags) {
+              const float* __restrict__ Bb, float* Cb, int* flags,
+              const int64_t* __restrict__ woff, float* Wk) {
   constexpr int TILE_A = TC_M * KC * 4;   // A operand, one split
   constexpr int TILE_B = TN * KC * 4;     // B operand, one split
   constexpr int STAGE = 2 * TILE_A + 2 * TILE_B;
@@ -123,7 +125,11 @@ __global__ void __launch_bounds__(TC_M + TN, KC == 16 ? (TN == 128 ? 3 : 2) : 1)
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   const uint32_t tmem = s_tmem;
   const uint32_t idesc = idesc_tf32(TC_M, TN);
-  const int nchunk = (o.k + KC - 1) / KC;
+  // split K (gridDim.z > 1): this CTA takes chunks [cbeg, cbeg + nchunk) of
+  // the product and leaves its partial tile in the work space Wk
+  const int nch_all = (o.k + KC - 1) / KC;
+  const int cbeg = (int)(((int64_t)nch_all * blockIdx.z) / gridDim.z);
+  const int nchunk = (int)(((int64_t)nch_all * (blockIdx.z + 1)) / gridDim.z) - cbeg;
   uint32_t phase[2] = {0u, 0u};
   bool ok = true;
 
@@ -154,7 +160,7 @@ __global__ void __launch_bounds__(TC_M + TN, KC == 16 ? (TN == 128 ? 3 : 2) : 1)
   const bool kfast = isA ? (o.transA != 0) : (o.transB == 0);   // k contiguous in memory
   const bool rin = base + row < lim;
   auto load = [&](int ch, float (&v)[KC]) {
-    const int k0 = ch * KC;
+    const int k0 = (cbeg + ch) * KC;
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
       const int kk = k0 + k;
@@ -248,13 +254,24 @@ __global__ void __launch_bounds__(TC_M + TN, KC == 16 ? (TN == 128 ? 3 : 2) : 1)
         for (int j = 0; j < 32; ++j) {
           const int c = cb + c0 + j;
           if (c < o.n) {
-            float* cp = &C[(int64_t)r + (int64_t)c * o.ldc];
-            const float x = al * __uint_as_float(v[j]);
-            *cp = o.beta != 0.f ? *cp + x : x;
+            if (gridDim.z > 1) {
+              Wk[woff[blockIdx.y] + (int64_t)blockIdx.z * o.m * o.n + r + (int64_t)c * o.m] =
+                  __uint_as_float(v[j]);
+            } else {
+              float* cp = &C[(int64_t)r + (int64_t)c * o.ldc];
+              const float x = al * __uint_as_float(v[j]);
+              *cp = o.beta != 0.f ? *cp + x : x;
+            }
           }
         }
       }
     }
+  } else if (ok && nchunk == 0 && gridDim.z > 1 && warp < 4) {
+    // an empty share of a split product contributes zero
+    const int r = rb + warp * 32 + lane;
+    if (r < o.m)
+      for (int c = cb; c < min(o.n, cb + TN); ++c)
+        Wk[woff[blockIdx.y] + (int64_t)blockIdx.z * o.m * o.n + r + (int64_t)c * o.m] = 0.f;
   } else if (!ok && tid == 0) {
     atomicCAS(&flags[FLAG_TIMEOUT], -1, (int)blockIdx.y);
   }
@@ -264,11 +281,28 @@ __global__ void __launch_bounds__(TC_M + TN, KC == 16 ? (TN == 128 ? 3 : 2) : 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TN));
 }
 
+// C = beta C + alpha (sum of the split partial tiles), summed in split order
+__global__ void k_splitk_reduce(const GemmOp* __restrict__ ops, const int64_t* __restrict__ woff,
+                                const float* __restrict__ Wk, int S, float* Cb) {
+  const GemmOp o = ops[blockIdx.y];
+  const int64_t mn = (int64_t)o.m * o.n;
+  const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (e >= mn) return;
+  const float* w = Wk + woff[blockIdx.y] + e;
+  float s = 0.f;
+  for (int z = 0; z < S; ++z) s += w[z * mn];
+  const int r = (int)(e % o.m), c = (int)(e / o.m);
+  float* cp = Cb + o.C + r + (int64_t)c * o.ldc;
+  const float x = o.alpha * s;
+  *cp = o.beta != 0.f ? *cp + x : x;
+}
+
 }  // namespace
 
 template <int KC, int TN>
 void launch_tc(const GemmOp* d_ops, int nops, int mt, const float* Abase, const float* Bbase,
-               float* Cbase, int* d_flags, cudaStream_t st) {
+               float* Cbase, int* d_flags, cudaStream_t st, int S = 1,
+               const int64_t* d_woff = nullptr, float* Wk = nullptr) {
   constexpr size_t smem = 2 * (size_t)(2 * TC_M * KC * 4 + 2 * TN * KC * 4);
   static bool attr = false;
   if (!attr) {
@@ -278,8 +312,8 @@ void launch_tc(const GemmOp* d_ops, int nops, int mt, const float* Abase, const 
   }
   for (int f0 = 0; f0 < nops; f0 += 65535) {
     const int nb = std::min(65535, nops - f0);
-    k_gemm_tc<KC, TN><<<dim3(mt, nb), TC_M + TN, smem, st>>>(d_ops + f0, Abase, Bbase, Cbase,
-                                                             d_flags);
+    k_gemm_tc<KC, TN><<<dim3(mt, nb, S), TC_M + TN, smem, st>>>(
+        d_ops + f0, Abase, Bbase, Cbase, d_flags, d_woff ? d_woff + f0 : nullptr, Wk);
     HIF_CHECK_LAUNCH();
   }
 }
@@ -302,6 +336,64 @@ void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Ab
   for (int i = 0; i < nops; ++i)
     mt = std::max(mt, ceil_div(h_ops[i].m, TC_M) * ceil_div(h_ops[i].n, tn));
   ProfScope ps(name, st, fl, 0.0);
+  // few output tiles and deep K (the pre-QR W1 = V^T A_t): split K so that
+  // the launch fills the GPU; partial tiles are summed in a fixed order
+  int tiles = 0, kmin = 1 << 30;
+  bool any_lower = false;
+  for (int i = 0; i < nops; ++i) {
+    tiles += ceil_div(h_ops[i].m, TC_M) * ceil_div(h_ops[i].n, tn);
+    kmin = std::min(kmin, h_ops[i].k);
+    any_lower = any_lower || h_ops[i].lower;
+  }
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    HIF_CUDA_TRY(cudaGetDevice(&dev));
+    HIF_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int kc = narrow ? 32 : 16;
+  const int per_sm = narrow ? 1 : (tn == 256 ? 2 : 3);
+  // S minimises the waves per unit of work, ceil(tiles S / capacity) / S,
+  // with at least 16 chunks of K per share
+  int S = 1;
+  if (!any_lower && nops <= 65535) {
+    const int cap = per_sm * nsm;
+    const int smax = std::max(1, std::min(8, kmin / (16 * kc)));
+    double best = 1e30;
+    for (int s = 1; s <= smax; ++s) {
+      const double cost = (double)ceil_div(tiles * s, cap) / s;
+      if (cost < best - 1e-9) {
+        best = cost;
+        S = s;
+      }
+    }
+  }
+  int64_t* d_woff = nullptr;
+  float* Wk = nullptr;
+  if (S > 1) {
+    std::vector<int64_t> woff(nops);
+    int64_t tot = 0;
+    int64_t mnmax = 1;
+    for (int i = 0; i < nops; ++i) {
+      woff[i] = tot;
+      tot += (int64_t)S * h_ops[i].m * h_ops[i].n;
+      mnmax = std::max<int64_t>(mnmax, (int64_t)h_ops[i].m * h_ops[i].n);
+    }
+    HIF_CUDA_TRY(cudaMallocAsync(&d_woff, sizeof(int64_t) * nops, st));
+    HIF_CUDA_TRY(cudaMallocAsync(&Wk, sizeof(float) * tot, st));
+    HIF_CUDA_TRY(cudaMemcpyAsync(d_woff, woff.data(), sizeof(int64_t) * nops,
+                                 cudaMemcpyHostToDevice, st));
+    if (narrow) launch_tc<32, 128>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st, S, d_woff, Wk);
+    else if (tn == 256)
+      launch_tc<16, 256>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st, S, d_woff, Wk);
+    else launch_tc<16, 128>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st, S, d_woff, Wk);
+    k_splitk_reduce<<<dim3((unsigned)ceil_div(mnmax, 256), nops), 256, 0, st>>>(d_ops, d_woff, Wk,
+                                                                                S, Cbase);
+    HIF_CHECK_LAUNCH();
+    HIF_CUDA_TRY(cudaFreeAsync(Wk, st));
+    HIF_CUDA_TRY(cudaFreeAsync(d_woff, st));
+    return;
+  }
   if (narrow) launch_tc<32, 128>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st);
   else if (tn == 256) launch_tc<16, 256>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st);
   else launch_tc<16, 128>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st);
