@@ -146,6 +146,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def job_rate(units_per_rank: float, seconds: float, dist=None, device: str = "cpu"):
+    """Whole-job rate of N replicas: the slowest rank's seconds (max over
+    ranks) and units of all ranks / that time.  Returns (seconds, rate)."""
+    ws = 1
+    if dist is not None:
+        import torch
+        ws = dist.get_world_size()
+        t = torch.tensor([seconds], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        seconds = float(t.item())
+    return seconds, units_per_rank * ws / seconds
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -344,12 +357,8 @@ def main():
         per_step.append(ev[k].elapsed_time(ev[k + 1]) / 1e3)
     fac_s = [sub[k][0].elapsed_time(sub[k][1]) / 1e3 for k in range(args.steps)]
     sol_s = [sub[k][1].elapsed_time(sub[k][2]) / 1e3 for k in range(args.steps)]
-    total = sum(per_step)
-    if dist is not None:
-        t = torch.tensor([total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-    value = N * nrhs * args.steps * ws / total / 1e6
+    total, rate = job_rate(N * nrhs * args.steps, sum(per_step), dist, "cuda")
+    value = rate / 1e6
 
     # residual check of the last solve (FP64 operator, through the C ABI)
     r = torch.empty_like(f_d)
@@ -368,12 +377,8 @@ def main():
         with hif.factor(n, m, a_pin.numpy(), b_const=w["b"], eps=w["eps"], precision=prec) as h2:
             h2.solve(f_pin.numpy(), u_pin.numpy())
     barrier()
-    e2e_t = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e_value = N * nrhs * e2e_steps * ws / e2e_t / 1e6
+    e2e_t, e2e_rate = job_rate(N * nrhs * e2e_steps, time.perf_counter() - t0, dist, "cuda")
+    e2e_value = e2e_rate / 1e6
 
     # roofline of the dominant kernel (largest share of the timed region)
     hbm_peak, bf16_peak, peak_src = _peaks()
