@@ -74,7 +74,7 @@ KERNEL_BOUND = {
     "skel_gather": "hbm", "merge_children": "hbm", "spmv": "hbm", "residual": "hbm",
     "chol_panel": "alu", "chol_trailing_update": "alu", "gemm_batched": "alu",
     "trtri_merge": "alu", "id_cpqr_smem": "alu", "id_rowreduce_update": "alu",
-    "skel_z_products": "alu",
+    "skel_z_products": "alu", "chol_block_update": "tensor",
 }
 
 # nominal dense TF32 / bf16 tensor ratio (1.1 / 2.25 PFLOP/s)

@@ -6,6 +6,7 @@
 // 2-D grid: blockIdx.y = descriptor, blockIdx.x = tile / chunk inside it.
 // Fronts whose work is finished, and tiles outside a front, exit at once.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdlib>
 #include <type_traits>
@@ -136,8 +137,11 @@ __device__ __forceinline__ void tri_index(int t, int& ti, int& tj) {
 }
 
 // ---- trailing update: K[j1:n, j1:n] -= K[j1:n, j0:j1] K[j1:n, j0:j1]^T (lower tiles)
+// (jmax < n: only the columns below jmax, i.e. the rest of an outer block;
+// the tiles then form nrow x ncol rectangles, strictly upper ones skipped)
 template <typename T>
-__global__ void __launch_bounds__(256) k_syrk(const DFront* __restrict__ fr, T* Kar, int j0) {
+__global__ void __launch_bounds__(256) k_syrk(const DFront* __restrict__ fr, T* Kar, int j0,
+                                              int jmax) {
   const DFront d = fr[blockIdx.y];
   if (j0 >= d.p) return;
   const int jb = min(NB, d.p - j0);
@@ -145,9 +149,17 @@ __global__ void __launch_bounds__(256) k_syrk(const DFront* __restrict__ fr, T* 
   const int n = d.n;
   const int64_t ld = d.ld;
   const int nt = (n - j1 + TILE - 1) / TILE;
-  if ((int)blockIdx.x >= nt * (nt + 1) / 2) return;
   int ti, tj;
-  tri_index(blockIdx.x, ti, tj);
+  if (jmax >= n) {
+    if ((int)blockIdx.x >= nt * (nt + 1) / 2) return;
+    tri_index(blockIdx.x, ti, tj);
+  } else {
+    const int nct = (jmax - j1 + TILE - 1) / TILE;
+    if (nct <= 0 || (int)blockIdx.x >= nt * nct) return;
+    ti = blockIdx.x % nt;
+    tj = blockIdx.x / nt;
+    if (tj > ti) return;
+  }
   const int rb = j1 + ti * TILE, cb = j1 + tj * TILE;
   T* K = Kar + d.K;
   __shared__ T As[KC][TILE + 4];
@@ -170,7 +182,7 @@ __global__ void __launch_bounds__(256) k_syrk(const DFront* __restrict__ fr, T* 
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int c = cb + tc + j;
-    if (c >= n) continue;
+    if (c >= n || c >= jmax) continue;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int r = rb + tr + i;
@@ -380,40 +392,82 @@ void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront
   HIF_CUDA_TRY(cudaMallocAsync(&d_lead, sizeof(DFront) * nfront, st));
   HIF_CUDA_TRY(cudaMemcpyAsync(d_lead, lead.data(), sizeof(DFront) * nfront,
                                cudaMemcpyHostToDevice, st));
-  for (int j0 = 0; j0 < pmax; j0 += NB) {
-    int nact = 0;
-    while (nact < nfront && lead[nact].p > j0) ++nact;
-    const int nm = lead[0].p;   // fronts are sorted by p, largest first
-    const int j1min = j0 + 1;   // smallest possible j1 among active fronts
-    const int chunks = std::max(1, ceil_div(std::max(0, nm - j1min), PANEL_ROWS));
-    int ntile = ceil_div(std::max(0, nm - j1min), TILE);
-    const int pairs = std::max(1, ntile * (ntile + 1) / 2);
-    // algorithmic counts of this step (only while profiling)
-    double pf = 0, pb = 0, sf = 0, sb = 0;
-    if (prof_enabled()) {
-      for (int f = 0; f < nact; ++f) {
-        const double jb = std::min(NB, lead[f].p - j0);
-        const double rest = lead[f].p - j0 - jb;
-        pf += jb * jb * jb / 3.0 + rest * jb * jb;
-        pb += sizeof(T) * (jb * jb / 2.0 + 2.0 * rest * jb);
-        sf += rest * (rest + 1.0) * jb;
-        sb += sizeof(T) * (rest * jb + rest * (rest + 1.0));
+  // two levels: inner panels of NB factor an outer block of NB2 columns and
+  // update only its remaining columns; the rows and columns right of the
+  // outer block then get one rank-NB2 update A22 -= L21 L21^T as a batched
+  // product (tensor cores for FP32)
+  constexpr int NB2 = 256;
+  const bool outer = pmax > NB2;
+  for (int J0 = 0; J0 < pmax; J0 += NB2) {
+    const int jend = outer ? J0 + NB2 : INT_MAX;
+    for (int j0 = J0; j0 < std::min(pmax, J0 + NB2); j0 += NB) {
+      int nact = 0;
+      while (nact < nfront && lead[nact].p > j0) ++nact;
+      const int nm = lead[0].p;   // fronts are sorted by p, largest first
+      const int j1min = j0 + 1;   // smallest possible j1 among active fronts
+      const int chunks = std::max(1, ceil_div(std::max(0, nm - j1min), PANEL_ROWS));
+      const int ntile = ceil_div(std::max(0, nm - j1min), TILE);
+      const int nctile = outer ? std::max(1, ceil_div(std::max(0, jend - j1min), TILE)) : 0;
+      const int grid = outer ? std::max(1, ntile * nctile) : std::max(1, ntile * (ntile + 1) / 2);
+      // algorithmic counts of this step (only while profiling)
+      double pf = 0, pb = 0, sf = 0, sb = 0;
+      if (prof_enabled()) {
+        for (int f = 0; f < nact; ++f) {
+          const double jb = std::min(NB, lead[f].p - j0);
+          const double rest = lead[f].p - j0 - jb;
+          const double cols = std::min<double>(rest, (double)std::min(jend, lead[f].p) - j0 - jb);
+          pf += jb * jb * jb / 3.0 + rest * jb * jb;
+          pb += sizeof(T) * (jb * jb / 2.0 + 2.0 * rest * jb);
+          sf += (2.0 * rest - cols + 1.0) * cols * jb;
+          sb += sizeof(T) * (rest * jb + (2.0 * rest - cols + 1.0) * cols);
+        }
+      }
+      for (int f0 = 0; f0 < nact; f0 += MAX_GRID_Y) {
+        const int nb = std::min(MAX_GRID_Y, nact - f0);
+        {
+          ProfScope ps("chol_panel", st, pf, pb);
+          k_panel<T><<<dim3(chunks, nb), PANEL_ROWS, 0, st>>>(d_lead + f0, Karena, Parena, j0,
+                                                              d_flags);
+          HIF_CHECK_LAUNCH();
+        }
+        {
+          ProfScope ps("chol_trailing_update", st, sf, sb);
+          k_syrk<T><<<dim3(grid, nb), 256, 0, st>>>(d_lead + f0, Karena, j0,
+                                                     outer ? jend : INT_MAX);
+          HIF_CHECK_LAUNCH();
+        }
       }
     }
-    for (int f0 = 0; f0 < nact; f0 += MAX_GRID_Y) {
-      const int nb = std::min(MAX_GRID_Y, nact - f0);
-      {
-        ProfScope ps("chol_panel", st, pf, pb);
-        k_panel<T><<<dim3(chunks, nb), PANEL_ROWS, 0, st>>>(d_lead + f0, Karena, Parena, j0,
-                                                            d_flags);
-        HIF_CHECK_LAUNCH();
-      }
-      {
-        ProfScope ps("chol_trailing_update", st, sf, sb);
-        k_syrk<T><<<dim3(pairs, nb), 256, 0, st>>>(d_lead + f0, Karena, j0);
-        HIF_CHECK_LAUNCH();
-      }
+    if (!outer) break;
+    // A22 -= L21 L21^T for the fronts that extend past the outer block
+    std::vector<GemmOp> uo;
+    for (int f = 0; f < nfront && lead[f].p > jend; ++f) {
+      const DFront& h = lead[f];
+      const int64_t ld = h.ld;
+      const int rest = h.p - jend;
+      uo.push_back(GemmOp{h.K + jend + (int64_t)J0 * ld, h.K + jend + (int64_t)J0 * ld,
+                          h.K + jend + (int64_t)jend * ld, rest, rest, NB2, (int)ld, (int)ld,
+                          (int)ld, 0, 1, -1.f, 1.f, 1, 0});
     }
+    if (uo.empty()) continue;
+    GemmOp* d_uo = nullptr;
+    HIF_CUDA_TRY(cudaMallocAsync(&d_uo, sizeof(GemmOp) * uo.size(), st));
+    HIF_CUDA_TRY(cudaMemcpyAsync(d_uo, uo.data(), sizeof(GemmOp) * uo.size(),
+                                 cudaMemcpyHostToDevice, st));
+    if constexpr (std::is_same<T, float>::value) {
+      if (use_tc) {
+        gemm_tc(d_uo, uo.data(), (int)uo.size(), reinterpret_cast<const float*>(Karena),
+                reinterpret_cast<const float*>(Karena), reinterpret_cast<float*>(Karena), d_flags,
+                st, "chol_block_update");
+      } else {
+        gemm_batched<T>(d_uo, uo.data(), (int)uo.size(), Karena, Karena, Karena, st,
+                        "chol_block_update");
+      }
+    } else {
+      gemm_batched<T>(d_uo, uo.data(), (int)uo.size(), Karena, Karena, Karena, st,
+                      "chol_block_update");
+    }
+    HIF_CUDA_TRY(cudaFreeAsync(d_uo, st));
   }
   HIF_CUDA_TRY(cudaFreeAsync(d_lead, st));
   // 2. Linv = L^{-1}: invert the NB x NB diagonal blocks, then merge
