@@ -356,9 +356,11 @@ void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Ab
   // S minimises the waves per unit of work, ceil(tiles S / capacity) / S,
   // with at least 16 chunks of K per share
   int S = 1;
-  if (!any_lower && nops <= 65535) {
-    const int cap = per_sm * nsm;
-    const int smax = std::max(1, std::min(8, kmin / (16 * kc)));
+  const int cap = per_sm * nsm;
+  if (!any_lower && nops <= 65535 && tiles < cap) {
+    // only launches that leave SMs idle; at most about two waves' worth
+    const int smax =
+        std::max(1, std::min({8, kmin / (16 * kc), ceil_div(2 * cap, std::max(1, tiles))}));
     double best = 1e30;
     for (int s = 1; s <= smax; ++s) {
       const double cost = (double)ceil_div(tiles * s, cap) / s;
