@@ -72,7 +72,11 @@ typedef struct {
                         HIF_PREC_FP32: factor blocks in float (ID column
                         norms still accumulated in double); hif_solve keeps
                         the residual r = f - A u in double. */
-  int use_graphs;    /* 1: capture each hif_apply sweep in a CUDA graph */
+  int use_graphs;    /* 1: the two sweeps of an apply (hif_apply, and the
+                        preconditioner inside hif_solve) are captured once
+                        per nrhs as a CUDA graph on a private stream and
+                        replayed on the caller's stream (not while the kernel
+                        profile is on); 0: launched one by one */
   double pcg_tol;    /* hif_solve stops when ||r||_2 <= pcg_tol ||f||_2 */
   int max_iter;      /* hif_solve iteration limit */
   int tensor_cores;  /* HIF_PREC_FP32 only.  1: the deep products of the

@@ -224,6 +224,52 @@ struct Factor : FactorBase {
   DevBuf y, work;               // apply buffers (grown on demand)
   int64_t work_cap = 0, y_cap = 0;
   int64_t work_stride = 0;
+  // with opt.use_graphs: the two sweeps of an apply (every stage forward,
+  // then backward) captured once per nrhs on a private stream and replayed
+  // on the caller's stream; the graphs name y and work, so they are dropped
+  // whenever those buffers grow
+  struct SweepGraph {
+    int nrhs;
+    cudaGraphExec_t exec;
+  };
+  std::vector<SweepGraph> graphs;
+  cudaStream_t cap_st = nullptr;
+
+  ~Factor() override {
+    drop_graphs();
+    if (cap_st) cudaStreamDestroy(cap_st);
+  }
+  void drop_graphs() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+  }
+  void sweeps(T* yv, T* w, int nrhs, cudaStream_t st) {
+    const int64_t N = (int64_t)n * n * n;
+    for (auto& s : stages) run_stage(s, true, yv, N, w, work_stride, nrhs, st);
+    for (auto it = stages.rbegin(); it != stages.rend(); ++it)
+      run_stage(*it, false, yv, N, w, work_stride, nrhs, st);
+  }
+  void sweeps_maybe_graph(T* yv, T* w, int nrhs, cudaStream_t st) {
+    if (!opt.use_graphs || prof_enabled()) {
+      sweeps(yv, w, nrhs, st);
+      return;
+    }
+    cudaGraphExec_t exec = nullptr;
+    for (auto& g : graphs)
+      if (g.nrhs == nrhs) exec = g.exec;
+    if (!exec) {
+      if (!cap_st) HIF_CUDA_TRY(cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking));
+      cudaGraph_t graph = nullptr;
+      HIF_CUDA_TRY(cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal));
+      sweeps(yv, w, nrhs, cap_st);
+      HIF_CUDA_TRY(cudaStreamEndCapture(cap_st, &graph));
+      const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      HIF_CUDA_TRY(e);
+      graphs.push_back(SweepGraph{nrhs, exec});
+    }
+    HIF_CUDA_TRY(cudaGraphLaunch(exec, st));
+  }
 
   void run_stage(Stage& s, bool fwd, T* yv, int64_t ys, T* w, int64_t vs, int nrhs,
                  cudaStream_t st) {
@@ -244,19 +290,19 @@ struct Factor : FactorBase {
   void apply(const double* f_dev, double* u_dev, int nrhs, cudaStream_t st) override {
     const int64_t N = (int64_t)n * n * n;
     if (y_cap < N * nrhs) {
+      drop_graphs();
       y.alloc(sizeof(T) * N * nrhs, &mem);
       y_cap = N * nrhs;
     }
     if (work_cap < work_stride * nrhs) {
+      drop_graphs();
       work.alloc(sizeof(T) * std::max<int64_t>(1, work_stride * nrhs), &mem);
       work_cap = work_stride * nrhs;
     }
     T* yv = y.as<T>();
     T* w = work.as<T>();
     vec_convert_in<T>(f_dev, yv, N * nrhs, st);
-    for (auto& s : stages) run_stage(s, true, yv, N, w, work_stride, nrhs, st);
-    for (auto it = stages.rbegin(); it != stages.rend(); ++it)
-      run_stage(*it, false, yv, N, w, work_stride, nrhs, st);
+    sweeps_maybe_graph(yv, w, nrhs, st);
     vec_convert_out<T>(yv, u_dev, N * nrhs, st);
   }
 
@@ -274,9 +320,7 @@ struct Factor : FactorBase {
     T* yv = static_cast<T*>(scratch);
     T* w = reinterpret_cast<T*>(static_cast<char*>(scratch) + round256(sizeof(T) * N * nrhs));
     vec_convert_in<T>(f_dev, yv, N * nrhs, st);
-    for (auto& s : stages) run_stage(s, true, yv, N, w, work_stride, nrhs, st);
-    for (auto it = stages.rbegin(); it != stages.rend(); ++it)
-      run_stage(*it, false, yv, N, w, work_stride, nrhs, st);
+    sweeps(yv, w, nrhs, st);
     vec_convert_out<T>(yv, u_dev, N * nrhs, st);
   }
 };

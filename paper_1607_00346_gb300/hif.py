@@ -262,11 +262,11 @@ class Handle:
 
 def factor(n: int, m: int, a, b=None, b_const: float = 0.0, eps: float = 1e-6,
            precision: int = PREC_FP64, pcg_tol: float = 1e-10, max_iter: int = 200,
-           stream=None, tensor_cores: bool = True) -> Handle:
+           stream=None, tensor_cores: bool = True, use_graphs: bool = True) -> Handle:
     """hif_factor: a (and b) are n^3 float64 arrays, host or device."""
     g = Grid(n, m, 0)
     o = default_options(eps=eps, precision=precision, pcg_tol=pcg_tol, max_iter=max_iter,
-                        tensor_cores=int(bool(tensor_cores)))
+                        tensor_cores=int(bool(tensor_cores)), use_graphs=int(bool(use_graphs)))
     ap, _ka = _ptr(a)
     bp, _kb = _ptr(b)
     out = ctypes.c_void_p()

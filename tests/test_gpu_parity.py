@@ -202,3 +202,23 @@ def test_paper_example_fields_within_2x_oracle(H, field, n, eps):
     its, rel = h.solve(_dev(f), u)
     r = f[0] - A @ u.cpu().numpy()[0]
     assert rel[0] <= 1e-10 and np.linalg.norm(r) <= 1.0000001e-10 * np.linalg.norm(f[0])
+
+
+def test_graph_replayed_apply_is_bitwise_the_launched_one(H):
+    # the apply sweeps captured in a CUDA graph run the same kernels in the
+    # same order as the launched sweeps: identical results, also on replay
+    n = 32
+    a = _coeff(n, 951)
+    f = inputs.normal_rhs(n, 3, 952)
+    hg = H.factor(n, 4, _dev(a), eps=1e-6, precision=1, use_graphs=True)
+    hl = H.factor(n, 4, _dev(a), eps=1e-6, precision=1, use_graphs=False)
+    ug1 = _gpu_apply(hg, f)
+    ug2 = _gpu_apply(hg, f)          # replay of the captured graph
+    ul = _gpu_apply(hl, f)
+    assert np.array_equal(ug1, ul) and np.array_equal(ug2, ul)
+    u1 = torch.zeros(f.shape, dtype=torch.float64, device="cuda")
+    u2 = torch.zeros(f.shape, dtype=torch.float64, device="cuda")
+    its1, _ = hg.solve(_dev(f), u1)
+    its2, _ = hl.solve(_dev(f), u2)
+    torch.cuda.synchronize()
+    assert its1 == its2 and torch.equal(u1, u2)
