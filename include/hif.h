@@ -206,6 +206,22 @@ hif_status hif_profile_end(hif_kernel_profile* out, int cap, int* count);
 /* Release every resource of the handle (NULL is ignored). */
 void hif_destroy(hif_handle h);
 
+/*
+ * hif_save / hif_load -- factor persistence (no counterpart in the paper: a
+ * serving process keeps factored operators across restarts).
+ *   hif_save writes the handle's factor (every stage's device arrays and
+ *   mat-vec lists, the operator, options and statistics) to `path`, a
+ *   versioned binary file; it synchronises the device first.
+ *   hif_load reads such a file into a new handle (*out; NULL on error); the
+ *   handle applies and solves exactly as the saved one (bitwise the same
+ *   results).  Files are read only by the build that wrote them (the
+ *   option and statistics layouts are checked).
+ * Errors: INVALID_ARG (NULL arguments, unreadable or unwritable path, not a
+ * factor file, another version, truncated or corrupt file), OOM, CUDA.
+ */
+hif_status hif_save(hif_handle h, const char* path);
+hif_status hif_load(const char* path, hif_handle* out);
+
 /* Message for the calling thread's last failed call ("" if none). */
 const char* hif_last_error(void);
 

@@ -1142,6 +1142,163 @@ void* noalloc_scratch_address() {
 
 }  // namespace
 
+namespace hif {
+namespace {
+
+// ---- factor files: a versioned binary image of a handle ------------------------
+// Layout: "HIFF", format version, sizes of the option/stats structs (a file
+// is read only by the build that wrote it), the scalars of the factor, the
+// operator, then every stage: its scalars, its device arrays (byte count +
+// bytes) and its mat-vec lists (count + descriptors).
+constexpr uint32_t kFileVersion = 1;
+
+struct FileOut {
+  std::FILE* f = nullptr;
+  explicit FileOut(const char* path) : f(std::fopen(path, "wb")) {
+    if (!f) throw Error{HIF_ERR_INVALID_ARG, std::string("cannot open ") + path + " for writing"};
+  }
+  ~FileOut() { if (f) std::fclose(f); }
+  void raw(const void* p, size_t n) {
+    if (n && std::fwrite(p, 1, n, f) != n) throw Error{HIF_ERR_INVALID_ARG, "write failed"};
+  }
+  template <typename U> void put(const U& v) { raw(&v, sizeof(U)); }
+  void buf(const DevBuf& b) {
+    const uint64_t n = b.bytes();
+    put(n);
+    if (!n) return;
+    std::vector<unsigned char> h(n);
+    HIF_CUDA_TRY(cudaMemcpy(h.data(), b.as<void>(), n, cudaMemcpyDeviceToHost));
+    raw(h.data(), n);
+  }
+  void list(const GemvList& gl) {
+    put(gl.trans);
+    put(gl.mat);
+    const uint64_t c = gl.h.size();
+    put(c);
+    raw(gl.h.data(), sizeof(GemvOp) * c);
+  }
+};
+
+struct FileIn {
+  std::FILE* f = nullptr;
+  explicit FileIn(const char* path) : f(std::fopen(path, "rb")) {
+    if (!f) throw Error{HIF_ERR_INVALID_ARG, std::string("cannot open ") + path};
+  }
+  ~FileIn() { if (f) std::fclose(f); }
+  void raw(void* p, size_t n) {
+    if (n && std::fread(p, 1, n, f) != n) throw Error{HIF_ERR_INVALID_ARG, "truncated factor file"};
+  }
+  template <typename U> U get() {
+    U v;
+    raw(&v, sizeof(U));
+    return v;
+  }
+  void buf(DevBuf& b, MemStats* ms) {
+    const uint64_t n = get<uint64_t>();
+    if (n > (uint64_t(1) << 40)) throw Error{HIF_ERR_INVALID_ARG, "corrupt factor file"};
+    b.alloc(n, ms);
+    if (!n) return;
+    std::vector<unsigned char> h(n);
+    raw(h.data(), n);
+    HIF_CUDA_TRY(cudaMemcpy(b.as<void>(), h.data(), n, cudaMemcpyHostToDevice));
+  }
+  void list(GemvList& gl, MemStats* ms) {
+    gl.trans = get<int>();
+    gl.mat = get<int>();
+    const uint64_t c = get<uint64_t>();
+    if (c > (uint64_t(1) << 32)) throw Error{HIF_ERR_INVALID_ARG, "corrupt factor file"};
+    gl.h.resize(c);
+    raw(gl.h.data(), sizeof(GemvOp) * c);
+    gl.d.alloc(sizeof(GemvOp) * c, ms);
+    if (c)
+      HIF_CUDA_TRY(cudaMemcpy(gl.d.as<void>(), gl.h.data(), sizeof(GemvOp) * c,
+                              cudaMemcpyHostToDevice));
+  }
+};
+
+template <typename T>
+void save_factor(const Factor<T>& F, FileOut& o) {
+  o.put(F.n);
+  o.put(F.m);
+  o.put(F.L);
+  o.put(F.precision);
+  o.put(F.eps);
+  o.put(F.opt);
+  o.put(F.stats);
+  o.put(F.work_stride);
+  o.buf(F.cpl);
+  o.buf(F.diag);
+  const uint64_t ns = F.stages.size();
+  o.put(ns);
+  for (const Stage& s : F.stages) {
+    o.put(s.kind);
+    o.put(s.level);
+    o.put(s.nidx);
+    o.put(s.nset);
+    o.put(s.nacc);
+    o.put(s.entries);
+    o.buf(s.idx);
+    o.buf(s.panels);
+    o.buf(s.tmats);
+    o.buf(s.set_g);
+    o.buf(s.set_p);
+    o.buf(s.acc_tgt);
+    o.buf(s.acc_ptr);
+    o.buf(s.acc_src);
+    o.put((uint32_t)s.fwd.size());
+    for (const auto& gl : s.fwd) o.list(gl);
+    o.put((uint32_t)s.bwd.size());
+    for (const auto& gl : s.bwd) o.list(gl);
+  }
+}
+
+template <typename T>
+void load_factor(Factor<T>& F, FileIn& in) {
+  F.n = in.get<int>();
+  F.m = in.get<int>();
+  F.L = in.get<int>();
+  F.precision = in.get<int>();
+  F.eps = in.get<double>();
+  F.opt = in.get<hif_options>();
+  F.stats = in.get<hif_stats>();
+  F.work_stride = in.get<int64_t>();
+  if (F.n < 1 || F.n > 1024 || F.L < 0 || F.L > 16)
+    throw Error{HIF_ERR_INVALID_ARG, "corrupt factor file"};
+  in.buf(F.cpl, &F.mem);
+  in.buf(F.diag, &F.mem);
+  const uint64_t ns = in.get<uint64_t>();
+  if (ns > 4096) throw Error{HIF_ERR_INVALID_ARG, "corrupt factor file"};
+  F.stages.resize(ns);
+  for (Stage& s : F.stages) {
+    s.kind = in.get<int>();
+    s.level = in.get<int>();
+    s.nidx = in.get<int64_t>();
+    s.nset = in.get<int64_t>();
+    s.nacc = in.get<int64_t>();
+    s.entries = in.get<int64_t>();
+    in.buf(s.idx, &F.mem);
+    in.buf(s.panels, &F.mem);
+    in.buf(s.tmats, &F.mem);
+    in.buf(s.set_g, &F.mem);
+    in.buf(s.set_p, &F.mem);
+    in.buf(s.acc_tgt, &F.mem);
+    in.buf(s.acc_ptr, &F.mem);
+    in.buf(s.acc_src, &F.mem);
+    const uint32_t nf = in.get<uint32_t>();
+    if (nf > 8) throw Error{HIF_ERR_INVALID_ARG, "corrupt factor file"};
+    s.fwd.resize(nf);
+    for (auto& gl : s.fwd) in.list(gl, &F.mem);
+    const uint32_t nb = in.get<uint32_t>();
+    if (nb > 8) throw Error{HIF_ERR_INVALID_ARG, "corrupt factor file"};
+    s.bwd.resize(nb);
+    for (auto& gl : s.bwd) in.list(gl, &F.mem);
+  }
+  F.stats.factor_bytes = F.mem.cur;
+}
+
+}  // namespace
+}  // namespace hif
+
 extern "C" {
 
 void hif_default_options(hif_options* o) {
@@ -1320,5 +1477,57 @@ size_t hif_predict_bytes(const hif_grid* grid, const hif_options* opt) {
 }
 
 void hif_destroy(hif_handle h) { delete h; }
+
+hif_status hif_save(hif_handle h, const char* path) {
+  HIF_API_BEGIN
+  if (!h || !path) throw Error{HIF_ERR_INVALID_ARG, "handle and path must not be NULL"};
+  HIF_CUDA_TRY(cudaDeviceSynchronize());
+  hif::FileOut o(path);
+  o.raw("HIFF", 4);
+  o.put(hif::kFileVersion);
+  o.put((uint32_t)sizeof(hif_options));
+  o.put((uint32_t)sizeof(hif_stats));
+  if (h->f->precision == HIF_PREC_FP32)
+    hif::save_factor(*static_cast<hif::Factor<float>*>(h->f.get()), o);
+  else
+    hif::save_factor(*static_cast<hif::Factor<double>*>(h->f.get()), o);
+  return HIF_OK;
+  HIF_API_END
+}
+
+hif_status hif_load(const char* path, hif_handle* out) {
+  if (out) *out = nullptr;
+  HIF_API_BEGIN
+  if (!path || !out) throw Error{HIF_ERR_INVALID_ARG, "path and out must not be NULL"};
+  hif::FileIn in(path);
+  char magic[4];
+  in.raw(magic, 4);
+  if (std::memcmp(magic, "HIFF", 4) != 0) throw Error{HIF_ERR_INVALID_ARG, "not a factor file"};
+  if (in.get<uint32_t>() != hif::kFileVersion || in.get<uint32_t>() != sizeof(hif_options) ||
+      in.get<uint32_t>() != sizeof(hif_stats))
+    throw Error{HIF_ERR_INVALID_ARG, "factor file written by another version"};
+  auto hh = std::make_unique<hif_handle_s>();
+  // the precision decides the factor's word size: peek at it after n, m, L
+  const long pos = std::ftell(in.f);
+  in.get<int>();
+  in.get<int>();
+  in.get<int>();
+  const int prec = in.get<int>();
+  std::fseek(in.f, pos, SEEK_SET);
+  if (prec == HIF_PREC_FP32) {
+    auto* F = new hif::Factor<float>();
+    hh->f.reset(F);
+    hif::load_factor(*F, in);
+  } else if (prec == HIF_PREC_FP64) {
+    auto* F = new hif::Factor<double>();
+    hh->f.reset(F);
+    hif::load_factor(*F, in);
+  } else {
+    throw Error{HIF_ERR_INVALID_ARG, "corrupt factor file"};
+  }
+  *out = hh.release();
+  return HIF_OK;
+  HIF_API_END
+}
 
 }  // extern "C"

@@ -59,7 +59,7 @@ _lib = None
 EXPORTS = ["hif_default_options", "hif_factor", "hif_apply", "hif_apply_noalloc",
            "hif_residual", "hif_solve",
            "hif_query_stats", "hif_predict_bytes", "hif_profile_begin", "hif_profile_end",
-           "hif_destroy", "hif_last_error", "hif_version"]
+           "hif_destroy", "hif_last_error", "hif_version", "hif_save", "hif_load"]
 
 
 class KernelProfile(ctypes.Structure):
@@ -106,6 +106,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.hif_profile_end.restype = i
     lib.hif_destroy.argtypes = [vp]
     lib.hif_destroy.restype = None
+    lib.hif_save.argtypes = [vp, ctypes.c_char_p]
+    lib.hif_save.restype = i
+    lib.hif_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp)]
+    lib.hif_load.restype = i
     lib.hif_last_error.argtypes = []
     lib.hif_last_error.restype = ctypes.c_char_p
     lib.hif_version.argtypes = []
@@ -191,6 +195,10 @@ class Handle:
             load().hif_destroy(self._h)
             self._h = None
 
+    def save(self, path: str):
+        """hif_save: write the factor to a file (hif_load reads it back)."""
+        _check(load().hif_save(self._h, os.fsencode(path)))
+
     def __del__(self):
         try:
             self.close()
@@ -258,6 +266,15 @@ class Handle:
                     factor_bytes=s.factor_bytes, peak_bytes=s.peak_bytes,
                     stored_entries=s.stored_entries, kernel_launches=s.kernel_launches,
                     apply_launches=s.apply_launches)
+
+
+def load_factor(path: str) -> Handle:
+    """hif_load: a handle from a file written by Handle.save."""
+    out = ctypes.c_void_p()
+    _check(load().hif_load(os.fsencode(path), ctypes.byref(out)))
+    s = Stats()
+    _check(load().hif_query_stats(out, ctypes.byref(s)))
+    return Handle(out, s.n)
 
 
 def factor(n: int, m: int, a, b=None, b_const: float = 0.0, eps: float = 1e-6,

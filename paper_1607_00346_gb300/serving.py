@@ -9,7 +9,9 @@ right-hand sides.  The server
   factorizations already on the device; the least recently used idle
   operators are released to make room;
 * keeps factored operators resident, so later requests for the same operator
-  skip the factorization;
+  skip the factorization; with a spill directory, an evicted operator is
+  written to disk (hif_save) and brought back by hif_load when it is asked
+  for again;
 * batches all waiting requests for one operator into a single multi-column
   PCG solve (one apply launch sequence for all their right-hand sides);
 * runs admitted jobs on several worker threads, each with its own CUDA stream,
@@ -107,6 +109,13 @@ class HifBackend:
     def release(self, h):
         h.close()
 
+    def save(self, h, path: str):
+        h.save(path)
+
+    def load(self, path: str, stream):
+        h = self.hif.load_factor(path)
+        return h, int(h.stats()["factor_bytes"])
+
 
 @dataclass
 class _Resident:
@@ -116,10 +125,14 @@ class _Resident:
 
 
 class Server:
-    def __init__(self, backend, mem_budget: int, workers: int = 4):
+    def __init__(self, backend, mem_budget: int, workers: int = 4, spill_dir: str | None = None):
         self.be = backend
         self.budget = int(mem_budget)
         self.workers = workers
+        # with spill_dir, an evicted operator is written to disk (hif_save)
+        # and a later request for it loads the file instead of refactoring
+        self.spill_dir = spill_dir
+        self.spilled: dict = {}    # op_key -> (path, bytes)
         self.lock = threading.Condition()
         self.resident: OrderedDict = OrderedDict()   # op_key -> _Resident (LRU order)
         self.reserved = 0          # bytes of factorizations in progress
@@ -140,6 +153,11 @@ class Server:
             if victim is None:
                 return False
             r = self.resident.pop(victim)
+            if self.spill_dir is not None:
+                import os
+                path = os.path.join(self.spill_dir, "op_%d_%d_%d.hiff" % victim)
+                self.be.save(r.handle, path)
+                self.spilled[victim] = (path, r.bytes)
             self.be.release(r.handle)
             self.log.append((time.perf_counter(), "evict", victim))
         return True
@@ -161,7 +179,8 @@ class Server:
                     self.pending.remove(r)
                 self.inflight_keys.add(key)
                 return key, batch, 0
-            need = self.be.predict_bytes(req.n, req.m)
+            spilled = self.spilled.get(key)
+            need = spilled[1] if spilled else self.be.predict_bytes(req.n, req.m)
             if need > self.budget:
                 # can never be admitted: fail these requests and move on
                 for r in batch:
@@ -196,7 +215,13 @@ class Server:
                 r.t_start = t0
             try:
                 if reserved:
-                    h, fbytes = self.be.factor(n, m, seed, stream)
+                    with self.lock:
+                        spilled = self.spilled.pop(key, None)
+                    if spilled:
+                        h, fbytes = self.be.load(spilled[0], stream)
+                        self.log.append((time.perf_counter(), "load", key))
+                    else:
+                        h, fbytes = self.be.factor(n, m, seed, stream)
                     with self.lock:
                         self.reserved -= reserved
                         reserved = 0

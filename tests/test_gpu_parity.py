@@ -222,3 +222,23 @@ def test_graph_replayed_apply_is_bitwise_the_launched_one(H):
     its2, _ = hl.solve(_dev(f), u2)
     torch.cuda.synchronize()
     assert its1 == its2 and torch.equal(u1, u2)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_saved_and_loaded_factor_is_bitwise_the_same(H, tmp_path, precision):
+    n = 16
+    a = _coeff(n, 971)
+    f = inputs.normal_rhs(n, 2, 972)
+    h = H.factor(n, 4, _dev(a), b_const=0.1, eps=1e-6, precision=precision)
+    path = str(tmp_path / "f.hiff")
+    h.save(path)
+    h2 = H.load_factor(path)
+    assert np.array_equal(_gpu_apply(h, f), _gpu_apply(h2, f))
+    st, st2 = h.stats(), h2.stats()
+    assert st["root_size"] == st2["root_size"] and st["stored_entries"] == st2["stored_entries"]
+    u1 = torch.zeros(f.shape, dtype=torch.float64, device="cuda")
+    u2 = torch.zeros(f.shape, dtype=torch.float64, device="cuda")
+    its1, _ = h.solve(_dev(f), u1)
+    its2, _ = h2.solve(_dev(f), u2)
+    torch.cuda.synchronize()
+    assert its1 == its2 and torch.equal(u1, u2)

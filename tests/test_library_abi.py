@@ -45,6 +45,24 @@ def test_host_only_entry_points(lib):
     assert hif.load().hif_version().startswith(b"hif-gb300")
 
 
+def test_load_rejects_bad_files(tmp_path):
+    from paper_1607_00346_gb300 import hif
+    hif.load()
+    with pytest.raises(hif.HifError) as e:
+        hif.load_factor(str(tmp_path / "missing.hiff"))
+    assert e.value.status == 1
+    bad = tmp_path / "bad.hiff"
+    bad.write_bytes(b"NOTAFACTORFILE")
+    with pytest.raises(hif.HifError) as e:
+        hif.load_factor(str(bad))
+    assert e.value.status == 1
+    trunc = tmp_path / "trunc.hiff"
+    trunc.write_bytes(b"HIFF\x01\x00\x00\x00")
+    with pytest.raises(hif.HifError) as e:
+        hif.load_factor(str(trunc))
+    assert e.value.status == 1
+
+
 def test_invalid_grid_rejected_before_any_device_work():
     from paper_1607_00346_gb300 import hif
     import numpy as np

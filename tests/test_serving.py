@@ -29,6 +29,7 @@ class FakeBackend:
         self.live = 0
         self.peak = 0
         self.factorizations = []
+        self.loads = []
         self.solve_batches = []
 
     def new_stream(self):
@@ -56,6 +57,19 @@ class FakeBackend:
         h.released = True
         with self.mu:
             self.live -= h.n ** 3 * self.per_dof
+
+    def save(self, h, path):
+        with open(path, "w") as fh:
+            fh.write("%d %d" % (h.n, h.seed))
+
+    def load(self, path, stream):
+        with open(path) as fh:
+            n, seed = map(int, fh.read().split())
+        with self.mu:
+            self.live += n ** 3 * self.per_dof
+            self.peak = max(self.peak, self.live)
+            self.loads.append((n, seed))
+        return FakeHandle(n, seed), n ** 3 * self.per_dof
 
 
 def _check_results(done):
@@ -109,6 +123,24 @@ def test_oversized_request_is_refused_and_others_served():
     _check_results(srv.done)
 
 
+def test_evicted_operators_spill_to_disk_and_come_back(tmp_path):
+    be = FakeBackend(per_dof=100)
+    # room for one 16^3 operator at a time: A, B, A, B ... forces evictions
+    srv = Server(be, mem_budget=16 ** 3 * 100 + 10, workers=1, spill_dir=str(tmp_path))
+    reqs = []
+    for i in range(6):
+        seed = 1 if i % 2 == 0 else 2
+        reqs.append(Request(rid=i, n=16, seed=seed, nrhs=1, arrival=0.05 * i))
+    srv.run(reqs, realtime=True)
+    srv.release_all()
+    assert len(srv.done) == 6 and not srv.failed
+    _check_results(srv.done)
+    # each operator is factored once; later uses come back from disk
+    assert sorted(be.factorizations) == [(16, 1), (16, 2)]
+    assert len(be.loads) >= 1
+    assert be.peak <= srv.budget
+
+
 def test_leaf_sizes():
     assert [leaf_size(n) for n in (16, 32, 48, 64, 96, 128)] == [4, 4, 3, 4, 3, 4]
 
@@ -136,3 +168,33 @@ def test_gpu_result_same_alone_and_in_the_mix():
         alone.release_all()
         # the same factorization and the same solve: identical up to rounding
         assert np.allclose(a.u, r.u, rtol=0, atol=1e-12 * np.abs(a.u).max())
+
+
+@pytest.mark.gpu
+def test_gpu_spilled_operator_gives_the_same_solution(tmp_path):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_00346_gb300 import build
+    from paper_1607_00346_gb300.serving import HifBackend
+    build.build_library()
+    be = HifBackend(eps=1e-6, precision=1, keep_u=True)
+    one = be.predict_bytes(16, 4)
+    # room for one new operator next to a resident one (admission uses the
+    # predicted footprint): alternating requests evict, spill and reload
+    srv = Server(be, mem_budget=int(1.05 * one), workers=1, spill_dir=str(tmp_path))
+    reqs = [Request(rid=i, n=16, seed=11 + (i % 2), nrhs=2, arrival=0.3 * i) for i in range(4)]
+    st = srv.run(reqs)
+    srv.release_all()
+    assert st["requests"] == 4 and st["failed"] == 0
+    assert any(ev == "load" for _, ev, _ in srv.log)
+    first = {}
+    for r in sorted(srv.done, key=lambda r: r.rid):
+        assert max(r.relres) <= 1e-10
+        alone = Server(be, mem_budget=8 << 30, workers=1)
+        alone.run([Request(rid=r.rid, n=r.n, m=r.m, seed=r.seed, nrhs=r.nrhs, arrival=0.0)])
+        a = alone.done[0]
+        alone.release_all()
+        # a reloaded factor is bitwise the saved one: the same solution
+        assert np.array_equal(a.u, r.u)
+        first.setdefault(r.seed, r)
