@@ -69,11 +69,12 @@ FP64_ALU_PEAK_TFLOPS = 1.25
 # algebra, or HBM streams (the ID's trailing-matrix passes and the apply's
 # mat-vecs read each entry once per step / per sweep)
 KERNEL_BOUND = {
-    "gemm_tc": "tensor", "id_rowreduce_w1": "tensor",
+    "gemm_tc": "tensor",
     "id_cpqr": "hbm", "id_rowreduce_panel": "hbm", "apply_gemv_n": "hbm", "apply_gemv_t": "hbm",
     "skel_gather": "hbm", "merge_children": "hbm", "spmv": "hbm", "residual": "hbm",
+    "id_rowreduce_update": "hbm",
     "chol_panel": "alu", "chol_trailing_update": "alu", "gemm_batched": "alu",
-    "trtri_merge": "alu", "id_cpqr_smem": "alu", "id_rowreduce_update": "alu",
+    "trtri_merge": "alu", "id_cpqr_smem": "alu", "id_rowreduce_w1": "alu",
     "skel_z_products": "alu", "chol_block_update": "tensor",
 }
 

@@ -14,7 +14,8 @@
 //     columns (norms accumulated in double), the explicit reflector matrix V
 //     and the triangular T of the compact form Q = I - V T V^T (forward
 //     accumulation: T_{j+1} = [T_j, -tau_j T_j V_j^T v_j; 0, tau_j]);
-//   * trailing columns: W = V^T A, W = T^T W, A -= V W (batched GEMMs).
+//   * trailing columns: W = T^T V^T A and A -= V W, two kernels that stream
+//     the trailing columns from HBM once each (k_qr_w1/k_qr_w2, k_qr_update).
 #include <algorithm>
 #include <cstdlib>
 #include <type_traits>
@@ -40,7 +41,7 @@ constexpr int QR_WARPS = QR_THREADS / 32;
 struct QRDesc {
   int64_t A;     // matrix (m x n, ld) offset in the gather arena
   int64_t V;     // reflector block (m x QB, ld = m) offset in the V arena
-  int64_t W;     // two QB x n work blocks (ld = QB) offset in the W arena
+  int64_t W;     // QB x n work block (ld = QB) offset in the W arena
   int64_t Tt;    // QB x QB offset in the T arena
   int m, n, ld;
   int pad;
@@ -329,6 +330,268 @@ __global__ void k_extract_r(const QRDesc* __restrict__ ds, const int64_t* __rest
   Rar[roff[blockIdx.y] + e] = r <= c ? Gar[d.A + r + (int64_t)c * d.ld] : T(0);
 }
 
+// ---- trailing columns of a panel: W = T^T V^T A_t, A_t -= V W ---------------
+// Both products stream A_t (the (m-p) x nt columns right of the panel) from
+// HBM once; V (m-p) x jb and W (jb x nt) are small and come from L2.
+//
+// eight consecutive values from 16-byte aligned shared memory
+__device__ __forceinline__ void load8(float (&x)[8], const float* p) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  const float4 b = *reinterpret_cast<const float4*>(p + 4);
+  x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+  x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+}
+__device__ __forceinline__ void load8(double (&x)[8], const double* p) {
+#pragma unroll
+  for (int i = 0; i < 8; i += 2) {
+    const double2 a = *reinterpret_cast<const double2*>(p + i);
+    x[i] = a.x;
+    x[i + 1] = a.y;
+  }
+}
+
+// asynchronous copy of one element global -> shared (zero when !ok)
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool ok) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+                 "r"(ok ? 4 : 0)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src),
+                 "r"(ok ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// k_qr_w1: partial V^T A_t over one split of the rows.  A CTA owns 64
+// columns and a contiguous range of 32-row chunks, streamed through a ring
+// of W1_ST shared-memory stages by asynchronous copies (W1_ST - 1 chunks in
+// flight while one is multiplied).  Its 8 warps take 4 rows of each chunk,
+// every lane an 8 x 8 block of the 32 x 64 partial (8 consecutive V columns
+// by 8 consecutive A columns, read as 16-byte vectors), and the 8 warps'
+// partials are added in warp order at the end.  Partial s of front f goes
+// to Wp + wpo[f] + s QB nt (QB x nt, ld = QB).
+constexpr int W1_NC = 64;
+constexpr int W1_KC = 32;
+constexpr int W1_ST = 4;
+constexpr int W1_THREADS = 256;
+constexpr int W1_AP = W1_NC + 4;   // row pitches of a staged chunk (16-byte rows)
+constexpr int W1_VP = QB + 4;
+constexpr int W1_STAGE = W1_KC * (W1_AP + W1_VP);   // elements per stage
+
+template <typename T>
+constexpr size_t w1_smem_bytes() {
+  const size_t ring = sizeof(T) * (size_t)W1_ST * W1_STAGE;
+  const size_t red = sizeof(T) * (size_t)(W1_THREADS / 32) * QB * W1_NC;
+  return ring > red ? ring : red;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(W1_THREADS, sizeof(T) == 4 ? 2 : 1)
+    k_qr_w1(const QRDesc* __restrict__ ds, const T* __restrict__ Gar, const T* __restrict__ Var,
+            T* Wp, const int64_t* __restrict__ wpo, int p, int S) {
+  const QRDesc d = ds[blockIdx.y];
+  if (p >= d.n) return;
+  const int jb = min(QB, d.n - p);
+  const int nt = d.n - p - jb;
+  const int c0 = (int)(blockIdx.x / S) * W1_NC, s = (int)(blockIdx.x % S);
+  if (nt <= 0 || c0 >= nt) return;
+  const int mp = d.m - p;
+  const int nch = (mp + W1_KC - 1) / W1_KC;
+  const int kc0 = (int)((int64_t)nch * s / S), kc1 = (int)((int64_t)nch * (s + 1) / S);
+  const T* A = Gar + d.A + p + (int64_t)(p + jb) * d.ld;   // A_t(0, 0)
+  const T* V = Var + d.V;                                   // V(r, j) = V[r + j m]
+  extern __shared__ __align__(16) unsigned char w1sm[];
+  T* ring = reinterpret_cast<T*>(w1sm);   // stage: As[k W1_AP + c], then Vs[k W1_VP + j]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lv = lane & 3, la = lane >> 2;                  // V columns lv*8+i, A columns la*8+jj
+  // thread tid copies row tid % W1_KC of a chunk, A and V columns
+  // tid / W1_KC + CS q
+  constexpr int NQA = W1_NC * W1_KC / W1_THREADS, NQV = W1_KC * QB / W1_THREADS;
+  constexpr int CS = W1_THREADS / W1_KC;
+  const int sk = tid % W1_KC, sc = tid / W1_KC;
+  auto issue = [&](int kc) {
+    if (kc < kc1) {
+      T* As = ring + (size_t)((kc - kc0) % W1_ST) * W1_STAGE;
+      T* Vs = As + W1_KC * W1_AP;
+      const int r = kc * W1_KC + sk;
+#pragma unroll
+      for (int q = 0; q < NQA; ++q) {
+        const int cc = c0 + sc + CS * q;
+        const bool ok = r < mp && cc < nt;
+        cp_async_elem(As + sk * W1_AP + sc + CS * q, ok ? A + r + (int64_t)cc * d.ld : A, ok);
+      }
+#pragma unroll
+      for (int q = 0; q < NQV; ++q) {
+        const int j = sc + CS * q;
+        const bool ok = r < mp && j < jb;
+        cp_async_elem(Vs + sk * W1_VP + j, ok ? V + r + (int64_t)j * d.m : V, ok);
+      }
+    }
+    cp_async_commit();   // one group per chunk slot, empty past the end
+  };
+  T acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) acc[i][jj] = T(0);
+#pragma unroll
+  for (int i = 0; i < W1_ST - 1; ++i) issue(kc0 + i);
+  for (int kc = kc0; kc < kc1; ++kc) {
+    cp_async_wait<W1_ST - 2>();   // this thread's copies of chunk kc are done
+    __syncthreads();              // everyone's are; stage (kc - 1) is free again
+    issue(kc + W1_ST - 1);
+    const T* As = ring + (size_t)((kc - kc0) % W1_ST) * W1_STAGE;
+    const T* Vs = As + W1_KC * W1_AP;
+#pragma unroll 1
+    for (int kk = 0; kk < W1_KC / 8; ++kk) {
+      const int k = warp * (W1_KC / 8) + kk;
+      T v[8], a[8];
+      load8(v, Vs + k * W1_VP + lv * 8);
+      load8(a, As + k * W1_AP + la * 8);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fma(v[i], a[jj], acc[i][jj]);
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  // the 8 warps' partials, added in warp order
+  T* R = reinterpret_cast<T*>(w1sm);   // R[w QB W1_NC + i + QB c]
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj)
+      R[(size_t)warp * QB * W1_NC + (lv * 8 + i) + QB * (la * 8 + jj)] = acc[i][jj];
+  __syncthreads();
+  T* out = Wp + wpo[blockIdx.y] + (int64_t)s * QB * nt;
+  for (int e = tid; e < QB * W1_NC; e += W1_THREADS) {
+    const int i = e % QB, c = e / QB;
+    if (c0 + c >= nt) continue;
+    T t = R[e];
+    for (int w = 1; w < W1_THREADS / 32; ++w) t += R[(size_t)w * QB * W1_NC + e];
+    out[i + (int64_t)(c0 + c) * QB] = t;
+  }
+}
+
+// k_qr_w2: W = T^T (sum of the S partials, in split order), one thread per
+// column; W goes to the front's work block (War + W, ld = QB).
+template <typename T>
+__global__ void __launch_bounds__(128) k_qr_w2(const QRDesc* __restrict__ ds,
+                                               const T* __restrict__ Wp,
+                                               const int64_t* __restrict__ wpo,
+                                               const T* __restrict__ Tar, T* War, int p, int S) {
+  const QRDesc d = ds[blockIdx.y];
+  if (p >= d.n) return;
+  const int jb = min(QB, d.n - p);
+  const int nt = d.n - p - jb;
+  __shared__ T Ts[QB][QB + 1];   // Ts[i][j] = T(i, j)
+  const T* Tt = Tar + d.Tt;
+  for (int e = threadIdx.x; e < QB * QB; e += 128) Ts[e % QB][e / QB] = Tt[e];
+  __syncthreads();
+  const int c = blockIdx.x * 128 + threadIdx.x;
+  if (c >= nt) return;
+  T w1[QB];
+#pragma unroll
+  for (int i = 0; i < QB; ++i) w1[i] = T(0);
+  const T* src = Wp + wpo[blockIdx.y] + (int64_t)c * QB;
+  for (int s = 0; s < S; ++s)
+#pragma unroll
+    for (int i = 0; i < QB; ++i) w1[i] += src[(int64_t)s * QB * nt + i];
+  T* dst = War + d.W + (int64_t)c * QB;
+#pragma unroll
+  for (int i = 0; i < QB; ++i) {
+    T t = T(0);
+#pragma unroll
+    for (int j = 0; j <= i; ++j) t = fma(Ts[j][i], w1[j], t);   // T upper triangular
+    dst[i] = i < jb ? t : T(0);
+  }
+}
+
+// k_qr_update: A_t -= V W over 128 x 64 tiles; lane l of warp w holds rows
+// l + 32 i (i < 4) and columns 8 w + jj (jj < 8) of the tile.
+template <typename T>
+__global__ void __launch_bounds__(256) k_qr_update(const QRDesc* __restrict__ ds, T* Gar,
+                                                   const T* __restrict__ Var,
+                                                   const T* __restrict__ War, int p) {
+  const QRDesc d = ds[blockIdx.y];
+  if (p >= d.n) return;
+  const int jb = min(QB, d.n - p);
+  const int nt = d.n - p - jb;
+  const int mp = d.m - p;
+  const int tm = (mp + 127) / 128, tn = (nt + 63) / 64;
+  if (nt <= 0 || (int)blockIdx.x >= tm * tn) return;
+  const int rb = (int)(blockIdx.x % tm) * 128, cb = (int)(blockIdx.x / tm) * 64;
+  T* A = Gar + d.A + p + (int64_t)(p + jb) * d.ld;
+  const T* V = Var + d.V;
+  const T* W = War + d.W;
+  __shared__ __align__(16) T Vs[QB][128];
+  __shared__ __align__(16) T Ws[QB][64 + 4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // this thread's entries of A_t, loaded before the staging so that their
+  // latency overlaps it
+  T a[4][8];
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    const int c = cb + warp * 8 + jj;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = rb + lane + 32 * i;
+      a[i][jj] = (r < mp && c < nt) ? A[r + (int64_t)c * d.ld] : T(0);
+    }
+  }
+  // V rows rb.. and W columns cb.. of the tile, all loads issued before the
+  // shared-memory stores
+  {
+    T sv[QB * 128 / 256], sw[QB * 64 / 256];
+    const int r = threadIdx.x % 128, j0 = threadIdx.x / 128;
+#pragma unroll
+    for (int q = 0; q < QB * 128 / 256; ++q) {
+      const int j = j0 + 2 * q;
+      sv[q] = (rb + r < mp && j < jb) ? V[rb + r + (int64_t)j * d.m] : T(0);
+    }
+    const int k = threadIdx.x % QB, c0 = threadIdx.x / QB;
+#pragma unroll
+    for (int q = 0; q < QB * 64 / 256; ++q) {
+      const int c = c0 + 8 * q;
+      sw[q] = (cb + c < nt) ? W[k + (int64_t)(cb + c) * QB] : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < QB * 128 / 256; ++q) Vs[j0 + 2 * q][r] = sv[q];
+#pragma unroll
+    for (int q = 0; q < QB * 64 / 256; ++q) Ws[k][c0 + 8 * q] = sw[q];
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int k = 0; k < QB; ++k) {
+    T v[4], w[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = Vs[k][lane + 32 * i];
+    load8(w, &Ws[k][warp * 8]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) a[i][jj] = fma(-v[i], w[jj], a[i][jj]);
+  }
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    const int c = cb + warp * 8 + jj;
+    if (c >= nt) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = rb + lane + 32 * i;
+      if (r < mp) A[r + (int64_t)c * d.ld] = a[i][jj];
+    }
+  }
+}
+
 }  // namespace
 
 constexpr size_t QRC_SMEM_MAX = 160 * 1024;
@@ -375,11 +638,9 @@ inline bool panel_cluster_fits(int cs, int rb, int tsize) {
 // arena); their n x n triangular factors go to Rout at rOff (ld = n).
 template <typename T>
 void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garena, T* Rout,
-                    const std::vector<int64_t>& rOff, int* d_flags, bool tensor_cores,
-                    cudaStream_t st) {
+                    const std::vector<int64_t>& rOff, cudaStream_t st) {
   const int nq = (int)which.size();
   if (nq == 0) return;
-  const bool use_tc = std::is_same<T, float>::value && tensor_cores;
   // fronts sorted by n (largest first) so that the fronts still factoring a
   // panel are a prefix
   std::vector<int> ord(nq);
@@ -401,14 +662,13 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
     d.Tt = toff;
     d.pad = 0;
     voff += (int64_t)d.m * QB;
-    woff += 2LL * QB * d.n;
+    woff += (int64_t)QB * d.n;
     toff += QB * QB;
     ro[i] = rOff[ord[i]];
   }
   T *Var = nullptr, *War = nullptr, *Tar = nullptr;
   QRDesc* d_qd = nullptr;
   int64_t* d_ro = nullptr;
-  GemmOp* d_ops = nullptr;
   HIF_CUDA_TRY(cudaMallocAsync(&Var, sizeof(T) * voff, st));
   HIF_CUDA_TRY(cudaMallocAsync(&War, sizeof(T) * woff, st));
   HIF_CUDA_TRY(cudaMallocAsync(&Tar, sizeof(T) * toff, st));
@@ -420,49 +680,37 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
   int nsm = 0, dev = 0;
   HIF_CUDA_TRY(cudaGetDevice(&dev));
   HIF_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  // GEMM descriptors of every panel, uploaded once
-  std::vector<GemmOp> ops;
-  std::vector<int64_t> opOff;   // per panel: start of its 3 lists
-  std::vector<int> opCnt;
+  // split of the rows of W = V^T A_t: enough CTAs for two waves at two per
+  // SM; the partials' workspace holds the largest split of any panel
+  constexpr int W1_SPLIT_MAX = 8;
+  auto w1_split = [&](int p) {
+    int tiles = 0;
+    for (int i = 0; i < nq && qd[i].n > p; ++i) {
+      const int nt = qd[i].n - p - std::min(QB, qd[i].n - p);
+      if (nt > 0) tiles += ceil_div(nt, W1_NC);
+    }
+    return tiles == 0 ? 0 : std::max(1, std::min(W1_SPLIT_MAX, ceil_div(4 * nsm, tiles)));
+  };
+  int smax = 0;
+  for (int p = 0; p < nmax; p += QB) smax = std::max(smax, w1_split(p));
+  std::vector<int64_t> wpo(nq);
+  int64_t wptot = 0;
+  for (int i = 0; i < nq; ++i) {
+    wpo[i] = wptot;
+    wptot += (int64_t)smax * QB * qd[i].n;
+  }
+  T* Wp = nullptr;
+  int64_t* d_wpo = nullptr;
+  HIF_CUDA_TRY(cudaMallocAsync(&Wp, sizeof(T) * std::max<int64_t>(1, wptot), st));
+  HIF_CUDA_TRY(cudaMallocAsync(&d_wpo, sizeof(int64_t) * nq, st));
+  HIF_CUDA_TRY(cudaMemcpyAsync(d_wpo, wpo.data(), sizeof(int64_t) * nq, cudaMemcpyHostToDevice, st));
+  static bool w1_attr = false;
+  if (!w1_attr) {
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_qr_w1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)w1_smem_bytes<T>()));
+    w1_attr = true;
+  }
   for (int p = 0; p < nmax; p += QB) {
-    opOff.push_back((int64_t)ops.size());
-    int cnt = 0;
-    for (int i = 0; i < nq; ++i) {
-      const QRDesc& d = qd[i];
-      if (p >= d.n) break;
-      const int jb = std::min(QB, d.n - p);
-      const int nt = d.n - p - jb;
-      if (nt <= 0) continue;
-      ++cnt;
-    }
-    opCnt.push_back(cnt);
-    for (int which_gemm = 0; which_gemm < 3; ++which_gemm) {
-      for (int i = 0; i < nq; ++i) {
-        const QRDesc& d = qd[i];
-        if (p >= d.n) break;
-        const int jb = std::min(QB, d.n - p);
-        const int nt = d.n - p - jb;
-        if (nt <= 0) continue;
-        const int mp = d.m - p;
-        const int64_t At = d.A + p + (int64_t)(p + jb) * d.ld;
-        GemmOp o;
-        if (which_gemm == 0)        // W1 = V^T A_t
-          o = GemmOp{d.V, At, d.W, jb, nt, mp, d.m, d.ld, QB, 1, 0, 1.f, 0.f};
-        else if (which_gemm == 1)   // W2 = T^T W1
-          o = GemmOp{d.Tt, d.W, d.W + (int64_t)QB * d.n, jb, nt, jb, QB, QB, QB, 1, 0, 1.f, 0.f};
-        else                        // A_t -= V W2
-          o = GemmOp{d.V, d.W + (int64_t)QB * d.n, At, mp, nt, jb, d.m, QB, d.ld, 0, 0, -1.f, 1.f};
-        ops.push_back(o);
-      }
-    }
-  }
-  if (!ops.empty()) {
-    HIF_CUDA_TRY(cudaMallocAsync(&d_ops, sizeof(GemmOp) * ops.size(), st));
-    HIF_CUDA_TRY(cudaMemcpyAsync(d_ops, ops.data(), sizeof(GemmOp) * ops.size(),
-                                 cudaMemcpyHostToDevice, st));
-  }
-  int pi = 0;
-  for (int p = 0; p < nmax; p += QB, ++pi) {
     int nact = 0;
     while (nact < nq && qd[nact].n > p) ++nact;
     {
@@ -505,26 +753,36 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
       }
       HIF_CHECK_LAUNCH();
     }
-    const int cnt = opCnt[pi];
-    if (cnt == 0) continue;
-    const int64_t o0 = opOff[pi];
-    // W1 = V^T A_t (deep K) goes to the tensor cores for FP32 fronts; the
-    // rank-QB update A_t -= V W2 is a read-modify-write of A_t with K = QB and
-    // runs faster on the SIMT kernel, which keeps more CTAs resident per SM
-    auto product = [&](int which_gemm, const T* A, const T* B, T* C) {
-      const int64_t oi = o0 + (int64_t)which_gemm * cnt;
-      if constexpr (std::is_same<T, float>::value) {
-        if (use_tc && which_gemm == 0) {
-          gemm_tc(d_ops + oi, ops.data() + oi, cnt, A, B, C, d_flags, st, "id_rowreduce_w1");
-          return;
-        }
-      }
-      gemm_batched<T>(d_ops + oi, ops.data() + oi, cnt, A, B, C, st,
-                      which_gemm == 0 ? "id_rowreduce_w1" : "id_rowreduce_update");
-    };
-    product(0, Var, Garena, War);
-    product(1, Tar, War, War);
-    product(2, Var, War, Garena);
+    // trailing columns: W = T^T V^T A_t (partials over row splits, then
+    // their sum and T^T), A_t -= V W
+    const int S = w1_split(p);
+    if (S == 0) continue;
+    int ct = 0, ntmax = 0, ut = 0;
+    double f1 = 0, b1 = 0, b2 = 0;
+    for (int i = 0; i < nact; ++i) {
+      const int jb = std::min(QB, qd[i].n - p), nt = qd[i].n - p - jb, mp = qd[i].m - p;
+      if (nt <= 0) continue;
+      ct = std::max(ct, ceil_div(nt, W1_NC));
+      ntmax = std::max(ntmax, nt);
+      ut = std::max(ut, ceil_div(mp, 128) * ceil_div(nt, 64));
+      f1 += 2.0 * jb * (double)nt * mp;
+      b1 += sizeof(T) * ((double)mp * nt + (double)mp * jb);
+      b2 += 2.0 * sizeof(T) * (double)mp * nt;
+    }
+    {
+      ProfScope ps("id_rowreduce_w1", st, f1, b1);
+      k_qr_w1<T><<<dim3((unsigned)(ct * S), nact), W1_THREADS, w1_smem_bytes<T>(), st>>>(
+          d_qd, Garena, Var, Wp, d_wpo, p, S);
+      HIF_CHECK_LAUNCH();
+      k_qr_w2<T><<<dim3((unsigned)ceil_div(ntmax, 128), nact), 128, 0, st>>>(d_qd, Wp, d_wpo, Tar,
+                                                                           War, p, S);
+      HIF_CHECK_LAUNCH();
+    }
+    {
+      ProfScope ps("id_rowreduce_update", st, f1, b2);
+      k_qr_update<T><<<dim3((unsigned)ut, nact), 256, 0, st>>>(d_qd, Garena, Var, War, p);
+      HIF_CHECK_LAUNCH();
+    }
   }
   {
     ProfScope ps("id_rowreduce_extract", st);
@@ -532,7 +790,8 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
     k_extract_r<T><<<dim3(ceil_div(mx, 256), nq), 256, 0, st>>>(d_qd, d_ro, Garena, Rout);
     HIF_CHECK_LAUNCH();
   }
-  if (d_ops) HIF_CUDA_TRY(cudaFreeAsync(d_ops, st));
+  HIF_CUDA_TRY(cudaFreeAsync(d_wpo, st));
+  HIF_CUDA_TRY(cudaFreeAsync(Wp, st));
   HIF_CUDA_TRY(cudaFreeAsync(d_ro, st));
   HIF_CUDA_TRY(cudaFreeAsync(d_qd, st));
   HIF_CUDA_TRY(cudaFreeAsync(Tar, st));
@@ -541,8 +800,8 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
 }
 
 template void reduce_rows_qr<float>(const SkelDesc*, const std::vector<int>&, float*, float*,
-                                    const std::vector<int64_t>&, int*, bool, cudaStream_t);
+                                    const std::vector<int64_t>&, cudaStream_t);
 template void reduce_rows_qr<double>(const SkelDesc*, const std::vector<int>&, double*, double*,
-                                     const std::vector<int64_t>&, int*, bool, cudaStream_t);
+                                     const std::vector<int64_t>&, cudaStream_t);
 
 }  // namespace hif
