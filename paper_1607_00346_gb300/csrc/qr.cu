@@ -138,11 +138,13 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_panel(const QRDesc* __restric
 // panel's active rows (p..m-1) are split into CS contiguous slices held in
 // the shared memory of the cluster's CTAs.  Per column: each CTA adds up its
 // slice's part of the tail norm, the parts meet in distributed shared memory
-// and every CTA forms the same reflector from them (summed in rank order);
-// then each CTA computes its slice's part of the reflector's products with
-// the remaining panel columns, the parts meet again, and each CTA updates its
-// slice.  Two cluster barriers per column; the panel is read and written
-// once.  Sums run in the factor precision (FP64 arithmetic is slow here).
+// and every warp forms the same reflector from them (added by a fixed
+// butterfly across lanes, one lane per CTA); then each CTA computes its
+// slice's part of the reflector's products with the remaining panel
+// columns (summed over each warp's lanes by a transposing butterfly), the
+// parts meet again, and each CTA updates its slice.  Two cluster barriers per
+// column; the panel is read and written once.  Sums run in the factor
+// precision (FP64 arithmetic is slow here).
 constexpr int QRC_THREADS = 256;
 constexpr int QRC_WARPS = QRC_THREADS / 32;
 
@@ -169,7 +171,6 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_panel_cluster(const QRDesc* 
   __shared__ double s_tau[QB], s_v0[QB];
   __shared__ double s_T[QB][QB + 1];
   __shared__ double s_Gsum[QB][QB + 1];
-  __shared__ T s_sc[3];                              // v0, tau, alpha of the current column
   __shared__ T s_w[QB];                              // tau w_jj of the current column
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int nr = max(0, r1 - r0);
@@ -178,14 +179,15 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_panel_cluster(const QRDesc* 
     P[i + (int64_t)j * rb] = A[(p + r0 + i) + (int64_t)(p + j) * ld];
   }
   __syncthreads();
+  // thread tid owns the slice rows i = tid + QRC_THREADS k throughout, so
+  // the column updates and the next column's norm part need no barrier
+  T s = T(0);   // this thread's part of the tail norm of the current column
+  for (int i = tid; i < nr; i += QRC_THREADS)
+    if (r0 + i > 0) s = fma(P[i], P[i], s);
   for (int j = 0; j < jb; ++j) {
     const int par = j & 1;
-    // 1. tail norm part (rows below the diagonal) and x0 from its owner
-    T s = T(0);
-    for (int i = max(0, j + 1 - r0) + tid; i < nr; i += QRC_THREADS) {
-      const T x = P[i + (int64_t)j * rb];
-      s = fma(x, x, s);
-    }
+    // 1. tail norm parts (rows below the diagonal) and x0 from its owner meet
+    //    in distributed shared memory; every warp forms the same reflector
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) s_red[warp][0] = s;
     __syncthreads();
@@ -196,70 +198,75 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_panel_cluster(const QRDesc* 
       if (j >= r0 && j < r1) s_x0[par] = P[(j - r0) + (int64_t)j * rb];
     }
     cl.sync();
+    T tail = lane < CS ? *cl.map_shared_rank(&s_nrm[par], lane) : T(0);
+    for (int o = 16; o > 0; o >>= 1) tail += __shfl_xor_sync(0xffffffffu, tail, o);
+    const T x0 = *cl.map_shared_rank(&s_x0[par], min(CS - 1, j / rb));
+    const T nx = sqrt(fma(x0, x0, tail));
+    const T alpha = x0 >= T(0) ? -nx : nx;
+    const T v0 = x0 - alpha;
+    const T vtv = fma(v0, v0, tail);
+    const T tau = vtv > T(0) ? T(2) / vtv : T(0);
     if (tid == 0) {
-      T tail = T(0);
-      for (int q2 = 0; q2 < CS; ++q2) tail += *cl.map_shared_rank(&s_nrm[par], q2);
-      const T x0 = *cl.map_shared_rank(&s_x0[par], min(CS - 1, j / rb));
-      const T nx = sqrt(fma(x0, x0, tail));
-      const T alpha = x0 >= T(0) ? -nx : nx;
-      const T v0 = x0 - alpha;
-      const T vtv = fma(v0, v0, tail);
-      s_sc[0] = v0;
-      s_sc[1] = vtv > T(0) ? T(2) / vtv : T(0);
-      s_sc[2] = alpha;
-      s_tau[j] = (double)s_sc[1];
+      s_tau[j] = (double)tau;
       s_v0[j] = (double)v0;
+      if (j >= r0 && j < r1) P[(j - r0) + (int64_t)j * rb] = alpha;   // R_jj (v0 is kept apart)
     }
-    __syncthreads();
-    const T v0 = s_sc[0], tau = s_sc[1];
-    // 2. parts of w_jj = v^T a_jj for the remaining panel columns (v = v0 at
-    //    row j, the column's entries below it)
     const int nrem = jb - j - 1;
-    if (nrem > 0) {
-      T acc[QB];
+    if (nrem == 0) break;
+    // 2. parts of w_jj = v^T a_jj for the remaining panel columns (v = v0 at
+    //    row j, the column's entries below it), summed over the warp by a
+    //    transposing butterfly (lane l ends with column l)
+    T acc[QB];
 #pragma unroll
-      for (int jj = 0; jj < QB; ++jj) acc[jj] = T(0);
-      for (int i = max(0, j - r0) + tid; i < nr; i += QRC_THREADS) {
-        const int row = r0 + i;
-        const T vi = row == j ? v0 : P[i + (int64_t)j * rb];
-#pragma unroll
-        for (int jj = 0; jj < QB; ++jj)
-          if (jj > j && jj < jb) acc[jj] = fma(vi, P[i + (int64_t)jj * rb], acc[jj]);
-      }
-#pragma unroll
-      for (int jj = 0; jj < QB; ++jj) {
-        if (jj > j && jj < jb) {
-          T x = acc[jj];
-          for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-          if (lane == 0) s_red[warp][jj] = x;
-        }
-      }
-      __syncthreads();
-      if (tid < QB && tid > j && tid < jb) {
-        T t = T(0);
-        for (int w = 0; w < QRC_WARPS; ++w) t += s_red[w][tid];
-        s_dot[par][tid] = t;
-      }
-    }
-    cl.sync();
-    if (tid < QB && tid > j && tid < jb) {
-      T t = T(0);
-      for (int q2 = 0; q2 < CS; ++q2) t += *cl.map_shared_rank(&s_dot[par][tid], q2);
-      s_w[tid] = tau * t;
-    }
-    __syncthreads();
-    // 3. update the slice: a_jj -= (tau w_jj) v; the diagonal gets alpha
-    for (int e = tid; e < nr * nrem; e += QRC_THREADS) {
-      const int i = e % nr, jj = j + 1 + e / nr;
+    for (int jj = 0; jj < QB; ++jj) acc[jj] = T(0);
+    for (int i = tid; i < nr; i += QRC_THREADS) {
       const int row = r0 + i;
       if (row < j) continue;
       const T vi = row == j ? v0 : P[i + (int64_t)j * rb];
-      P[i + (int64_t)jj * rb] = fma(-s_w[jj], vi, P[i + (int64_t)jj * rb]);
+#pragma unroll
+      for (int jj = 0; jj < QB; ++jj)
+        if (jj > j && jj < jb) acc[jj] = fma(vi, P[i + (int64_t)jj * rb], acc[jj]);
+    }
+#pragma unroll
+    for (int o = QB / 2; o > 0; o >>= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int q = 0; q < o; ++q) {
+        const T send = up ? acc[q] : acc[q + o];
+        const T keep = up ? acc[q + o] : acc[q];
+        acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    }
+    s_red[warp][lane] = acc[0];
+    __syncthreads();
+    if (tid < QB) {
+      T t = T(0);
+      for (int w = 0; w < QRC_WARPS; ++w) t += s_red[w][tid];
+      s_dot[par][tid] = t;
+    }
+    cl.sync();
+    // warp w adds the cluster's parts of columns w + QRC_WARPS q
+    for (int jj = warp; jj < QB; jj += QRC_WARPS) {
+      T t = lane < CS ? *cl.map_shared_rank(&s_dot[par][jj], lane) : T(0);
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) s_w[jj] = tau * t;
     }
     __syncthreads();
-    if (tid == 0 && j >= r0 && j < r1) P[(j - r0) + (int64_t)j * rb] = s_sc[2];
-    __syncthreads();
+    // 3. update the slice, a_jj -= (tau w_jj) v, and take this thread's part
+    //    of the next column's tail norm on the way
+    s = T(0);
+    for (int i = tid; i < nr; i += QRC_THREADS) {
+      const int row = r0 + i;
+      if (row < j) continue;
+      const T vi = row == j ? v0 : P[i + (int64_t)j * rb];
+      for (int jj = j + 1; jj < jb; ++jj) {
+        const T x = fma(-s_w[jj], vi, P[i + (int64_t)jj * rb]);
+        P[i + (int64_t)jj * rb] = x;
+        if (jj == j + 1 && row > j + 1) s = fma(x, x, s);
+      }
+    }
   }
+  __syncthreads();
   // reflectors to V (rows p..m-1, zeros above each diagonal), the slice back
   // to A, and this slice's part of the Gram matrix V^T V
   for (int e = tid; e < nr * QB; e += QRC_THREADS) {
