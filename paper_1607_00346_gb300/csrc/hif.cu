@@ -147,16 +147,16 @@ class DevBuf {
   bool async_ = false;
 };
 
-template <typename U>
-void upload_async(DevBuf& b, const std::vector<U>& h, MemStats* ms, cudaStream_t st) {
+template <typename U, typename A>
+void upload_async(DevBuf& b, const std::vector<U, A>& h, MemStats* ms, cudaStream_t st) {
   b.alloc_async(h.size() * sizeof(U), ms, st);
   if (!h.empty())
     HIF_CUDA_TRY(cudaMemcpyAsync(b.as<void>(), h.data(), h.size() * sizeof(U),
                                  cudaMemcpyHostToDevice, st));
 }
 
-template <typename U>
-void upload(DevBuf& b, const std::vector<U>& h, MemStats* ms, cudaStream_t st) {
+template <typename U, typename A>
+void upload(DevBuf& b, const std::vector<U, A>& h, MemStats* ms, cudaStream_t st) {
   b.alloc(h.size() * sizeof(U), ms);
   if (!h.empty())
     HIF_CUDA_TRY(cudaMemcpyAsync(b.as<void>(), h.data(), h.size() * sizeof(U),
@@ -388,7 +388,7 @@ class Builder {
   bool have_spec_ = false;
   CellPlan spec_cells_;
   std::vector<int64_t> spec_mapOff_;
-  std::vector<int32_t> spec_map_;
+  PlanVec32 spec_map_;
 };
 
 template <typename T>
@@ -448,7 +448,7 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
     CellPlan& cp = *cpp;
     tr_.mark(level, "start");
     std::vector<int64_t> mapOff;
-    std::vector<int32_t> map;
+    PlanVec32 map;
     if (have_spec_) {
       cp = std::move(spec_cells_);
       mapOff = std::move(spec_mapOff_);

@@ -28,6 +28,25 @@ void parallel_for(int64_t n, F&& f) {
   for (auto& x : th) x.join();
 }
 
+// f(t, a, b) on nt contiguous chunks [a, b) of [0, n), in parallel; the
+// chunks are in index order, so per-chunk results combine deterministically
+template <class F>
+int parallel_chunks(int64_t n, F&& f) {
+  unsigned hw = std::thread::hardware_concurrency();
+  if (hw == 0) hw = 1;
+  const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(hw, n / 4096));
+  if (nt == 1) {
+    f(0, (int64_t)0, n);
+    return 1;
+  }
+  std::vector<std::thread> th;
+  th.reserve(nt);
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t] { f(t, n * t / nt, n * (t + 1) / nt); });
+  for (auto& x : th) x.join();
+  return nt;
+}
+
 inline int popc3(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1); }
 
 }  // namespace
@@ -44,15 +63,14 @@ Symbolic::Symbolic(int n, int m) : n_(n), m_(m), L_(hif_num_levels(n, m)) {
   for (size_t i = 0; i < active_.size(); ++i) active_[i] = (int32_t)i;
 }
 
-int32_t Symbolic::pos_in_cell(const CellPlan& cp, int32_t g, int cx, int cy, int cz) const {
-  int32_t sl = cp.slot[g];
-  if (sl < 0) return -1;
-  int64_t pk = cp.packed[sl];
-  int sep = (int)(pk >> 48);
-  int c[3] = {cx, cy, cz};
+namespace {
+// Boundary position in cell c (coordinates) of the DOF at active slot sl
+// with packed geometry pk, or -1 if the cell's closure does not hold it.
+inline int32_t pos_at(const CellPlan& cp, int32_t sl, int64_t pk, const int* c) {
+  const int sep = (int)(pk >> 48);
   int q = 0;
   for (int d = 0; d < 3; ++d) {
-    int lc = (int)((pk >> (16 * d)) & 0xffff);
+    const int lc = (int)((pk >> (16 * d)) & 0xffff);
     if (c[d] == lc) continue;
     if (((sep >> d) & 1) && c[d] == lc + 1) {
       q |= 1 << d;
@@ -61,6 +79,14 @@ int32_t Symbolic::pos_in_cell(const CellPlan& cp, int32_t g, int cx, int cy, int
     return -1;
   }
   return cp.posB[(int64_t)sl * 8 + q];
+}
+}  // namespace
+
+int32_t Symbolic::pos_in_cell(const CellPlan& cp, int32_t g, int cx, int cy, int cz) const {
+  const int32_t sl = cp.slot[g];
+  if (sl < 0) return -1;
+  const int c[3] = {cx, cy, cz};
+  return pos_at(cp, sl, cp.packed[sl], c);
 }
 
 void Symbolic::build_cells(int level, CellPlan& cp) const { build_cells_from(level, active_, cp); }
@@ -77,8 +103,8 @@ void Symbolic::filter_rows(SkelPlan& sp, const std::vector<uint8_t>& alive) cons
   });
   std::vector<int64_t> off(nf + 1, 0);
   for (int f = 0; f < nf; ++f) off[f + 1] = off[f] + kept[f];
-  std::vector<int32_t> dof(off[nf]);
-  std::vector<int32_t> pos(off[nf] * ncp);
+  PlanVec32 dof(off[nf]);
+  PlanVec32 pos(off[nf] * ncp);
   parallel_for(nf, [&](int64_t f) {
     int64_t o = off[f];
     for (int64_t r = sp.rowOff[f]; r < sp.rowOff[f + 1]; ++r) {
@@ -105,7 +131,8 @@ void Symbolic::build_cells_from(int level, const std::vector<int32_t>& active, C
   cp.ncell = C * C * C;
   cp.active = active;
   const int64_t na = (int64_t)cp.active.size();
-  cp.slot.assign(N, -1);
+  cp.slot.resize(N);
+  parallel_for(N, [&](int64_t g) { cp.slot[g] = -1; });
   cp.packed.resize(na);
   parallel_for(na, [&](int64_t i) {
     int32_t g = cp.active[i];
@@ -121,67 +148,112 @@ void Symbolic::build_cells_from(int level, const std::vector<int32_t>& active, C
     }
     cp.packed[i] = pk | ((int64_t)sep << 48);
   });
-  std::vector<int32_t> cntI(cp.ncell, 0), cntB(cp.ncell, 0);
   auto cell_of = [&](int64_t pk, int q) {
     int c0 = (int)(pk & 0xffff) + (q & 1);
     int c1 = (int)((pk >> 16) & 0xffff) + ((q >> 1) & 1);
     int c2 = (int)((pk >> 32) & 0xffff) + ((q >> 2) & 1);
     return c0 + C * (c1 + C * c2);
   };
-  for (int64_t i = 0; i < na; ++i) {
-    int64_t pk = cp.packed[i];
-    int sep = (int)(pk >> 48);
-    if (sep == 0) {
-      cntI[cell_of(pk, 0)]++;
-    } else {
-      for (int q = 0; q < 8; ++q)
-        if ((q & ~sep) == 0) cntB[cell_of(pk, q)]++;
+  // interior / boundary counts per cell, per chunk of the active list; the
+  // chunks then fill the lists at their running offsets, so the lists keep
+  // ascending global order within each part, as a sequential pass would
+  unsigned hw = std::thread::hardware_concurrency();
+  const int ntmax = (int)std::max<int64_t>(1, std::min<int64_t>(hw == 0 ? 1 : hw, na / 4096));
+  std::vector<std::vector<int32_t>> cntI(ntmax), cntB(ntmax);
+  const int nt = parallel_chunks(na, [&](int t, int64_t a, int64_t b) {
+    std::vector<int32_t>& ci = cntI[t];
+    std::vector<int32_t>& cb = cntB[t];
+    ci.assign(cp.ncell, 0);
+    cb.assign(cp.ncell, 0);
+    for (int64_t i = a; i < b; ++i) {
+      int64_t pk = cp.packed[i];
+      int sep = (int)(pk >> 48);
+      if (sep == 0) {
+        ci[cell_of(pk, 0)]++;
+      } else {
+        for (int q = 0; q < 8; ++q)
+          if ((q & ~sep) == 0) cb[cell_of(pk, q)]++;
+      }
     }
-  }
+  });
   cp.off.assign(cp.ncell + 1, 0);
   cp.p.assign(cp.ncell, 0);
   for (int c = 0; c < cp.ncell; ++c) {
-    cp.off[c + 1] = cp.off[c] + cntI[c] + cntB[c];
-    cp.p[c] = cntI[c];
+    int32_t ti = 0, tb = 0;
+    for (int t = 0; t < nt; ++t) {   // counts become each chunk's start within the cell
+      const int32_t xi = cntI[t][c], xb = cntB[t][c];
+      cntI[t][c] = ti;
+      cntB[t][c] = tb;
+      ti += xi;
+      tb += xb;
+    }
+    cp.off[c + 1] = cp.off[c] + ti + tb;
+    cp.p[c] = ti;
   }
-  cp.dofs.assign(cp.off[cp.ncell], -1);
-  cp.posB.assign(na * 8, -1);
-  std::vector<int32_t> curI(cp.ncell, 0), curB(cp.ncell, 0);
-  for (int64_t i = 0; i < na; ++i) {
-    int64_t pk = cp.packed[i];
-    int sep = (int)(pk >> 48);
-    int32_t g = cp.active[i];
-    if (sep == 0) {
-      int c = cell_of(pk, 0);
-      cp.dofs[cp.off[c] + curI[c]++] = g;
-    } else {
-      for (int q = 0; q < 8; ++q) {
-        if (q & ~sep) continue;
-        int c = cell_of(pk, q);
-        int b = curB[c]++;
-        cp.dofs[cp.off[c] + cp.p[c] + b] = g;
-        cp.posB[i * 8 + q] = b;
+  cp.dofs.resize(cp.off[cp.ncell]);
+  cp.dofSlot.resize(cp.off[cp.ncell]);
+  cp.dofPk.resize(cp.off[cp.ncell]);
+  cp.posB.resize(na * 8);
+  parallel_chunks(na, [&](int t, int64_t a, int64_t b) {
+    std::vector<int32_t>& curI = cntI[t];
+    std::vector<int32_t>& curB = cntB[t];
+    for (int64_t i = a; i < b; ++i) {
+      int64_t pk = cp.packed[i];
+      int sep = (int)(pk >> 48);
+      int32_t g = cp.active[i];
+      int32_t* pb = &cp.posB[i * 8];
+      for (int q = 0; q < 8; ++q) pb[q] = -1;
+      if (sep == 0) {
+        int c = cell_of(pk, 0);
+        const int64_t e = cp.off[c] + curI[c]++;
+        cp.dofs[e] = g;
+        cp.dofSlot[e] = (int32_t)i;
+        cp.dofPk[e] = pk;
+      } else {
+        for (int q = 0; q < 8; ++q) {
+          if (q & ~sep) continue;
+          int c = cell_of(pk, q);
+          int bpos = curB[c]++;
+          const int64_t e = cp.off[c] + cp.p[c] + bpos;
+          cp.dofs[e] = g;
+          cp.dofSlot[e] = (int32_t)i;
+          cp.dofPk[e] = pk;
+          pb[q] = bpos;
+        }
       }
     }
-  }
+  });
 }
 
 void Symbolic::merge_maps(const CellPlan& child, const CellPlan& parent,
-                          std::vector<int64_t>& mapOff, std::vector<int32_t>& map) const {
+                          std::vector<int64_t>& mapOff, PlanVec32& map) const {
   const int C = parent.C, Cc = child.C;
   mapOff.assign(parent.ncell + 1, 0);
   for (int c = 0; c < parent.ncell; ++c)
     mapOff[c + 1] = mapOff[c] + 8 * (parent.off[c + 1] - parent.off[c]);
-  map.assign(mapOff[parent.ncell], -1);
+  map.resize(mapOff[parent.ncell]);
   parallel_for(parent.ncell, [&](int64_t c) {
     int px = (int)(c % C), py = (int)((c / C) % C), pz = (int)(c / ((int64_t)C * C));
     int64_t o = parent.off[c];
     int64_t nn = parent.off[c + 1] - o;
+    // each DOF's slot and geometry in the child plan are looked up once for
+    // all 8 children
+    int cc[8][3];
+    bool has[8];
     for (int q = 0; q < 8; ++q) {
-      int cx = 2 * px + (q & 1), cy = 2 * py + ((q >> 1) & 1), cz = 2 * pz + ((q >> 2) & 1);
-      if (cx >= Cc || cy >= Cc || cz >= Cc) continue;
-      int32_t* out = &map[mapOff[c] + (int64_t)q * nn];
-      for (int64_t a = 0; a < nn; ++a) out[a] = pos_in_cell(child, parent.dofs[o + a], cx, cy, cz);
+      cc[q][0] = 2 * px + (q & 1);
+      cc[q][1] = 2 * py + ((q >> 1) & 1);
+      cc[q][2] = 2 * pz + ((q >> 2) & 1);
+      has[q] = cc[q][0] < Cc && cc[q][1] < Cc && cc[q][2] < Cc;
+    }
+    int32_t* out = &map[mapOff[c]];
+    for (int64_t e = 0; e < 8 * nn; ++e) out[e] = -1;
+    for (int64_t a = 0; a < nn; ++a) {
+      const int32_t sl = child.slot[parent.dofs[o + a]];
+      if (sl < 0) continue;
+      const int64_t pk = child.packed[sl];
+      for (int q = 0; q < 8; ++q)
+        if (has[q]) out[(int64_t)q * nn + a] = pos_at(child, sl, pk, cc[q]);
     }
   });
 }
@@ -261,9 +333,11 @@ void Symbolic::build_skel(const CellPlan& cp, int kind, const std::vector<uint8_
     int32_t pos[4];
     for (int64_t u = moff[f]; u < moff[f + 1]; ++u) {
       const int32_t g = mem[u];
-      if (want_pos)
-        for (int j = 0; j < ncp; ++j)
-          pos[j] = pos_in_cell(cp, g, cx[3 * j], cx[3 * j + 1], cx[3 * j + 2]);
+      if (want_pos) {
+        const int32_t sl = cp.slot[g];
+        const int64_t pk = cp.packed[sl];
+        for (int j = 0; j < ncp; ++j) pos[j] = pos_at(cp, sl, pk, cx + 3 * j);
+      }
       emit(g, pos);
     }
     for (int i = 0; i < ncp; ++i) {
@@ -272,17 +346,18 @@ void Symbolic::build_skel(const CellPlan& cp, int kind, const std::vector<uint8_
       for (int64_t t = o; t < e; ++t) {
         const int32_t g = cp.dofs[t];
         if (!alive[g]) continue;
-        if (gkey(cp.packed[cp.slot[g]]) == fk) continue;
+        const int32_t sl = cp.dofSlot[t];
+        const int64_t pk = cp.dofPk[t];
+        if (gkey(pk) == fk) continue;
         bool earlier = false;
         for (int j = 0; j < i && !earlier; ++j) {
-          pos[j] = pos_in_cell(cp, g, cx[3 * j], cx[3 * j + 1], cx[3 * j + 2]);
+          pos[j] = pos_at(cp, sl, pk, cx + 3 * j);
           earlier = pos[j] >= 0;
         }
         if (earlier) continue;
         if (want_pos) {
           pos[i] = (int32_t)(t - o);
-          for (int j = i + 1; j < ncp; ++j)
-            pos[j] = pos_in_cell(cp, g, cx[3 * j], cx[3 * j + 1], cx[3 * j + 2]);
+          for (int j = i + 1; j < ncp; ++j) pos[j] = pos_at(cp, sl, pk, cx + 3 * j);
         }
         emit(g, pos);
       }

@@ -17,19 +17,48 @@
 
 #include <stdint.h>
 
+#include <memory>
+#include <new>
+#include <utility>
 #include <vector>
 
 namespace hif {
+
+// Allocator whose value-less construct leaves the element uninitialized: the
+// large plan arrays are written in full by parallel loops, so zero-filling
+// them first on one thread would only cost time (and touch every page from
+// that thread).
+template <class T>
+struct DefaultInitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = DefaultInitAlloc<U>;
+  };
+  DefaultInitAlloc() = default;
+  template <class U>
+  DefaultInitAlloc(const DefaultInitAlloc<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... Args>
+  void construct(U* p, Args&&... args) {
+    ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...);
+  }
+};
+using PlanVec32 = std::vector<int32_t, DefaultInitAlloc<int32_t>>;
 
 struct CellPlan {
   int level = 0, s = 0, C = 0;   // cell side, cells per dimension
   int ncell = 0;
   std::vector<int32_t> active;   // sorted global ids active at the start of the level
-  std::vector<int32_t> slot;     // global id -> index in `active`, -1 if inactive
+  PlanVec32 slot;                // global id -> index in `active`, -1 if inactive
   std::vector<int64_t> off;      // per cell offset into dofs (ncell + 1)
-  std::vector<int32_t> dofs;     // frontal lists: interior, then boundary
+  PlanVec32 dofs;                // frontal lists: interior, then boundary
+  PlanVec32 dofSlot;             // per dofs entry: its active slot
+  std::vector<int64_t, DefaultInitAlloc<int64_t>> dofPk;   // per dofs entry: its packed geometry
   std::vector<int32_t> p;        // interior count per cell
-  std::vector<int32_t> posB;     // per active slot, 8 corners: position in that cell's boundary list
+  PlanVec32 posB;                // per active slot, 8 corners: position in that cell's boundary list
   std::vector<int64_t> packed;   // per active slot: low cells (3 x 16 bit) | separator mask << 48
 };
 
@@ -40,8 +69,8 @@ struct SkelPlan {
   std::vector<int32_t> cells;    // nfront * ncellPer cell ids
   std::vector<int32_t> nF, nR;   // front size and number of coupled rows
   std::vector<int64_t> rowOff;   // per front offset into rowDof (nfront + 1)
-  std::vector<int32_t> rowDof;   // global ids: the front's DOFs first, then R
-  std::vector<int32_t> rowPos;   // per row, ncellPer boundary positions (-1 = absent)
+  PlanVec32 rowDof;              // global ids: the front's DOFs first, then R
+  PlanVec32 rowPos;              // per row, ncellPer boundary positions (-1 = absent)
 };
 
 class Symbolic {
@@ -57,7 +86,7 @@ class Symbolic {
   // (level l): for each parent cell, 8 x n_parent entries (child corner q
   // major) giving the child's boundary position of the parent's DOF, or -1.
   void merge_maps(const CellPlan& child, const CellPlan& parent,
-                  std::vector<int64_t>& mapOff, std::vector<int32_t>& map) const;
+                  std::vector<int64_t>& mapOff, PlanVec32& map) const;
   // Faces (kind 1) or edges (kind 2) of the level with their coupled rows.
   // `alive` marks DOFs still active (redundant DOFs of faces are dropped
   // before the edges are planned).

@@ -62,7 +62,7 @@ int main(int argc, char** argv) {
     // merge maps
     if (level > 0) {
       std::vector<int64_t> moff;
-      std::vector<int32_t> map;
+      PlanVec32 map;
       sym.merge_maps(prev, cp, moff, map);
       for (int c = 0; c < cp.ncell; ++c) {
         const int64_t nn = cp.off[c + 1] - cp.off[c];
