@@ -54,10 +54,90 @@ struct TileAcc {
   }
 };
 
-// ---- panel: Cholesky of the diagonal block + triangular solve of the rows below
+// ---- panel: Cholesky of the diagonal block, then triangular solve of the rows below
+// k_chol_diag: one CTA per front factors the jb x jb diagonal block (jb <= 64)
+// right-looking with the block in registers: thread (ty, tx) of a 16 x 16 grid
+// holds rows ty + 16 i and columns tx + 16 j (i, j < 4).  Per column c the
+// threads holding column c scale it by the pivot and publish it to shared
+// memory; every thread then updates its entries right of c, and the holder
+// of entry (c+1, c+1) publishes the next pivot.  L goes to the factor panel
+// (zeros above the diagonal); a non-positive or non-finite pivot flags the
+// front and continues with 1.
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_diag(const DFront* __restrict__ fr, const T* Kar,
+                                                   T* Par, int j0, int* flags) {
+  const DFront d = fr[blockIdx.x];
+  if (j0 >= d.p) return;
+  const int jb = min(NB, d.p - j0);
+  const int64_t ld = d.ld;
+  const T* K = Kar + d.K + (int64_t)j0 + (int64_t)j0 * ld;
+  T* P = Par + d.P + (int64_t)j0 + (int64_t)j0 * ld;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  __shared__ T colv[2][NB];
+  __shared__ T diagv[NB];
+  T a[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      a[i][j] = (r < jb && c < jb && r >= c) ? K[r + (int64_t)c * ld] : T(0);
+      if (r == c && r == 0) diagv[0] = a[i][j];
+    }
+  __syncthreads();
+  for (int c = 0; c < jb; ++c) {
+    const int par = c & 1;
+    if (tx == c % 16) {
+      const int j = c / 16;
+      T dv = diagv[c];
+      if (!(dv > T(0)) || !isfinite(dv)) {
+        if (ty == 0) flag_front(flags, FLAG_NOT_SPD, d.id);
+        dv = T(1);
+      }
+      const T piv = sqrt(dv), inv = T(1) / piv;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = ty + 16 * i;
+        if (r > c) {
+          a[i][j] *= inv;
+          colv[par][r] = a[i][j];
+        } else if (r == c) {
+          a[i][j] = piv;
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = ty + 16 * i;
+      if (r <= c) continue;
+      const T lr = colv[par][r];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int cc = tx + 16 * j;
+        if (cc > c && cc <= r) {
+          a[i][j] = fma(-lr, colv[par][cc], a[i][j]);
+          if (r == cc && r == c + 1) diagv[r] = a[i][j];
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      if (r < jb && c < jb) P[r + (int64_t)c * ld] = r >= c ? a[i][j] : T(0);
+    }
+}
+
+// k_panel: the rows below the diagonal block, L21 = A21 L11^{-T}, by forward
+// substitution per row (one thread per row) with L11 read from the factor
+// panel; rows past the leading block also go to the panel.
 template <typename T>
 __global__ void __launch_bounds__(PANEL_ROWS) k_panel(const DFront* __restrict__ fr, T* Kar,
-                                                      T* Par, int j0, int* flags) {
+                                                      T* Par, int j0) {
   const DFront d = fr[blockIdx.y];
   if (j0 >= d.p) return;
   const int jb = min(NB, d.p - j0);
@@ -65,44 +145,16 @@ __global__ void __launch_bounds__(PANEL_ROWS) k_panel(const DFront* __restrict__
   const int n = d.n;
   const int64_t ld = d.ld;
   const int r0 = j1 + blockIdx.x * PANEL_ROWS;
-  if (blockIdx.x > 0 && r0 >= n) return;
+  if (r0 >= n) return;
   T* K = Kar + d.K;
   T* P = Par + d.P;
   __shared__ T D[NB][NB + 1];
   const int tid = threadIdx.x;
   for (int e = tid; e < NB * NB; e += PANEL_ROWS) {
     int r = e % NB, c = e / NB;
-    T v = T(0);
-    if (r < jb && c < jb && r >= c) v = K[(int64_t)(j0 + r) + (int64_t)(j0 + c) * ld];
-    D[r][c] = v;
+    D[r][c] = (r < jb && c < jb && r >= c) ? P[(int64_t)(j0 + r) + (int64_t)(j0 + c) * ld] : T(0);
   }
   __syncthreads();
-  // right-looking Cholesky of the jb x jb diagonal block in shared memory
-  for (int c = 0; c < jb; ++c) {
-    if (tid == 0) {
-      T dv = D[c][c];
-      if (!(dv > T(0)) || !isfinite(dv)) {
-        flag_front(flags, FLAG_NOT_SPD, d.id);
-        dv = T(1);
-      }
-      D[c][c] = sqrt(dv);
-    }
-    __syncthreads();
-    const T piv = D[c][c];
-    if (tid > c && tid < jb) D[tid][c] /= piv;
-    __syncthreads();
-    if (tid > c && tid < jb) {
-      const T lrc = D[tid][c];
-      for (int cc = c + 1; cc <= tid; ++cc) D[tid][cc] -= lrc * D[cc][c];
-    }
-    __syncthreads();
-  }
-  if (blockIdx.x == 0) {
-    for (int e = tid; e < jb * jb; e += PANEL_ROWS) {
-      int r = e % jb, c = e / jb;
-      P[(int64_t)(j0 + r) + (int64_t)(j0 + c) * ld] = r >= c ? D[r][c] : T(0);
-    }
-  }
   const int r = r0 + tid;
   if (r >= n) return;
   T x[NB];
@@ -405,7 +457,7 @@ void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront
       while (nact < nfront && lead[nact].p > j0) ++nact;
       const int nm = lead[0].p;   // fronts are sorted by p, largest first
       const int j1min = j0 + 1;   // smallest possible j1 among active fronts
-      const int chunks = std::max(1, ceil_div(std::max(0, nm - j1min), PANEL_ROWS));
+      const int chunks = ceil_div(std::max(0, nm - j1min), PANEL_ROWS);
       const int ntile = ceil_div(std::max(0, nm - j1min), TILE);
       const int nctile = outer ? std::max(1, ceil_div(std::max(0, jend - j1min), TILE)) : 0;
       const int grid = outer ? std::max(1, ntile * nctile) : std::max(1, ntile * (ntile + 1) / 2);
@@ -426,9 +478,12 @@ void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront
         const int nb = std::min(MAX_GRID_Y, nact - f0);
         {
           ProfScope ps("chol_panel", st, pf, pb);
-          k_panel<T><<<dim3(chunks, nb), PANEL_ROWS, 0, st>>>(d_lead + f0, Karena, Parena, j0,
-                                                              d_flags);
+          k_chol_diag<T><<<nb, 256, 0, st>>>(d_lead + f0, Karena, Parena, j0, d_flags);
           HIF_CHECK_LAUNCH();
+          if (chunks > 0) {
+            k_panel<T><<<dim3(chunks, nb), PANEL_ROWS, 0, st>>>(d_lead + f0, Karena, Parena, j0);
+            HIF_CHECK_LAUNCH();
+          }
         }
         {
           ProfScope ps("chol_trailing_update", st, sf, sb);

@@ -418,11 +418,14 @@ __global__ void __launch_bounds__(W1_THREADS, sizeof(T) == 4 ? 2 : 1)
   T* ring = reinterpret_cast<T*>(w1sm);   // stage: As[k W1_AP + c], then Vs[k W1_VP + j]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int lv = lane & 3, la = lane >> 2;                  // V columns lv*8+i, A columns la*8+jj
-  // thread tid copies row tid % W1_KC of a chunk, A and V columns
-  // tid / W1_KC + CS q
+  // thread tid copies row sk of a chunk, A and V columns sc + CS q: a warp
+  // covers 8 consecutive rows of 4 columns, so its global reads fill whole
+  // 32-byte sectors and its shared-memory stores (row pitch = 4 mod 32 banks)
+  // hit 32 different banks
+  static_assert(W1_KC == 32 && W1_THREADS == 256, "staging map assumes 32 rows, 8 warps");
   constexpr int NQA = W1_NC * W1_KC / W1_THREADS, NQV = W1_KC * QB / W1_THREADS;
   constexpr int CS = W1_THREADS / W1_KC;
-  const int sk = tid % W1_KC, sc = tid / W1_KC;
+  const int sk = (lane & 7) + 8 * (warp & 3), sc = (lane >> 3) + 4 * (warp >> 2);
   auto issue = [&](int kc) {
     if (kc < kc1) {
       T* As = ring + (size_t)((kc - kc0) % W1_ST) * W1_STAGE;
