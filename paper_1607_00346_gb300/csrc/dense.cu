@@ -160,13 +160,14 @@ __global__ void __launch_bounds__(PANEL_ROWS) k_panel(const DFront* __restrict__
   T x[NB];
 #pragma unroll
   for (int c = 0; c < NB; ++c) x[c] = c < jb ? K[(int64_t)r + (int64_t)(j0 + c) * ld] : T(0);
+  // four partial sums per dot product shorten the dependent chains
 #pragma unroll
   for (int c = 0; c < NB; ++c) {
     if (c < jb) {
-      T s = x[c];
+      T s[4] = {x[c], T(0), T(0), T(0)};
 #pragma unroll
-      for (int l = 0; l < c; ++l) s = fma(-x[l], D[c][l], s);
-      x[c] = s / D[c][c];
+      for (int l = 0; l < c; ++l) s[l & 3] = fma(-x[l], D[c][l], s[l & 3]);
+      x[c] = ((s[0] + s[1]) + (s[2] + s[3])) / D[c][c];
     }
   }
   const bool toP = r >= d.p;
