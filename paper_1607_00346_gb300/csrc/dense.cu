@@ -641,8 +641,11 @@ void gemv_batched(const GemvOp* d_ops, const GemvOp* h_ops, int nops, int trans,
   int mx = 1;
   for (int i = 0; i < nops; ++i)
     mx = std::max(mx, trans ? ceil_div(h_ops[i].cols, 8) : ceil_div(h_ops[i].rows, GEMV_ROWS));
+  // right-hand sides in blocks of 16, 8, 4, 2, 1: each block reads the
+  // factor once, and every column sees the same arithmetic in any block
   for (int q0 = 0; q0 < nrhs;) {
-    const int R = nrhs - q0 >= 8 ? 8 : 1;
+    const int left = nrhs - q0;
+    const int R = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
     T* w = work + (int64_t)q0 * vstride;
     for (int f0 = 0; f0 < nops; f0 += MAX_GRID_Y) {
       const int nb = std::min(MAX_GRID_Y, nops - f0);
@@ -659,11 +662,22 @@ void gemv_batched(const GemvOp* d_ops, const GemvOp* h_ops, int nops, int trans,
       }
       ProfScope ps(trans ? "apply_gemv_t" : "apply_gemv_n", st, fl, by);
       if (trans) {
-        if (R == 8) k_gemv_t<T, 8><<<grid, 256, 0, st>>>(d_ops + f0, Marena, w, vstride);
-        else k_gemv_t<T, 1><<<grid, 256, 0, st>>>(d_ops + f0, Marena, w, vstride);
+        switch (R) {
+          case 16: k_gemv_t<T, 16><<<grid, 256, 0, st>>>(d_ops + f0, Marena, w, vstride); break;
+          case 8: k_gemv_t<T, 8><<<grid, 256, 0, st>>>(d_ops + f0, Marena, w, vstride); break;
+          case 4: k_gemv_t<T, 4><<<grid, 256, 0, st>>>(d_ops + f0, Marena, w, vstride); break;
+          case 2: k_gemv_t<T, 2><<<grid, 256, 0, st>>>(d_ops + f0, Marena, w, vstride); break;
+          default: k_gemv_t<T, 1><<<grid, 256, 0, st>>>(d_ops + f0, Marena, w, vstride);
+        }
       } else {
-        if (R == 8) k_gemv_n<T, 8><<<grid, GEMV_ROWS * 2, 0, st>>>(d_ops + f0, Marena, w, vstride);
-        else k_gemv_n<T, 1><<<grid, GEMV_ROWS * 2, 0, st>>>(d_ops + f0, Marena, w, vstride);
+        constexpr int TH = GEMV_ROWS * 2;
+        switch (R) {
+          case 16: k_gemv_n<T, 16><<<grid, TH, 0, st>>>(d_ops + f0, Marena, w, vstride); break;
+          case 8: k_gemv_n<T, 8><<<grid, TH, 0, st>>>(d_ops + f0, Marena, w, vstride); break;
+          case 4: k_gemv_n<T, 4><<<grid, TH, 0, st>>>(d_ops + f0, Marena, w, vstride); break;
+          case 2: k_gemv_n<T, 2><<<grid, TH, 0, st>>>(d_ops + f0, Marena, w, vstride); break;
+          default: k_gemv_n<T, 1><<<grid, TH, 0, st>>>(d_ops + f0, Marena, w, vstride);
+        }
       }
       HIF_CHECK_LAUNCH();
       }

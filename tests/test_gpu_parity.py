@@ -122,6 +122,23 @@ def test_pcg_multi_rhs(H, precision):
     assert np.linalg.norm(uc[1] - uo) <= 1e-8 * np.linalg.norm(uo)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multi_rhs_apply_is_bitwise_per_column(H, precision):
+    # the apply's mat-vecs take right-hand sides in blocks of 16, 8, 4, 2 and 1
+    # (one read of the factor per block) with the same arithmetic for every
+    # column in any block: a 23-column apply (16 + 4 + 2 + 1) equals 23
+    # one-column applies bit for bit
+    n = 16
+    a = _coeff(n, 981)
+    f = inputs.normal_rhs(n, 23, 982)
+    h = H.factor(n, 4, _dev(a), b_const=0.1, eps=1e-6, precision=precision)
+    ub = _gpu_apply(h, f)
+    for c in range(23):
+        uc = _gpu_apply(h, f[c:c + 1])
+        assert np.array_equal(ub[c], uc[0]), c
+    h.close()
+
+
 def test_residual_matches_oracle_operator(H):
     n = 16
     a = _coeff(n, 601)
