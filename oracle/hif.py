@@ -14,7 +14,10 @@ and then F^{-1} = W^0 ... W^{L-1} W^L D^{-1} W^{L T} ... W^{0 T}.
 
 Readings (the paper is silent or ambiguous on these):
   * LDL^T is taken as Cholesky (D = I): A is SPD for b >= 0 with the Dirichlet
-    boundary, and so are all Schur complements;
+    boundary, and so are all Schur complements.  On the periodic grid A is
+    SPD only for b > 0, its smallest eigenvalue is about b, and a compression
+    error above that can leave an indefinite Schur complement (the paper's
+    LDL^T with GMRES covers that case; Cholesky then stops at the root);
   * faces of a level are skeletonized independently, each from the matrix as
     it stands after that level's cell eliminations (the distributed algorithm
     of §3.2 does them concurrently); edges likewise, after all faces;
@@ -108,12 +111,12 @@ def _zero_rows_cols(A: sp.csr_matrix, idx: np.ndarray) -> sp.csr_matrix:
     return A
 
 
-def _closure_dofs(groups: dict, cell_codes, exclude) -> np.ndarray:
+def _closure_dofs(groups: dict, cell_codes, exclude, ncode: int = 0) -> np.ndarray:
     """Active DOFs in the union of the closures of the given cells, minus `exclude`."""
     seen = set()
     parts = []
     for cc in cell_codes:
-        for g in geo.cell_closure(cc):
+        for g in geo.cell_closure(cc, ncode):
             if g in groups and g not in seen and g != exclude:
                 seen.add(g)
                 parts.append(groups[g])
@@ -131,13 +134,13 @@ def _check_local(A: sp.csr_matrix, rows: np.ndarray, allowed: np.ndarray):
         raise AssertionError(f"front couples to {extra.size} DOFs outside its closure")
 
 
-def _eliminate_cells(A, groups, level, fac: Factor, check: bool):
+def _eliminate_cells(A, groups, level, fac: Factor, check: bool, ncode: int = 0):
     rows, cols, vals = [], [], []
     eliminated = []
     for code, I in groups.items():
         if geo.kind(code) != geo.KIND_CELL:
             continue
-        N = _closure_dofs(groups, [code], exclude=code)
+        N = _closure_dofs(groups, [code], exclude=code, ncode=ncode)
         if check:
             _check_local(A, I, np.union1d(I, N))
         A_II = _dense(A, I, I)
@@ -162,14 +165,14 @@ def _eliminate_cells(A, groups, level, fac: Factor, check: bool):
     return A, (np.concatenate(eliminated) if eliminated else np.zeros(0, np.int64))
 
 
-def _skeletonize(A, groups, level, want_kind, eps, fac: Factor, check: bool):
+def _skeletonize(A, groups, level, want_kind, eps, fac: Factor, check: bool, ncode: int = 0):
     """Skeletonize every group of `want_kind` independently (level-synchronous)."""
     rows, cols, vals = [], [], []
     redundant = []
     for code, F in groups.items():
         if geo.kind(code) != want_kind or F.size == 0:
             continue
-        R = _closure_dofs(groups, geo.adjacent_cells(code), exclude=code)
+        R = _closure_dofs(groups, geo.adjacent_cells(code, ncode), exclude=code, ncode=ncode)
         if check:
             _check_local(A, F, np.union1d(F, R))
         A_RF = _dense(A, R, F)
@@ -209,8 +212,13 @@ def _skeletonize(A, groups, level, want_kind, eps, fac: Factor, check: bool):
     return A, red_all
 
 
-def hif_factor(A0: sp.spmatrix, n: int, m: int, eps: float, check: bool = True) -> Factor:
-    """Factor A ~= F per §2.4 and return the sparse factors W^0..W^L."""
+def hif_factor(A0: sp.spmatrix, n: int, m: int, eps: float, check: bool = True,
+               periodic: bool = False) -> Factor:
+    """Factor A ~= F per §2.4 and return the sparse factors W^0..W^L.
+
+    periodic=True takes the periodic geometry (every multiple of the cell side
+    is a separator and the cells wrap around, see geometry.py); A0 must then be
+    the periodic operator."""
     L = geo.num_levels(n, m)
     A = sp.csr_matrix(A0, dtype=np.float64, copy=True)
     fac = Factor(n=n, m=m, eps=float(eps))
@@ -218,13 +226,14 @@ def hif_factor(A0: sp.spmatrix, n: int, m: int, eps: float, check: bool = True) 
     for level in range(L):
         s = m << level
         before = int(active.sum())
-        groups = geo.group_active(np.flatnonzero(active), n, s)
-        A, elim = _eliminate_cells(A, groups, level, fac, check)
+        ncode = 2 * (n // s) if periodic else 0
+        groups = geo.group_active(np.flatnonzero(active), n, s, periodic)
+        A, elim = _eliminate_cells(A, groups, level, fac, check, ncode)
         active[elim] = False
         if eps > 0.0:
             for want in (geo.KIND_FACE, geo.KIND_EDGE):
-                groups = geo.group_active(np.flatnonzero(active), n, s)
-                A, red = _skeletonize(A, groups, level, want, eps, fac, check)
+                groups = geo.group_active(np.flatnonzero(active), n, s, periodic)
+                A, red = _skeletonize(A, groups, level, want, eps, fac, check, ncode)
                 active[red] = False
         fac.ranks.append((before, int(active.sum())))
     S = np.flatnonzero(active)

@@ -61,3 +61,29 @@ def test_every_dof_eliminated_once(eps):
     allidx = np.concatenate(parts)
     assert allidx.size == n ** 3
     assert np.array_equal(np.sort(allidx), np.arange(n ** 3))
+
+
+@pytest.mark.parametrize("n,m", [(8, 4), (16, 4), (32, 4), (12, 3)])
+def test_periodic_group_counts_closed_form(n, m):
+    # periodic grid: every multiple of s is a separator (each cell owns its
+    # first frame, §2.1), so c^3 cells, 3c^3 faces, 3c^3 edges, c^3 vertices
+    L = geo.num_levels(n, m)
+    for level in range(L):
+        s = m << level
+        c = n // s
+        got = geo.count_groups(n, s, periodic=True)
+        assert got == {geo.KIND_CELL: c ** 3, geo.KIND_FACE: 3 * c ** 3,
+                       geo.KIND_EDGE: 3 * c ** 3, geo.KIND_VERTEX: c ** 3}
+
+
+def test_periodic_closures_wrap():
+    # the last cell's closure holds plane 0; a face on plane 0 lies between
+    # the last cell and the first
+    n, s = 16, 4
+    ncode = 2 * (n // s)
+    last = (ncode - 1, 1, 1)
+    assert (0, 1, 1) in geo.cell_closure(last, ncode)
+    assert sorted(geo.adjacent_cells((0, 1, 1), ncode)) == [(1, 1, 1), (ncode - 1, 1, 1)]
+    g = geo.group_active(np.arange(n ** 3), n, s, periodic=True)
+    sizes = {geo.kind(k): v.size for k, v in g.items()}
+    assert sizes == {0: 27, 1: 9, 2: 3, 3: 1}   # every group has the interior shape

@@ -187,3 +187,32 @@ def test_planted_dropped_schur_term_is_caught(monkeypatch):
     f = np.random.default_rng(12).standard_normal(n ** 3)
     ref = sla.cho_solve(sla.cho_factor(A.toarray()), f)
     assert np.linalg.norm(hif.hif_apply(fac, f) - ref) > 1e-6 * np.linalg.norm(ref)
+
+
+# ---- periodic grid -------------------------------------------------------------
+
+@pytest.mark.parametrize("n,m,b", [(8, 4, 0.3), (12, 3, 1.0)])
+def test_periodic_exact_mode_matches_dense_solve(n, m, b):
+    rng = np.random.default_rng(21)
+    A = stencil.assemble(10.0 ** rng.uniform(-1, 1, n ** 3), b, n, periodic=True)
+    fac = hif.hif_factor(A, n, m, 0.0, periodic=True)
+    # eps = 0: the root keeps the separator planes of the last level, n^3 - (n - 2)^3
+    assert fac.root.S.size == n ** 3 - (n - 2) ** 3
+    f = rng.standard_normal((2, n ** 3))
+    u = hif.hif_apply(fac, f)
+    ref = sla.cho_solve(sla.cho_factor(A.toarray()), f.T).T
+    assert np.linalg.norm(u - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_periodic_error_scales_with_eps():
+    # a well-conditioned periodic problem (b = 20 keeps the smallest
+    # eigenvalue well above the compression error): e_s falls with eps
+    n = 16
+    rng = np.random.default_rng(22)
+    A = stencil.assemble(10.0 ** rng.uniform(-1, 1, n ** 3), 20.0, n, periodic=True)
+    x = rng.standard_normal(n ** 3)
+    es = []
+    for eps in (1e-2, 1e-4):
+        fac = hif.hif_factor(A, n, 4, eps, periodic=True)
+        es.append(np.linalg.norm(x - hif.hif_apply(fac, A @ x)) / np.linalg.norm(x))
+    assert es[1] < es[0] < 0.5 and es[1] < 1e-2
