@@ -80,10 +80,12 @@ typedef struct {
   double pcg_tol;    /* hif_solve stops when ||r||_2 <= pcg_tol ||f||_2 */
   int max_iter;      /* hif_solve iteration limit */
   int tensor_cores;  /* HIF_PREC_FP32 only.  1: the deep products of the
-                        partial Cholesky and of the row reduction run on the
-                        tensor cores (TF32 with the 3xTF32 split, FP32
-                        accumulation); 0: every product on the FP32 FMA
-                        units.  FP64 factors never use them. */
+                        partial Cholesky (the cell products X^T = A_NI L^-T and
+                        A_NN -= X^T X, the rank-256 block updates, the large
+                        triangular-inverse merges) run on the tensor cores
+                        (TF32 with the 3xTF32 split, FP32 accumulation); 0:
+                        every product on the FP32 FMA units.  FP64 factors
+                        never use them. */
 } hif_options;
 
 /* Fill *opt with defaults: eps 1e-6, FP64, graphs on, pcg_tol 1e-10, 200 its,
