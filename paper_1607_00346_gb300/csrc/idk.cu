@@ -519,12 +519,14 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
   // fronts whose matrix fits in shared memory: one CTA each, in three size
   // classes (128, 256 or 1024 threads; dynamic shared memory of the class's
   // largest front)
-  static bool smem_attr[2] = {false, false};
-  if (!smem_attr[sizeof(T) == 8]) {
+  // once per precision; a function-local static is initialised once even
+  // when several host threads factor at the same time
+  static const bool smem_attr = [] {
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_cpqr_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       SMEM_ID_MAX));
-    smem_attr[sizeof(T) == 8] = true;
-  }
+    return true;
+  }();
+  (void)smem_attr;
   constexpr size_t class_max[3] = {16 * 1024, 64 * 1024, (size_t)SMEM_ID_MAX};
   constexpr int class_threads[3] = {128, 256, 1024};
   std::vector<int> small[3], rest;
@@ -569,11 +571,11 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
     cs = std::min(cs, std::max(1, h_f[f].nF / 8));   // at least 8 columns per CTA
     bucket[cs].push_back(f);
   }
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[sizeof(T) == 8]) {
+  static const bool attr_set = [] {
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_cpqr<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    attr_set[sizeof(T) == 8] = true;
-  }
+    return true;
+  }();
+  (void)attr_set;
   for (int b = 1; b <= 16; ++b) {
     if (bucket[b].empty()) continue;
     int CS = b;

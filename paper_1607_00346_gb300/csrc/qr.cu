@@ -611,15 +611,15 @@ constexpr size_t QRC_SMEM_MAX = 160 * 1024;
 // memory limits).
 template <typename T>
 bool panel_cluster_fits_t(int cs, int rb) {
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {   // initialised once, also under concurrent factorizations
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel_cluster<T>,
                                       cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel_cluster<T>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)QRC_SMEM_MAX));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   const size_t smem = (size_t)rb * QB * sizeof(T);
   if (smem > QRC_SMEM_MAX) return false;
   cudaLaunchConfig_t q = {};
@@ -714,12 +714,12 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
   HIF_CUDA_TRY(cudaMallocAsync(&Wp, sizeof(T) * std::max<int64_t>(1, wptot), st));
   HIF_CUDA_TRY(cudaMallocAsync(&d_wpo, sizeof(int64_t) * nq, st));
   HIF_CUDA_TRY(cudaMemcpyAsync(d_wpo, wpo.data(), sizeof(int64_t) * nq, cudaMemcpyHostToDevice, st));
-  static bool w1_attr = false;
-  if (!w1_attr) {
+  static const bool w1_attr = [] {
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_qr_w1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)w1_smem_bytes<T>()));
-    w1_attr = true;
-  }
+    return true;
+  }();
+  (void)w1_attr;
   for (int p = 0; p < nmax; p += QB) {
     int nact = 0;
     while (nact < nq && qd[nact].n > p) ++nact;

@@ -304,12 +304,12 @@ void launch_tc(const GemmOp* d_ops, int nops, int mt, const float* Abase, const 
                float* Cbase, int* d_flags, cudaStream_t st, int S = 1,
                const int64_t* d_woff = nullptr, float* Wk = nullptr) {
   constexpr size_t smem = 2 * (size_t)(2 * TC_M * KC * 4 + 2 * TN * KC * 4);
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {   // initialised once, also under concurrent factorizations
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<KC, TN>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   for (int f0 = 0; f0 < nops; f0 += 65535) {
     const int nb = std::min(65535, nops - f0);
     k_gemm_tc<KC, TN><<<dim3(mt, nb, S), TC_M + TN, smem, st>>>(
@@ -336,8 +336,8 @@ void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Ab
   for (int i = 0; i < nops; ++i)
     mt = std::max(mt, ceil_div(h_ops[i].m, TC_M) * ceil_div(h_ops[i].n, tn));
   ProfScope ps(name, st, fl, 0.0);
-  // few output tiles and deep K (the pre-QR W1 = V^T A_t): split K so that
-  // the launch fills the GPU; partial tiles are summed in a fixed order
+  // few output tiles and deep K: split K so that the launch fills the GPU;
+  // partial tiles are summed in a fixed order
   int tiles = 0, kmin = 1 << 30;
   bool any_lower = false;
   for (int i = 0; i < nops; ++i) {
@@ -345,12 +345,12 @@ void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Ab
     kmin = std::min(kmin, h_ops[i].k);
     any_lower = any_lower || h_ops[i].lower;
   }
-  static int nsm = 0;
-  if (!nsm) {
-    int dev = 0;
+  static const int nsm = [] {
+    int dev = 0, count = 0;
     HIF_CUDA_TRY(cudaGetDevice(&dev));
-    HIF_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  }
+    HIF_CUDA_TRY(cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev));
+    return count;
+  }();
   const int kc = narrow ? 32 : 16;
   const int per_sm = narrow ? 1 : (tn == 256 ? 2 : 3);
   // S minimises the waves per unit of work, ceil(tiles S / capacity) / S,
