@@ -876,9 +876,9 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
   for (const SkelDesc& d : sda) {
     const int k = d.k, p = d.nF - k, nF = d.nF;
     if (k == 0) continue;
-    g1.push_back(GemmOp{d.Z + p + (int64_t)p * nF, d.Tm, d.Z + p, k, p, k, nF, k, nF, 0, 0, -1.f, 1.f});
-    g2.push_back(GemmOp{d.Z + (int64_t)p * nF, d.Tm, d.Z, p, p, k, nF, k, nF, 0, 0, -1.f, 1.f});
-    g3.push_back(GemmOp{d.Tm, d.Z + p, d.Z, p, p, k, k, nF, nF, 1, 0, -1.f, 1.f});
+    g1.push_back(GemmOp{d.Z + p + (int64_t)p * nF, d.Tm, d.Z + p, k, p, k, nF, k, nF, 0, 0, -1.f, 1.f, 0, 0});
+    g2.push_back(GemmOp{d.Z + (int64_t)p * nF, d.Tm, d.Z, p, p, k, nF, k, nF, 0, 0, -1.f, 1.f, 0, 0});
+    g3.push_back(GemmOp{d.Tm, d.Z + p, d.Z, p, p, k, k, nF, nF, 1, 0, -1.f, 1.f, 0, 0});
   }
   DevBuf g1d, g2d, g3d;
   upload_async(g1d, g1, &F_.mem, st_);
