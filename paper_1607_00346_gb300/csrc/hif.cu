@@ -1468,9 +1468,14 @@ size_t hif_predict_bytes(const hif_grid* grid, const hif_options* opt) {
   // Peak device bytes of hif_factor: the operator (32 B per DOF) plus factor
   // words per DOF growing with log2 n, fitted to measured peaks at eps = 1e-6
   // (64^3: ~2000 words per DOF, 128^3: ~3000) with a 25% margin, and at
-  // least 400 words per DOF for small grids.
+  // least 400 words per DOF for small grids.  A larger eps keeps fewer
+  // skeletons: the measured peaks shrink by ~0.56 per decade of eps above
+  // 1e-6 (64^3: 2.1 / 1.2 / 0.7 GB at 1e-6 / 1e-5 / 1e-4; 256^3 at 1e-4:
+  // 74 GB), taken here as 0.6 per decade, at most four decades.
   const double lg = std::log2((double)grid->n);
-  const double words = std::max(400.0, -3718.0 + 955.0 * lg);
+  double words = std::max(400.0, -3718.0 + 955.0 * lg);
+  const double eps = opt ? opt->eps : 1e-6;
+  if (eps > 1e-6) words *= std::pow(0.6, std::min(4.0, std::log10(eps / 1e-6)));
   return (size_t)(N * (32.0 + 1.25 * words * word) + (64u << 20));
 }
 

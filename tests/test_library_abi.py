@@ -45,6 +45,21 @@ def test_host_only_entry_points(lib):
     assert hif.load().hif_version().startswith(b"hif-gb300")
 
 
+def test_predicted_footprint_follows_eps_and_precision(lib):
+    # a larger eps keeps fewer skeletons, so the predicted peak shrinks; it
+    # stays above the operator (32 B per DOF) and above the peaks measured on
+    # the GPU for the same configurations (FP32 factor)
+    from paper_1607_00346_gb300 import hif
+    hif.load()
+    p = {e: hif.predict_bytes(64, 4, eps=e, precision=hif.PREC_FP32) for e in (0.0, 1e-6, 1e-5, 1e-4)}
+    assert p[0.0] == p[1e-6] > p[1e-5] > p[1e-4] > 32 * 64 ** 3
+    assert hif.predict_bytes(64, 4, eps=1e-6, precision=hif.PREC_FP64) > p[1e-6]
+    measured = {(64, 1e-6): 2.11e9, (64, 1e-5): 1.2e9, (64, 1e-4): 0.7e9,
+                (128, 1e-6): 24.9e9, (256, 1e-4): 74.3e9}
+    for (n, e), peak in measured.items():
+        assert hif.predict_bytes(n, 4, eps=e, precision=hif.PREC_FP32) > peak
+
+
 def test_load_rejects_bad_files(tmp_path):
     from paper_1607_00346_gb300 import hif
     hif.load()
