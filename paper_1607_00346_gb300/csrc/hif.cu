@@ -506,14 +506,16 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
     for (int32_t g : cp.active) alive[g] = 1;
     for (int c = 0; c < cp.ncell; ++c)
       for (int64_t t = cp.off[c]; t < cp.off[c] + cp.p[c]; ++t) alive[cp.dofs[t]] = 0;
+    // the planners read their own copy of `alive` (the face step changes
+    // it while the edge plan is still being built); declared before the
+    // futures, so it outlives them
+    std::vector<uint8_t> alive_plan;
     SkelPlan fplan, ep;
-    std::future<void> planning;
+    std::future<void> face_plan, edge_plan;
     if (level < L && F_.eps > 0.0) {
-      planning = std::async(std::launch::async, [&]() {
-        auto edges = std::async(std::launch::async, [&]() { sym_.build_skel(cp, 2, alive, ep); });
-        sym_.build_skel(cp, 1, alive, fplan);
-        edges.get();
-      });
+      alive_plan = alive;
+      face_plan = std::async(std::launch::async, [&]() { sym_.build_skel(cp, 1, alive_plan, fplan); });
+      edge_plan = std::async(std::launch::async, [&]() { sym_.build_skel(cp, 2, alive_plan, ep); });
     }
     cell_step(cpp, Kar, cdesc_d, cdesc, lists_d);
     tr_.mark(level, "cell elimination");
@@ -526,11 +528,15 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
       break;
     }
     if (F_.eps > 0.0) {
-      planning.get();
-      start_stage_jobs();
-      tr_.mark(level, "plans joined");
+      // the face step starts once its plan is ready; the edge plan goes on
+      // meanwhile and is joined after the face step
+      face_plan.get();
+      tr_.mark(level, "face plan joined");
       const int64_t dropped = skel_step(cp, 1, alive, Kar, cdesc_d, &fplan);
       tr_.mark(level, "faces");
+      edge_plan.get();
+      start_stage_jobs();
+      tr_.mark(level, "edge plan joined");
       if (dropped) sym_.filter_rows(ep, alive);
       // the next level's cells, assuming the edges keep every DOF (they
       // usually do), are planned on a host thread while the edges run;
