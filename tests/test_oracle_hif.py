@@ -216,3 +216,28 @@ def test_periodic_error_scales_with_eps():
         fac = hif.hif_factor(A, n, 4, eps, periodic=True)
         es.append(np.linalg.norm(x - hif.hif_apply(fac, A @ x)) / np.linalg.norm(x))
     assert es[1] < es[0] < 0.5 and es[1] < 1e-2
+
+
+def _golden(name):
+    import os
+    out = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                out[k] = float(v)
+    return out
+
+
+def test_periodic_example1_matches_the_papers_table():
+    # the paper's Example 1 at 32^3 (periodic, a = 1, b = 0.1 against the
+    # unscaled stencil, eps = 1e-3): the oracle keeps exactly the printed
+    # number of top-level points and its e_s lies in the printed range
+    g = _golden("example1_periodic_32.txt")
+    n, m = int(g["n"]), int(g["m"])
+    A = stencil.assemble(np.ones(n ** 3), g["b_over_stencil"] * n * n, n, periodic=True)
+    fac = hif.hif_factor(A, n, m, g["eps"], check=False, periodic=True)
+    assert fac.root.S.size == int(g["root_size"])
+    x = np.random.default_rng(2).standard_normal(n ** 3)
+    es = np.linalg.norm(x - hif.hif_apply(fac, A @ x)) / np.linalg.norm(x)
+    assert g["es_min"] <= es <= g["es_max"], es
