@@ -58,7 +58,8 @@ int hif_num_levels(int n, int m) {
   return (1 << L) == q ? L : -1;
 }
 
-Symbolic::Symbolic(int n, int m) : n_(n), m_(m), L_(hif_num_levels(n, m)) {
+Symbolic::Symbolic(int n, int m, bool periodic)
+    : n_(n), m_(m), L_(hif_num_levels(n, m)), periodic_(periodic) {
   active_.resize((size_t)n * n * n);
   for (size_t i = 0; i < active_.size(); ++i) active_[i] = (int32_t)i;
 }
@@ -72,7 +73,9 @@ inline int32_t pos_at(const CellPlan& cp, int32_t sl, int64_t pk, const int* c) 
   for (int d = 0; d < 3; ++d) {
     const int lc = (int)((pk >> (16 * d)) & 0xffff);
     if (c[d] == lc) continue;
-    if (((sep >> d) & 1) && c[d] == lc + 1) {
+    // the upper cell of a separator (wrapping on the periodic grid; with a
+    // Dirichlet boundary lc + 1 < C always holds)
+    if (((sep >> d) & 1) && c[d] == (lc + 1 == cp.C ? 0 : lc + 1)) {
       q |= 1 << d;
       continue;
     }
@@ -141,17 +144,19 @@ void Symbolic::build_cells_from(int level, const std::vector<int32_t>& active, C
     int64_t pk = 0;
     int sep = 0;
     for (int d = 0; d < 3; ++d) {
-      bool sd = x[d] != 0 && x[d] % s == 0;
-      int lc = sd ? x[d] / s - 1 : x[d] / s;
+      // periodic: the top level (one cell) has no separators; below it the
+      // cell under plane 0 is the last one
+      bool sd = periodic_ ? (level < L_ && x[d] % s == 0) : (x[d] != 0 && x[d] % s == 0);
+      int lc = sd ? (x[d] / s + C - 1) % C : x[d] / s;
       if (sd) sep |= 1 << d;
       pk |= (int64_t)lc << (16 * d);
     }
     cp.packed[i] = pk | ((int64_t)sep << 48);
   });
   auto cell_of = [&](int64_t pk, int q) {
-    int c0 = (int)(pk & 0xffff) + (q & 1);
-    int c1 = (int)((pk >> 16) & 0xffff) + ((q >> 1) & 1);
-    int c2 = (int)((pk >> 32) & 0xffff) + ((q >> 2) & 1);
+    int c0 = ((int)(pk & 0xffff) + (q & 1)) % C;
+    int c1 = ((int)((pk >> 16) & 0xffff) + ((q >> 1) & 1)) % C;
+    int c2 = ((int)((pk >> 32) & 0xffff) + ((q >> 2) & 1)) % C;
     return c0 + C * (c1 + C * c2);
   };
   // interior / boundary counts per cell, per chunk of the active list; the
@@ -316,7 +321,7 @@ void Symbolic::build_skel(const CellPlan& cp, int kind, const std::vector<uint8_
     int j = 0;
     for (int q = 0; q < 8; ++q) {
       if (q & ~sep) continue;
-      int c[3] = {lc[0] + (q & 1), lc[1] + ((q >> 1) & 1), lc[2] + ((q >> 2) & 1)};
+      int c[3] = {(lc[0] + (q & 1)) % C, (lc[1] + ((q >> 1) & 1)) % C, (lc[2] + ((q >> 2) & 1)) % C};
       sp.cells[(size_t)f * ncp + j] = c[0] + C * (c[1] + C * c[2]);
       for (int d = 0; d < 3; ++d) cellxyz[((size_t)f * ncp + j) * 3 + d] = c[d];
       ++j;

@@ -2,6 +2,9 @@
 //
 // Geometry (§2.1, read for a zero Dirichlet boundary): at level l the cell
 // side is s = m 2^l; coordinate x is a separator iff x % s == 0 and x != 0.
+// On the periodic grid every multiple of s below the top level is a
+// separator (x = 0 included, each cell owning its first frame as in §2.1)
+// and cell indices wrap: the cell below plane 0 is the last one.
 // A DOF with 0 / 1 / 2 / 3 separator coordinates is a cell-interior / face /
 // edge / vertex point.  The lowest cell holding coordinate x along a dimension
 // is x/s - 1 for a separator and x/s otherwise; a separator coordinate also
@@ -75,10 +78,11 @@ struct SkelPlan {
 
 class Symbolic {
  public:
-  Symbolic(int n, int m);
+  Symbolic(int n, int m, bool periodic = false);
   int n() const { return n_; }
   int m() const { return m_; }
   int levels() const { return L_; }
+  bool periodic() const { return periodic_; }
 
   // Build the cell plan of `level` from the current active set.
   void build_cells(int level, CellPlan& cp) const;
@@ -106,6 +110,7 @@ class Symbolic {
 
  private:
   int n_, m_, L_;
+  bool periodic_;
   std::vector<int32_t> active_;
 };
 

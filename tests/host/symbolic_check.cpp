@@ -1,6 +1,7 @@
 // Consistency check of the host symbolic pass (no GPU): every position the
 // kernels will dereference points at the DOF it claims, and the group counts
-// match the closed forms c^3, 3(c-1)c^2, 3(c-1)^2 c, (c-1)^3.
+// match the closed forms c^3, 3(c-1)c^2, 3(c-1)^2 c, (c-1)^3 (Dirichlet) or
+// c^3, 3c^3, 3c^3, c^3 (periodic grid: third argument "p").
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -22,13 +23,18 @@ static int fails = 0;
     }                                      \
   } while (0)
 
-static bool is_sep(int x, int s) { return x != 0 && x % s == 0; }
+static bool periodic = false;
+static int L = 0;
+static bool is_sep(int x, int s, int level) {
+  return periodic ? (level < L && x % s == 0) : (x != 0 && x % s == 0);
+}
 
 int main(int argc, char** argv) {
   int n = argc > 1 ? std::atoi(argv[1]) : 16;
   int m = argc > 2 ? std::atoi(argv[2]) : 4;
-  Symbolic sym(n, m);
-  const int L = sym.levels();
+  periodic = argc > 3 && argv[3][0] == 'p';
+  Symbolic sym(n, m, periodic);
+  L = sym.levels();
   const int64_t N = (int64_t)n * n * n;
   CellPlan prev;
   long long rows_total = 0;
@@ -47,8 +53,11 @@ int main(int argc, char** argv) {
         bool interior = t < cp.off[c] + cp.p[c];
         for (int d = 0; d < 3; ++d) {
           const int lo = s * cc[d], hi = std::min(s * (cc[d] + 1), n - 1);
-          CHECK(x[d] >= lo && x[d] <= hi, "dof %d outside closure of cell %d", g, c);
-          if (interior) CHECK(!is_sep(x[d], s), "interior dof %d on a separator", g);
+          if (periodic)   // the closure runs from plane lo to plane lo + s, wrapping
+            CHECK(((x[d] - lo) % n + n) % n <= s, "dof %d outside closure of cell %d", g, c);
+          else
+            CHECK(x[d] >= lo && x[d] <= hi, "dof %d outside closure of cell %d", g, c);
+          if (interior) CHECK(!is_sep(x[d], s, level), "interior dof %d on a separator", g);
         }
         if (interior) seenI[g]++;
         else {
@@ -132,7 +141,7 @@ int main(int argc, char** argv) {
       for (int32_t g : cp.active) {
         const int x[3] = {g % n, (g / n) % n, g / (n * n)};
         int ns = 0;
-        for (int d = 0; d < 3; ++d) ns += is_sep(x[d], s);
+        for (int d = 0; d < 3; ++d) ns += is_sep(x[d], s, level);
         if (ns == 1 && alive_post[g] && (t++ % 3 == 0)) alive_post[g] = 0;
       }
       SkelPlan a, b;
@@ -144,8 +153,8 @@ int main(int argc, char** argv) {
             "filtered edge plan differs at level %d", level);
     }
     const int c = C;
-    CHECK(counts[1] == 3 * (c - 1) * c * c, "face count");
-    CHECK(counts[2] == 3 * (c - 1) * (c - 1) * c, "edge count");
+    CHECK(counts[1] == (periodic ? 3 * c * c * c : 3 * (c - 1) * c * c), "face count");
+    CHECK(counts[2] == (periodic ? 3 * c * c * c : 3 * (c - 1) * (c - 1) * c), "edge count");
     std::printf("level %d: %d cells, %d faces, %d edges\n", level, counts[0], counts[1], counts[2]);
     std::vector<int32_t> next;
     for (int32_t g : cp.active)

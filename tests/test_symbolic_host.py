@@ -34,3 +34,14 @@ def test_symbolic_consistent(checker, n, m):
     assert p.stdout.strip().endswith("OK")
     root = [l for l in p.stdout.splitlines() if "root" in l][0]
     assert int(root.split(":")[1].split()[0]) == n ** 3 - (n - 1) ** 3
+
+
+@pytest.mark.parametrize("n,m", [(8, 4), (16, 4), (12, 3), (20, 5), (32, 4)])
+def test_symbolic_consistent_periodic(checker, n, m):
+    # periodic grid: wrapping closures, c^3 / 3c^3 / 3c^3 fronts per level, and
+    # at eps = 0 the root keeps the last level's separator planes, 0 and n/2
+    p = subprocess.run([checker, str(n), str(m), "p"], stdout=subprocess.PIPE, text=True)
+    assert p.returncode == 0, p.stdout
+    assert p.stdout.strip().endswith("OK")
+    root = [l for l in p.stdout.splitlines() if "root" in l][0]
+    assert int(root.split(":")[1].split()[0]) == n ** 3 - (n - 2) ** 3
