@@ -59,37 +59,42 @@ def field_desc(w: dict) -> str:
         return f"a=10^U({w['lo']},{w['hi']}) iid per point"
     return "a=1"
 
-# FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
-FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# FP64 peak of the part (1.25 TFLOP/s, the quoted dense FP64 rate of GB300)
-FP64_ALU_PEAK_TFLOPS = 1.25
-
-
-# roofline of each profiled kernel: tensor-core products, FMA-unit dense
-# algebra, or HBM streams (the ID's trailing-matrix passes and the apply's
-# mat-vecs read each entry once per step / per sweep)
+# Roofline class of each profiled kernel label.  "tensor": tcgen05 products
+# (algorithmic 2mnk flops over the measured TF32 tensor-core rate; the 3xTF32
+# split issues three TF32 products per algorithmic one, so such a kernel
+# tops out at a third of that rate).  "alu": dense algebra on the FMA units,
+# including the pivoted QR of the ID and the row-reduction panels, which are
+# latency- and FMA-bound (algorithmic Householder flops over the measured
+# FMA rate of the factor's precision).  "hbm": streams whose bytes bound them
+# (the apply's mat-vecs, gathers, the stencil, vector updates, the
+# row-reduction trailing update).
 KERNEL_BOUND = {
-    "gemm_tc": "tensor",
-    "id_cpqr": "hbm", "id_rowreduce_panel": "hbm", "apply_gemv_n": "hbm", "apply_gemv_t": "hbm",
-    "skel_gather": "hbm", "merge_children": "hbm", "spmv": "hbm", "residual": "hbm",
-    "id_rowreduce_update": "hbm",
+    "gemm_tc": "tensor", "chol_block_update_tc": "tensor", "trtri_merge_tc": "tensor",
     "chol_panel": "alu", "chol_trailing_update": "alu", "gemm_batched": "alu",
-    "trtri_merge": "alu", "id_cpqr_smem": "alu", "id_rowreduce_w1": "alu",
-    "skel_z_products": "alu", "chol_block_update": "tensor",
+    "trtri_merge": "alu", "trtri_diag": "alu", "id_cpqr": "alu", "id_cpqr_smem": "alu",
+    "id_rowreduce_panel": "alu", "id_rowreduce_w1": "alu", "skel_z_products": "alu",
+    "chol_block_update": "alu",
+    "apply_gemv_n": "hbm", "apply_gemv_t": "hbm", "apply_sweeps_graph": "hbm",
+    "apply_gather": "hbm", "apply_scatter": "hbm", "apply_accumulate": "hbm",
+    "convert": "hbm", "skel_gather": "hbm", "merge_children": "hbm", "spmv": "hbm",
+    "residual": "hbm", "dots": "hbm", "axpy": "hbm", "id_rowreduce_update": "hbm",
+    "stencil_coefficients": "hbm",
 }
 
-# nominal dense TF32 / bf16 tensor ratio (1.1 / 2.25 PFLOP/s)
-TF32_PER_BF16 = 1.1 / 2.25
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
+# kernel label in the bench workload, from the ncu capture summarised in
+# profiles/ (None where no capture of the current kernel exists).
+TRAFFIC_PER_LAUNCH = {}
 
 
-def _peaks():
-    """(hbm GB/s, bf16 TFLOP/s burst, source) from the measured peaks file."""
+def _hbm_peak():
+    """(hbm GB/s, source) from the measured peaks file."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             p = json.load(fh)
-        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+        return float(p["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
     except Exception:
-        return 6800.0, 1900.0, "fallback"
+        return 6800.0, "fallback"
 
 
 class ClockSampler:
@@ -213,15 +218,12 @@ def run_reference(args, w):
     return 0
 
 
-def run_serving(args):
-    """Config 4: Poisson request stream, resident operators, batched solves."""
+def serving_record(args):
+    """Serving workload: Poisson request stream, resident operators, batched solves."""
     import torch
 
-    import __graft_entry__ as ge
-    ge.build()
     from paper_1607_00346_gb300 import serving
 
-    torch.cuda.set_device(0)
     sizes = [32, 48, 64, 96, 128]
     be = serving.HifBackend(eps=1e-6, precision=1, lo=-2.0, hi=2.0, b=0.0)
     budget = int(args.serve_budget_gb * (1 << 30))
@@ -254,8 +256,54 @@ def run_serving(args):
         st = srv.run(reqs)
         srv.release_all()
         out["loads"][str(load)] = st
-    print(json.dumps(out), flush=True)
+    torch.cuda.synchronize()
+    return out
+
+
+def run_serving(args):
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    torch.cuda.set_device(0)
+    print(json.dumps(serving_record(args)), flush=True)
     return 0
+
+
+def contrast256_record(hif, torch):
+    """One untimed and one timed factor + PCG step of the 256^3 workload
+    (a = 10^U(-3,3), b = 0, eps = 1e-4, FP32 factor), with its memory."""
+    from paper_1607_00346_gb300 import inputs
+    w = WORKLOADS["contrast256"]
+    n, seed = w["n"], inputs.SEED_BASE + 4
+    a = torch.from_numpy(make_field(w, n, seed)).cuda()
+    f = torch.from_numpy(inputs.normal_rhs(n, 1, seed + 1)).cuda()
+    u = torch.zeros_like(f)
+    st = torch.cuda.current_stream()
+    rec = None
+    for k in range(2):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(st)
+        h = hif.factor(n, w["m"], a, b_const=w["b"], eps=w["eps"], precision=hif.PREC_FP32)
+        ev[1].record(st)
+        its, rel = h.solve(f, u)
+        ev[2].record(st)
+        torch.cuda.synchronize()
+        stt = h.stats()
+        h.close()
+        if k == 1:
+            fs, ss = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
+            rec = {"workload": f"n=256 (N={n ** 3}), {field_desc(w)}, b={w['b']}, eps={w['eps']}, "
+                               "fp32 factor, FP64 PCG to 1e-10, nrhs=1",
+                   "factor_s": fs, "solve_s": ss, "pcg_iters": its[0], "relres": rel[0],
+                   "value": n ** 3 / (fs + ss) / 1e6, "unit": UNIT,
+                   "peak_bytes": stt["peak_bytes"], "factor_bytes": stt["factor_bytes"],
+                   "predicted_bytes": hif.predict_bytes(n, w["m"], eps=w["eps"],
+                                                        precision=hif.PREC_FP32),
+                   "hbm_budget_bytes": 180 * 10 ** 9, "root_size": stt["root_size"]}
+    del a, f, u
+    torch.cuda.empty_cache()
+    return rec
 
 
 def main():
@@ -271,10 +319,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=32)
     ap.add_argument("--serve", action="store_true", help="run the serving benchmark instead")
-    ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--serve-requests", type=int, default=30)
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=200.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the serving and 256^3 records of the default line")
     args = ap.parse_args()
+    if args.gpus > 1 and int(os.environ.get("WORLD_SIZE", "1")) != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} runs one process per GPU: launch it with "
+                         f"python -m torch.distributed.run --nproc-per-node {args.gpus} ...")
     if args.serve:
         return run_serving(args)
     w = dict(WORKLOADS[args.workload])
@@ -302,6 +355,8 @@ def main():
         dist.barrier()
     from paper_1607_00346_gb300 import hif, inputs
     hif.load()
+    # arithmetic peaks of this GPU, measured before anything else runs
+    peaks = hif.measure_peaks()
 
     n, m, nrhs = w["n"], w["m"], w["nrhs"]
     N = n ** 3
@@ -382,7 +437,7 @@ def main():
     e2e_value = e2e_rate / 1e6
 
     # roofline of the dominant kernel (largest share of the timed region)
-    hbm_peak, bf16_peak, peak_src = _peaks()
+    hbm_peak, hbm_src = _hbm_peak()
     total_prof_s = max(sum(p["seconds"] for p in prof), 1e-12)
 
     def roofline(k):
@@ -391,28 +446,33 @@ def main():
         if bound == "tensor":
             # algorithmic flops 2mnk of the products (the 3xTF32 split issues
             # three TF32 products per algorithmic one; that cost is the kernel's)
-            peak = bf16_peak * TF32_PER_BF16
+            peak = peaks["tf32_mma_tflops"]
             ach = k["flops"] / max(k["launches"], 1) / per_launch_s / 1e12
-            src = f"{peak_src} bf16_tflops x nominal tf32/bf16 ratio"
+            src = "measured in this run: tcgen05 kind::tf32 loop (hif_measure_peaks)"
             unit = "TFLOP/s"
         elif bound == "alu":
-            peak = FP32_ALU_PEAK_TFLOPS if prec == hif.PREC_FP32 else FP64_ALU_PEAK_TFLOPS
+            fp32 = prec == hif.PREC_FP32
+            peak = peaks["fp32_fma_tflops" if fp32 else "fp64_fma_tflops"]
             ach = k["flops"] / max(k["launches"], 1) / per_launch_s / 1e12
-            src = "unit counts x max clock"
+            src = (f"measured in this run: {'FP32' if fp32 else 'FP64'} FMA loop "
+                   "(hif_measure_peaks)")
             unit = "TFLOP/s"
         else:
             peak = hbm_peak
             ach = k["bytes"] / max(k["launches"], 1) / per_launch_s / 1e9
-            src = f"{peak_src} hbm_gbs"
+            src = hbm_src
             unit = "GB/s"
         return {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                "traffic": None, "kernel": k["name"], "peak_source": src,
-                "share": k["seconds"] / total_prof_s}
+                "traffic": TRAFFIC_PER_LAUNCH.get(k["name"]), "kernel": k["name"],
+                "peak_source": src, "share": k["seconds"] / total_prof_s,
+                "launches_per_step": k["launches"] / args.steps}
 
     dom = max(prof, key=lambda p: p["seconds"])
-    launches = sum(p["launches"] for p in prof)
+    # kernels run in the timed region: every launch, the ones inside replayed
+    # apply graphs included
+    launches = sum(p["kernels"] for p in prof)
     roof = roofline(dom)
-    roof_top = [roofline(k) for k in sorted(prof, key=lambda p: -p["seconds"])[:8]]
+    roof_top = [roofline(k) for k in sorted(prof, key=lambda p: -p["seconds"])[:10]]
 
     # the plain FP64 GPU form of the same step (comparison point), one run
     fp64_form = None
@@ -436,6 +496,11 @@ def main():
                "kind": "oracle",
                "sample": f"CPU oracle factor + PCG on a {args.cpu_sample_n}^3 grid of the same "
                          f"coefficient law (N={args.cpu_sample_n ** 3}), {dt:.1f} s"}
+
+    extras = {}
+    if not args.no_extras and ws == 1:
+        extras["contrast256"] = contrast256_record(hif, torch)
+        extras["serving"] = serving_record(args)
 
     lat = sorted(per_step)
     p50 = statistics.median(lat)
@@ -466,8 +531,10 @@ def main():
                  if k in ("kernel", "bound", "achieved", "frac", "share", "unit")}
                 for r in roof_top], "cpu_baseline": cpu, "fp64_form": fp64_form,
             "kernels": {p["name"]: round(p["seconds"] / args.steps, 5) for p in
-                        sorted(prof, key=lambda p: -p["seconds"])[:8]},
+                        sorted(prof, key=lambda p: -p["seconds"])[:12]},
+            "peaks": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in peaks.items()},
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -75,8 +75,8 @@ typedef struct {
   int use_graphs;    /* 1: the two sweeps of an apply (hif_apply, and the
                         preconditioner inside hif_solve) are captured once
                         per nrhs as a CUDA graph on a private stream and
-                        replayed on the caller's stream (not while the kernel
-                        profile is on); 0: launched one by one */
+                        replayed on the caller's stream; 0: launched one by
+                        one */
   double pcg_tol;    /* hif_solve stops when ||r||_2 <= pcg_tol ||f||_2 */
   int max_iter;      /* hif_solve iteration limit */
   int tensor_cores;  /* HIF_PREC_FP32 only.  1: the deep products of the
@@ -181,6 +181,18 @@ typedef struct {
 hif_status hif_query_stats(hif_handle h, hif_stats* st);
 
 /*
+ * hif_query_active -- the DOFs still active after level `level` (Sigma^{l+1}
+ * of §2.4: what the level's cell eliminations and the interpolative
+ * decompositions of its faces and edges kept), as sorted grid indices in
+ * host memory.  level = L-1 gives the root set Sigma^L.  Call it with
+ * out = NULL to get *count, then again with cap >= *count.
+ * Errors: INVALID_ARG (NULL handle or count, level outside [0, L), cap too
+ * small).
+ */
+hif_status hif_query_active(hif_handle h, int level, int32_t* out, int64_t cap,
+                            int64_t* count);
+
+/*
  * hif_predict_bytes -- device bytes hif_factor is expected to need at its
  * peak for this grid and options (used for admission control): an upper
  * estimate fitted to measured peaks (within ~25-60% above them at eps 1e-6
@@ -195,11 +207,14 @@ size_t hif_predict_bytes(const hif_grid* grid, const hif_options* opt);
  * hif_profile_end() stops, waits for the recorded events and writes up to
  * cap per-kernel aggregates (*count receives the number available).  flops
  * and bytes are the algorithmic counts of the launches (0 where not defined).
+ * An apply whose sweeps replay a CUDA graph is timed as one launch named
+ * "apply_sweeps_graph" (its kernels are not timed one by one).
  * Process-wide; meant for benchmarking, not for concurrent use.
  */
 typedef struct {
   char name[48];
-  int64_t launches;
+  int64_t launches;    /* timed launches (a CUDA graph replay counts as one) */
+  int64_t kernels;     /* kernels those launches ran (a replay runs many) */
   double seconds;
   double flops;
   double bytes;
@@ -221,8 +236,12 @@ void hif_destroy(hif_handle h);
  *   handle applies and solves exactly as the saved one (bitwise the same
  *   results).  Files are read only by the build that wrote them (the
  *   option and statistics layouts are checked).
+ *   hif_load checks every count, index and mat-vec extent of the file
+ *   against the sizes of the arrays it read (and the apply work stride
+ *   against the stage lists) before any kernel can use them.
  * Errors: INVALID_ARG (NULL arguments, unreadable or unwritable path, not a
- * factor file, another version, truncated or corrupt file), OOM, CUDA.
+ * factor file, another version, truncated or corrupt file, inconsistent
+ * contents), OOM, CUDA.
  */
 hif_status hif_save(hif_handle h, const char* path);
 hif_status hif_load(const char* path, hif_handle* out);

@@ -21,12 +21,16 @@ import numpy as np
 import scipy.linalg as sla
 
 
-def cpqr(M: np.ndarray, eps: float):
+def cpqr(M: np.ndarray, eps: float, trace: list | None = None):
     """Column-pivoted QR stopped at tolerance eps.
 
     Returns (k, perm, R) where perm is the column permutation (perm[:k] are the
     pivot columns) and R is the k x ncols upper-trapezoidal factor of the
     permuted matrix.
+
+    With a list `trace`, each step appends (largest remaining column norm,
+    second largest, eps |R_11|): how clearly the pivot and the stop were
+    decided (test instrumentation; the arithmetic is the same either way).
     """
     W = np.array(M, dtype=np.float64, copy=True)
     m, n = W.shape
@@ -37,6 +41,9 @@ def cpqr(M: np.ndarray, eps: float):
     for i in range(kmax):
         norms = np.sqrt(np.sum(W[i:, i:] ** 2, axis=0))
         p = int(np.argmax(norms))  # first maximum = lowest current index
+        if trace is not None:
+            second = float(np.partition(norms, -2)[-2]) if norms.size > 1 else 0.0
+            trace.append((float(norms[p]), second, eps * (norms[p] if i == 0 else r11)))
         if i == 0:
             r11 = norms[p]
             if r11 == 0.0:
@@ -60,13 +67,28 @@ def cpqr(M: np.ndarray, eps: float):
     return k, perm, np.triu(W[:k, :])
 
 
-def interpolative_decomposition(M: np.ndarray, eps: float):
+def decision_margin(trace: list) -> float:
+    """Smallest relative gap of a traced CPQR: between the chosen and the next
+    column norm at every pivot step, and between the last norms seen and the
+    stopping threshold eps |R_11|.  Inputs perturbed by less than this
+    (relative) make the same choices."""
+    marg = np.inf
+    for best, second, thr in trace:
+        if best > 0.0:
+            marg = min(marg, (best - second) / best)
+        if thr > 0.0:
+            marg = min(marg, abs(best - thr) / thr)
+    return float(marg)
+
+
+def interpolative_decomposition(M: np.ndarray, eps: float, trace: list | None = None):
     """ID of M (rows R, columns F) to relative precision eps.
 
     Returns (k, skel, redund, T): local column indices of the skeleton F^ and
     the redundant set F~ and T (k x |F~|) with M[:, redund] ~= M[:, skel] @ T.
+    `trace` as for cpqr.
     """
-    k, perm, R = cpqr(M, eps)
+    k, perm, R = cpqr(M, eps, trace)
     skel = perm[:k]
     redund = perm[k:]
     if k == 0:

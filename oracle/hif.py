@@ -77,6 +77,12 @@ class Factor:
     root: RootRecord | None = None
     ranks: list = field(default_factory=list)   # per level: (|Sigma^l| before, after)
     flops: float = 0.0                          # algorithmic flop count (Cholesky k^3/3, TRSM, GEMM 2mnk)
+    # test instrumentation, filled when hif_factor(..., record=True):
+    # active[l] = sorted DOFs of Sigma^{l+1} (active after level l); ids =
+    # every ID of the factorization as (level, kind, F, skeleton DOFs,
+    # decision margin of its CPQR, see cpqr.decision_margin)
+    active: list = field(default_factory=list)
+    ids: list = field(default_factory=list)
 
     @property
     def N(self):
@@ -165,8 +171,10 @@ def _eliminate_cells(A, groups, level, fac: Factor, check: bool, ncode: int = 0)
     return A, (np.concatenate(eliminated) if eliminated else np.zeros(0, np.int64))
 
 
-def _skeletonize(A, groups, level, want_kind, eps, fac: Factor, check: bool, ncode: int = 0):
+def _skeletonize(A, groups, level, want_kind, eps, fac: Factor, check: bool, ncode: int = 0,
+                 record: bool = False):
     """Skeletonize every group of `want_kind` independently (level-synchronous)."""
+    from .cpqr import decision_margin
     rows, cols, vals = [], [], []
     redundant = []
     for code, F in groups.items():
@@ -176,7 +184,10 @@ def _skeletonize(A, groups, level, want_kind, eps, fac: Factor, check: bool, nco
         if check:
             _check_local(A, F, np.union1d(F, R))
         A_RF = _dense(A, R, F)
-        k, skel, red, T = interpolative_decomposition(A_RF, eps)
+        trace = [] if record else None
+        k, skel, red, T = interpolative_decomposition(A_RF, eps, trace)
+        if record:
+            fac.ids.append((level, want_kind, F, F[skel], decision_margin(trace)))
         fac.flops += 2.0 * R.size * F.size * F.size
         if red.size == 0:
             continue
@@ -213,12 +224,13 @@ def _skeletonize(A, groups, level, want_kind, eps, fac: Factor, check: bool, nco
 
 
 def hif_factor(A0: sp.spmatrix, n: int, m: int, eps: float, check: bool = True,
-               periodic: bool = False) -> Factor:
+               periodic: bool = False, record: bool = False) -> Factor:
     """Factor A ~= F per §2.4 and return the sparse factors W^0..W^L.
 
     periodic=True takes the periodic geometry (every multiple of the cell side
     is a separator and the cells wrap around, see geometry.py); A0 must then be
-    the periodic operator."""
+    the periodic operator.  record=True keeps the active set after every
+    level and the decisions of every ID (Factor.active, Factor.ids)."""
     L = geo.num_levels(n, m)
     A = sp.csr_matrix(A0, dtype=np.float64, copy=True)
     fac = Factor(n=n, m=m, eps=float(eps))
@@ -233,9 +245,11 @@ def hif_factor(A0: sp.spmatrix, n: int, m: int, eps: float, check: bool = True,
         if eps > 0.0:
             for want in (geo.KIND_FACE, geo.KIND_EDGE):
                 groups = geo.group_active(np.flatnonzero(active), n, s, periodic)
-                A, red = _skeletonize(A, groups, level, want, eps, fac, check, ncode)
+                A, red = _skeletonize(A, groups, level, want, eps, fac, check, ncode, record)
                 active[red] = False
         fac.ranks.append((before, int(active.sum())))
+        if record:
+            fac.active.append(np.flatnonzero(active))
     S = np.flatnonzero(active)
     A_SS = _dense(A, S, S)
     fac.root = RootRecord(S, sla.cholesky(A_SS, lower=True))

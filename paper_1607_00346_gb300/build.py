@@ -18,7 +18,8 @@ LIB = os.path.join(BUILD, "libhif.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["dense.cu", "tc.cu", "front.cu", "idk.cu", "qr.cu", "solve.cu", "prof.cu", "hif.cu"]
+CU_SOURCES = ["dense.cu", "tc.cu", "front.cu", "idk.cu", "qr.cu", "solve.cu", "prof.cu", "peaks.cu",
+              "hif.cu"]
 CXX_SOURCES = ["symbolic.cpp"]
 
 
@@ -48,7 +49,7 @@ def build_library(verbose: bool = False, force: bool = False, ptxas_verbose: boo
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    headers.append(os.path.join(INCLUDE, "hif.h"))
+    headers += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     jobs = []
     objs = []
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]

@@ -38,6 +38,10 @@ bool prof_enabled();
 // Add algorithmic counts to a kernel's record without a launch (used when the
 // counts are only known after the launch, e.g. the ranks found by the ID).
 void prof_add(const char* name, double flops, double bytes);
+// A scope also counts the kernels launched inside it (this thread's launch
+// counter; a CUDA graph replay adds the kernels of the graph).  While a
+// ProfSuspend is alive on this thread (a stream capture), scopes record
+// nothing.
 class ProfScope {
  public:
   ProfScope(const char* name, cudaStream_t st, double flops = 0.0, double bytes = 0.0);
@@ -51,6 +55,17 @@ class ProfScope {
   cudaEvent_t a_ = nullptr, b_ = nullptr;
   std::string name_;
   double flops_ = 0.0, bytes_ = 0.0;
+  int64_t k0_ = 0;
+};
+class ProfSuspend {
+ public:
+  ProfSuspend();
+  ~ProfSuspend();
+  ProfSuspend(const ProfSuspend&) = delete;
+  ProfSuspend& operator=(const ProfSuspend&) = delete;
+
+ private:
+  bool prev_;
 };
 
 #define HIF_CHECK_LAUNCH()                 \

@@ -514,7 +514,7 @@ void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront
       if (use_tc) {
         gemm_tc(d_uo, uo.data(), (int)uo.size(), reinterpret_cast<const float*>(Karena),
                 reinterpret_cast<const float*>(Karena), reinterpret_cast<float*>(Karena), d_flags,
-                st, "chol_block_update");
+                st, "chol_block_update_tc");
       } else {
         gemm_batched<T>(d_uo, uo.data(), (int)uo.size(), Karena, Karena, Karena, st,
                         "chol_block_update");
@@ -567,8 +567,8 @@ void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront
                                  cudaMemcpyHostToDevice, st));
     if constexpr (std::is_same<T, float>::value) {
       if (use_tc && s >= 128) {
-        gemm_tc(d_ops, tops.data(), (int)cnt, Karena, Parena, d_scr, d_flags, st, "trtri_merge");
-        gemm_tc(d_ops + cnt, rops.data(), (int)cnt, Parena, d_scr, Parena, d_flags, st, "trtri_merge");
+        gemm_tc(d_ops, tops.data(), (int)cnt, Karena, Parena, d_scr, d_flags, st, "trtri_merge_tc");
+        gemm_tc(d_ops + cnt, rops.data(), (int)cnt, Parena, d_scr, Parena, d_flags, st, "trtri_merge_tc");
       } else {
         gemm_batched<T>(d_ops, tops.data(), (int)cnt, Karena, Parena, d_scr, st, "trtri_merge");
         gemm_batched<T>(d_ops + cnt, rops.data(), (int)cnt, Parena, d_scr, Parena, st, "trtri_merge");

@@ -163,6 +163,17 @@ void upload(DevBuf& b, const std::vector<U, A>& h, MemStats* ms, cudaStream_t st
                                  cudaMemcpyHostToDevice, st));
 }
 
+// Device of a device (or managed) pointer; -1 for host memory.
+int pointer_device(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return -1;
+  return at.device;
+}
+
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes at;
   cudaError_t e = cudaPointerGetAttributes(&at, p);
@@ -210,9 +221,13 @@ struct FactorBase {
   virtual void apply_in_scratch(const double* f_dev, double* u_dev, int nrhs, void* scratch,
                                 cudaStream_t st) = 0;
   int n = 0, m = 0, L = 0, precision = 0;
+  int device = -1;              // CUDA device holding every buffer of the factor
   double eps = 0;
   MemStats mem;
   DevBuf cpl, diag;             // operator for the residual
+  // active[l]: sorted grid indices of the DOFs still active after level l
+  // (Sigma^{l+1} of §2.4); active[L-1] is the root set
+  std::vector<std::vector<int32_t>> active;
   hif_stats stats{};
   hif_options opt{};
 };
@@ -230,6 +245,7 @@ struct Factor : FactorBase {
   struct SweepGraph {
     int nrhs;
     cudaGraphExec_t exec;
+    int64_t kernels;             // kernels one replay runs
   };
   std::vector<SweepGraph> graphs;
   cudaStream_t cap_st = nullptr;
@@ -248,26 +264,58 @@ struct Factor : FactorBase {
     for (auto it = stages.rbegin(); it != stages.rend(); ++it)
       run_stage(*it, false, yv, N, w, work_stride, nrhs, st);
   }
+  // Algorithmic counts of the two sweeps for nrhs right-hand sides: every
+  // stored factor entry is read once per sweep and per block of right-hand
+  // sides (blocks of 16, 8, 4, 2, 1) and used in one multiply-add per
+  // column; gathers and sets move an index and the values in and out.
+  void sweep_counts(int nrhs, double* flops, double* bytes) const {
+    int64_t ent = 0, slots = 0;
+    for (const Stage& s : stages) {
+      ent += s.entries;
+      slots += s.nidx + s.nset;
+    }
+    int blocks = 0;
+    for (int left = nrhs; left > 0;) {
+      const int R = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+      left -= R;
+      ++blocks;
+    }
+    *flops = 2.0 * 2.0 * (double)ent * nrhs;
+    *bytes = 2.0 * ((double)ent * sizeof(T) * blocks + (double)slots * (6.0 + 2.0 * sizeof(T) * nrhs));
+  }
   void sweeps_maybe_graph(T* yv, T* w, int nrhs, cudaStream_t st) {
-    if (!opt.use_graphs || prof_enabled()) {
+    if (!opt.use_graphs) {
       sweeps(yv, w, nrhs, st);
       return;
     }
-    cudaGraphExec_t exec = nullptr;
-    for (auto& g : graphs)
-      if (g.nrhs == nrhs) exec = g.exec;
-    if (!exec) {
+    const SweepGraph* g = nullptr;
+    for (auto& x : graphs)
+      if (x.nrhs == nrhs) g = &x;
+    if (!g) {
       if (!cap_st) HIF_CUDA_TRY(cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking));
       cudaGraph_t graph = nullptr;
-      HIF_CUDA_TRY(cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal));
-      sweeps(yv, w, nrhs, cap_st);
-      HIF_CUDA_TRY(cudaStreamEndCapture(cap_st, &graph));
+      cudaGraphExec_t exec = nullptr;
+      const int64_t l0 = launch_counter();
+      {
+        // the kernel profile times the replay as a whole, not the captured launches
+        ProfSuspend quiet;
+        HIF_CUDA_TRY(cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal));
+        sweeps(yv, w, nrhs, cap_st);
+        HIF_CUDA_TRY(cudaStreamEndCapture(cap_st, &graph));
+      }
+      const int64_t nk = launch_counter() - l0;
+      launch_counter() = l0;   // counted again at every replay
       const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
       cudaGraphDestroy(graph);
       HIF_CUDA_TRY(e);
-      graphs.push_back(SweepGraph{nrhs, exec});
+      graphs.push_back(SweepGraph{nrhs, exec, nk});
+      g = &graphs.back();
     }
-    HIF_CUDA_TRY(cudaGraphLaunch(exec, st));
+    double fl = 0.0, by = 0.0;
+    if (prof_enabled()) sweep_counts(nrhs, &fl, &by);
+    ProfScope ps("apply_sweeps_graph", st, fl, by);
+    HIF_CUDA_TRY(cudaGraphLaunch(g->exec, st));
+    launch_counter() += g->kernels;
   }
 
   void run_stage(Stage& s, bool fwd, T* yv, int64_t ys, T* w, int64_t vs, int nrhs,
@@ -563,6 +611,7 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
     for (int32_t g : cp.active)
       if (alive[g]) next.push_back(g);
     F_.stats.active_after[level] = (int64_t)next.size();
+    F_.active.push_back(next);
     sym_.set_active(std::move(next));
     prevp = std::move(cpp);
     prevK = std::move(Kar);
@@ -822,21 +871,18 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
   fsc.release();
   Rbuf.release();
   if (prof_enabled()) {
-    // pivoted QR: each of the k steps spends 4 flops per entry of the
-    // trailing (idm - i) x (nF - i - 1) block; the cluster kernel reads and
-    // writes that block in HBM once per step, the shared-memory kernel reads
-    // the matrix once and writes the pivots and T
+    // algorithmic counts of the ID (§2.3): Householder pivoted QR, 4 flops
+    // per entry of the trailing (idm - i) x (nF - i - 1) block at each of
+    // the k steps, then T = R11^{-1} R12 (k^2 (nF - k) flops); bytes: the
+    // matrix read once, T and the pivots written once
     double fl[2] = {0.0, 0.0}, by[2] = {0.0, 0.0};
     for (int f = 0; f < nf; ++f) {
       const int sm = id_in_shared_memory(sd[f].idm, sd[f].nF, (int)sizeof(T)) ? 1 : 0;
-      for (int i = 0; i < sd[f].k; ++i) {
-        const double e = (double)(sd[f].idm - i) * (sd[f].nF - i - 1);
-        fl[sm] += 4.0 * e;
-        if (!sm) by[sm] += 2.0 * sizeof(T) * e;
-      }
-      if (sm)
-        by[sm] += sizeof(T) * ((double)sd[f].idm * sd[f].nF +
-                               (double)sd[f].k * (sd[f].nF - sd[f].k)) + 4.0 * sd[f].nF;
+      const double k = sd[f].k, nF = sd[f].nF;
+      for (int i = 0; i < sd[f].k; ++i)
+        fl[sm] += 4.0 * (double)(sd[f].idm - i) * (sd[f].nF - i - 1);
+      fl[sm] += k * k * (nF - k);
+      by[sm] += sizeof(T) * ((double)sd[f].idm * nF + k * (nF - k)) + 4.0 * nF;
     }
     prof_add("id_cpqr", fl[0], by[0]);
     prof_add("id_cpqr_smem", fl[1], by[1]);
@@ -1154,7 +1200,7 @@ namespace {
 // is read only by the build that wrote it), the scalars of the factor, the
 // operator, then every stage: its scalars, its device arrays (byte count +
 // bytes) and its mat-vec lists (count + descriptors).
-constexpr uint32_t kFileVersion = 1;
+constexpr uint32_t kFileVersion = 2;
 
 struct FileOut {
   std::FILE* f = nullptr;
@@ -1197,12 +1243,16 @@ struct FileIn {
     raw(&v, sizeof(U));
     return v;
   }
-  void buf(DevBuf& b, MemStats* ms) {
+  // a device array; with `keep`, its bytes also stay on the host (for the
+  // consistency checks of load_factor)
+  void buf(DevBuf& b, MemStats* ms, std::vector<unsigned char>* keep = nullptr) {
     const uint64_t n = get<uint64_t>();
     if (n > (uint64_t(1) << 40)) throw Error{HIF_ERR_INVALID_ARG, "corrupt factor file"};
     b.alloc(n, ms);
+    std::vector<unsigned char> local;
+    std::vector<unsigned char>& h = keep ? *keep : local;
+    h.assign(n, 0);
     if (!n) return;
-    std::vector<unsigned char> h(n);
     raw(h.data(), n);
     HIF_CUDA_TRY(cudaMemcpy(b.as<void>(), h.data(), n, cudaMemcpyHostToDevice));
   }
@@ -1254,6 +1304,77 @@ void save_factor(const Factor<T>& F, FileOut& o) {
     o.put((uint32_t)s.bwd.size());
     for (const auto& gl : s.bwd) o.list(gl);
   }
+  o.put((uint64_t)F.active.size());
+  for (const auto& a : F.active) {
+    o.put((uint64_t)a.size());
+    o.raw(a.data(), sizeof(int32_t) * a.size());
+  }
+}
+
+[[noreturn]] void corrupt(const char* what) {
+  throw Error{HIF_ERR_INVALID_ARG, std::string("corrupt factor file: ") + what};
+}
+
+// The host bytes of an int array read from a factor file, as values.
+template <typename I>
+std::vector<I> as_values(const std::vector<unsigned char>& b, int64_t count, const char* what) {
+  if ((int64_t)b.size() != count * (int64_t)sizeof(I)) corrupt(what);
+  std::vector<I> v((size_t)count);
+  if (count) std::memcpy(v.data(), b.data(), b.size());
+  return v;
+}
+
+// Every index and mat-vec extent of a loaded stage must stay inside the
+// arrays the apply sweeps give it: the gather list and set / accumulate
+// targets inside the grid (N), their work positions inside the stage's two
+// work vectors (2 nidx), and every matrix inside its arena.
+template <typename T>
+void check_stage(const Stage& s, int64_t N, const std::vector<unsigned char>& idx_b,
+                 const std::vector<unsigned char>& setg_b, const std::vector<unsigned char>& setp_b,
+                 const std::vector<unsigned char>& tgt_b, const std::vector<unsigned char>& ptr_b,
+                 const std::vector<unsigned char>& src_b) {
+  if (s.nidx < 0 || s.nidx > (int64_t(1) << 30) || s.nset < 0 || s.nacc < 0)
+    corrupt("stage counts");
+  const int64_t W = 2 * s.nidx;   // work entries of the stage, per right-hand side
+  for (int32_t g : as_values<int32_t>(idx_b, s.nidx, "gather list"))
+    if (g < 0 || g >= N) corrupt("gather index");
+  const auto sg = as_values<int32_t>(setg_b, s.nset, "set list");
+  const auto sp = as_values<int32_t>(setp_b, s.nset, "set positions");
+  for (int64_t i = 0; i < s.nset; ++i)
+    if (sg[i] < 0 || sg[i] >= N || sp[i] < 0 || sp[i] >= W) corrupt("set entry");
+  if (s.nacc) {
+    const auto tg = as_values<int32_t>(tgt_b, s.nacc, "accumulate targets");
+    const auto pt = as_values<int64_t>(ptr_b, s.nacc + 1, "accumulate pointers");
+    const int64_t nsrc = (int64_t)(src_b.size() / sizeof(int32_t));
+    const auto sr = as_values<int32_t>(src_b, nsrc, "accumulate sources");
+    if (pt[0] != 0 || pt[s.nacc] != nsrc) corrupt("accumulate pointers");
+    for (int64_t t = 0; t < s.nacc; ++t) {
+      if (tg[t] < 0 || tg[t] >= N || pt[t + 1] < pt[t]) corrupt("accumulate entry");
+    }
+    for (int32_t q : sr)
+      if (q < 0 || q >= W) corrupt("accumulate source");
+  } else if (!tgt_b.empty() || !ptr_b.empty() || !src_b.empty()) {
+    corrupt("accumulate lists");
+  }
+  const int64_t npan = (int64_t)(s.panels.bytes() / sizeof(T));
+  const int64_t ntm = (int64_t)(s.tmats.bytes() / sizeof(T));
+  auto lists_ok = [&](const std::vector<GemvList>& lists) {
+    for (const GemvList& gl : lists) {
+      if ((gl.trans != 0 && gl.trans != 1) || (gl.mat != 0 && gl.mat != 1)) corrupt("mat-vec list");
+      const int64_t arena = gl.mat ? ntm : npan;
+      for (const GemvOp& o : gl.h) {
+        if (o.rows < 0 || o.cols < 0 || o.ld < std::max(1, o.rows) || o.M < 0 || o.x < 0 ||
+            o.y < 0 || (o.tri != 0 && o.tri != 1) || (o.beta_one != 0 && o.beta_one != 1))
+          corrupt("mat-vec shape");
+        if (o.rows && o.cols && o.M + (int64_t)(o.cols - 1) * o.ld + o.rows > arena)
+          corrupt("mat-vec matrix extent");
+        const int64_t xin = gl.trans ? o.rows : o.cols, yout = gl.trans ? o.cols : o.rows;
+        if (o.x + xin > W || o.y + yout > W) corrupt("mat-vec vector extent");
+      }
+    }
+  };
+  lists_ok(s.fwd);
+  lists_ok(s.bwd);
 }
 
 template <typename T>
@@ -1265,14 +1386,17 @@ void load_factor(Factor<T>& F, FileIn& in) {
   F.eps = in.get<double>();
   F.opt = in.get<hif_options>();
   F.stats = in.get<hif_stats>();
-  F.work_stride = in.get<int64_t>();
-  if (F.n < 1 || F.n > 1024 || F.L < 0 || F.L > 16)
-    throw Error{HIF_ERR_INVALID_ARG, "corrupt factor file"};
+  const int64_t stride_in_file = in.get<int64_t>();
+  if (F.n < 1 || F.n > 1024 || F.L < 0 || F.L > 16) corrupt("grid");
+  const int64_t N = (int64_t)F.n * F.n * F.n;
   in.buf(F.cpl, &F.mem);
   in.buf(F.diag, &F.mem);
+  if (F.cpl.bytes() != sizeof(double) * 3 * N || F.diag.bytes() != sizeof(double) * N)
+    corrupt("operator size");
   const uint64_t ns = in.get<uint64_t>();
-  if (ns > 4096) throw Error{HIF_ERR_INVALID_ARG, "corrupt factor file"};
+  if (ns > 4096) corrupt("stage count");
   F.stages.resize(ns);
+  F.work_stride = 0;
   for (Stage& s : F.stages) {
     s.kind = in.get<int>();
     s.level = in.get<int>();
@@ -1280,22 +1404,38 @@ void load_factor(Factor<T>& F, FileIn& in) {
     s.nset = in.get<int64_t>();
     s.nacc = in.get<int64_t>();
     s.entries = in.get<int64_t>();
-    in.buf(s.idx, &F.mem);
+    std::vector<unsigned char> idx_b, setg_b, setp_b, tgt_b, ptr_b, src_b;
+    in.buf(s.idx, &F.mem, &idx_b);
     in.buf(s.panels, &F.mem);
     in.buf(s.tmats, &F.mem);
-    in.buf(s.set_g, &F.mem);
-    in.buf(s.set_p, &F.mem);
-    in.buf(s.acc_tgt, &F.mem);
-    in.buf(s.acc_ptr, &F.mem);
-    in.buf(s.acc_src, &F.mem);
+    in.buf(s.set_g, &F.mem, &setg_b);
+    in.buf(s.set_p, &F.mem, &setp_b);
+    in.buf(s.acc_tgt, &F.mem, &tgt_b);
+    in.buf(s.acc_ptr, &F.mem, &ptr_b);
+    in.buf(s.acc_src, &F.mem, &src_b);
     const uint32_t nf = in.get<uint32_t>();
-    if (nf > 8) throw Error{HIF_ERR_INVALID_ARG, "corrupt factor file"};
+    if (nf > 8) corrupt("mat-vec list count");
     s.fwd.resize(nf);
     for (auto& gl : s.fwd) in.list(gl, &F.mem);
     const uint32_t nb = in.get<uint32_t>();
-    if (nb > 8) throw Error{HIF_ERR_INVALID_ARG, "corrupt factor file"};
+    if (nb > 8) corrupt("mat-vec list count");
     s.bwd.resize(nb);
     for (auto& gl : s.bwd) in.list(gl, &F.mem);
+    check_stage<T>(s, N, idx_b, setg_b, setp_b, tgt_b, ptr_b, src_b);
+    // the sweeps' work stride follows from the stages, as in hif_factor
+    F.work_stride = std::max(F.work_stride, 2 * s.nidx);
+  }
+  if (F.work_stride != stride_in_file) corrupt("work stride");
+  const uint64_t na = in.get<uint64_t>();
+  if (na > 16) corrupt("active set count");
+  F.active.resize(na);
+  for (auto& a : F.active) {
+    const uint64_t c = in.get<uint64_t>();
+    if (c > (uint64_t)N) corrupt("active set size");
+    a.resize(c);
+    in.raw(a.data(), sizeof(int32_t) * c);
+    for (size_t i = 0; i < a.size(); ++i)
+      if (a[i] < 0 || a[i] >= N || (i && a[i] <= a[i - 1])) corrupt("active set");
   }
   F.stats.factor_bytes = F.mem.cur;
 }
@@ -1345,7 +1485,10 @@ hif_status hif_factor(const hif_grid* grid, const double* a, const double* b, do
   ain.set(a, N, st);
   bin.set(b, N, st);
   auto h = std::make_unique<hif_handle_s>();
+  int dev = 0;
+  HIF_CUDA_TRY(cudaGetDevice(&dev));
   auto build = [&](auto* F) {
+    F->device = dev;
     F->n = n;
     F->m = m;
     F->L = L;
@@ -1408,6 +1551,16 @@ hif_status hif_apply_noalloc(hif_handle h, const double* f, double* u, int nrhs,
     throw Error{HIF_ERR_INVALID_ARG, "hif_apply_noalloc cannot run while kernel profiling is on"};
   if (!hif::is_device_ptr(f) || !hif::is_device_ptr(u))
     throw Error{HIF_ERR_INVALID_ARG, "hif_apply_noalloc needs f and u in device memory"};
+  {
+    // the work array used is the current device's copy: the factor, f and u
+    // must all live on that device
+    int cur = -1;
+    HIF_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != h->f->device || hif::pointer_device(f) != cur || hif::pointer_device(u) != cur)
+      throw Error{HIF_ERR_INVALID_ARG,
+                  "hif_apply_noalloc: the factor (device " + std::to_string(h->f->device) +
+                      "), f and u must be on the current device (" + std::to_string(cur) + ")"};
+  }
   const size_t need = h->f->sweep_scratch_bytes(nrhs);
   if (need > kNoAllocScratchBytes)
     throw Error{HIF_ERR_INVALID_ARG,
@@ -1466,6 +1619,23 @@ hif_status hif_query_stats(hif_handle h, hif_stats* st) {
   return HIF_OK;
 }
 
+hif_status hif_query_active(hif_handle h, int level, int32_t* out, int64_t cap,
+                            int64_t* count) {
+  HIF_API_BEGIN
+  if (!h || !count) throw Error{HIF_ERR_INVALID_ARG, "NULL handle or count"};
+  const auto& act = h->f->active;
+  if (level < 0 || level >= (int)act.size())
+    throw Error{HIF_ERR_INVALID_ARG, "level must be in [0, L)"};
+  const auto& a = act[(size_t)level];
+  *count = (int64_t)a.size();
+  if (out) {
+    if (cap < (int64_t)a.size()) throw Error{HIF_ERR_INVALID_ARG, "out holds fewer than count entries"};
+    std::memcpy(out, a.data(), sizeof(int32_t) * a.size());
+  }
+  return HIF_OK;
+  HIF_API_END
+}
+
 size_t hif_predict_bytes(const hif_grid* grid, const hif_options* opt) {
   if (!grid || hif::hif_num_levels(grid->n, grid->m) < 0) return 0;
   const double N = (double)grid->n * grid->n * grid->n;
@@ -1516,6 +1686,8 @@ hif_status hif_load(const char* path, hif_handle* out) {
       in.get<uint32_t>() != sizeof(hif_stats))
     throw Error{HIF_ERR_INVALID_ARG, "factor file written by another version"};
   auto hh = std::make_unique<hif_handle_s>();
+  int dev = 0;
+  HIF_CUDA_TRY(cudaGetDevice(&dev));
   // the precision decides the factor's word size: peek at it after n, m, L
   const long pos = std::ftell(in.f);
   in.get<int>();
@@ -1526,10 +1698,12 @@ hif_status hif_load(const char* path, hif_handle* out) {
   if (prec == HIF_PREC_FP32) {
     auto* F = new hif::Factor<float>();
     hh->f.reset(F);
+    F->device = dev;
     hif::load_factor(*F, in);
   } else if (prec == HIF_PREC_FP64) {
     auto* F = new hif::Factor<double>();
     hh->f.reset(F);
+    F->device = dev;
     hif::load_factor(*F, in);
   } else {
     throw Error{HIF_ERR_INVALID_ARG, "corrupt factor file"};

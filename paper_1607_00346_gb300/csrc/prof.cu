@@ -19,12 +19,15 @@ struct Pending {
   std::string name;
   cudaEvent_t a, b;
   double flops, bytes;
+  int64_t kernels;
 };
 
 struct Agg {
-  int64_t launches = 0;
+  int64_t launches = 0, kernels = 0;
   double seconds = 0, flops = 0, bytes = 0;
 };
+
+thread_local bool t_suspended = false;
 
 struct ProfState {
   std::mutex mu;
@@ -57,6 +60,7 @@ void drain(ProfState& s) {
     HIF_CUDA_TRY(cudaEventElapsedTime(&ms, p.a, p.b));
     Agg& g = s.agg[p.name];
     g.launches++;
+    g.kernels += p.kernels;
     g.seconds += ms * 1e-3;
     g.flops += p.flops;
     g.bytes += p.bytes;
@@ -72,23 +76,27 @@ bool prof_enabled() { return state().on; }
 
 void prof_add(const char* name, double flops, double bytes) {
   ProfState& s = state();
-  if (!s.on) return;
+  if (!s.on || t_suspended) return;
   std::lock_guard<std::mutex> lk(s.mu);
   Agg& g = s.agg[name];
   g.flops += flops;
   g.bytes += bytes;
 }
 
+ProfSuspend::ProfSuspend() : prev_(t_suspended) { t_suspended = true; }
+ProfSuspend::~ProfSuspend() { t_suspended = prev_; }
+
 ProfScope::ProfScope(const char* name, cudaStream_t st, double flops, double bytes)
     : st_(st), active_(false) {
   ProfState& s = state();
-  if (!s.on) return;
+  if (!s.on || t_suspended) return;
   std::lock_guard<std::mutex> lk(s.mu);
   a_ = get_event(s);
   b_ = get_event(s);
   name_ = name;
   flops_ = flops;
   bytes_ = bytes;
+  k0_ = launch_counter();
   HIF_CUDA_TRY(cudaEventRecord(a_, st_));
   active_ = true;
 }
@@ -98,7 +106,7 @@ ProfScope::~ProfScope() {
   ProfState& s = state();
   std::lock_guard<std::mutex> lk(s.mu);
   cudaEventRecord(b_, st_);
-  s.pending.push_back(Pending{name_, a_, b_, flops_, bytes_});
+  s.pending.push_back(Pending{name_, a_, b_, flops_, bytes_, launch_counter() - k0_});
   if (s.pending.size() > 4096) {
     try {
       drain(s);
@@ -138,6 +146,7 @@ hif_status hif_profile_end(hif_kernel_profile* out, int cap, int* count) {
         std::memset(&o, 0, sizeof(o));
         std::strncpy(o.name, kv.first.c_str(), sizeof(o.name) - 1);
         o.launches = kv.second.launches;
+        o.kernels = kv.second.kernels;
         o.seconds = kv.second.seconds;
         o.flops = kv.second.flops;
         o.bytes = kv.second.bytes;

@@ -15,7 +15,9 @@
 //   * one thread issues tcgen05.mma.cta_group::1.kind::tf32 (M = 128, N = TN,
 //     K = 8 per instruction) into a TN-column TMEM accumulator and commits
 //     to the buffer's mbarrier; the wait on it has an iteration limit (on
-//     expiry the kernel records FLAG_TIMEOUT, frees its TMEM and returns);
+//     expiry the CTA agrees on the failure with a block-wide vote, waits
+//     once more, again bounded, for its commits still in flight, records
+//     FLAG_TIMEOUT, frees its TMEM and returns without reading it);
 //   * with KC = 16 a 128 x 128 CTA holds 64 KB of shared memory and three
 //     share an SM (384 of its 512 TMEM columns); a 128 x 256 CTA holds 96 KB
 //     and two share an SM (all 512 columns), so one CTA's loads overlap the
@@ -31,6 +33,7 @@
 
 #include "common.cuh"
 #include "dense.cuh"
+#include "tcgen05.cuh"
 
 namespace hif {
 
@@ -39,25 +42,10 @@ namespace {
 constexpr int TC_M = 128;        // tile rows (TMEM lanes)
 constexpr long long WAIT_LIMIT = 20000000;     // mbarrier polls before giving up
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// shared memory matrix descriptor: no swizzle, K-major core matrices
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
-  d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
-  d |= (uint64_t)1 << 46;          // descriptor version of this architecture
-  return d;                        // base offset 0, swizzle mode 0 (none)
-}
-
-// instruction descriptor: D = F32, A = B = TF32, both K-major, M x N
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
+using tc5::idesc_tf32;
+using tc5::mma_tf32;
+using tc5::sdesc;
+using tc5::smem_u32;
 
 __device__ __forceinline__ float tf32_hi(float x) {
   uint32_t r;
@@ -69,14 +57,6 @@ __device__ __forceinline__ float tf32_hi(float x) {
 template <int KC>
 __device__ __forceinline__ int core_off(int row, int k) {
   return ((row >> 3) * (KC / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4;
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 // C (M x N) = beta C + alpha op(A) op(B) for a batch of problems (GemmOp
@@ -131,9 +111,13 @@ __global__ void __launch_bounds__(TC_M + TN, KC == 16 ? (TN == 128 ? 3 : 2) : 1)
   const int cbeg = (int)(((int64_t)nch_all * blockIdx.z) / gridDim.z);
   const int nchunk = (int)(((int64_t)nch_all * (blockIdx.z + 1)) / gridDim.z) - cbeg;
   uint32_t phase[2] = {0u, 0u};
+  // outstanding[s]: products committed on buffer s whose completion this
+  // thread has not yet seen (at most one commit per buffer is in flight)
+  bool outstanding[2] = {false, false};
   bool ok = true;
 
-  // bounded wait for the products issued on buffer s
+  // bounded wait for the products issued on buffer s; the phase advances
+  // only when the commit has arrived, so an expired wait can be retried
   auto wait_buf = [&](int s) {
     long long it = 0;
     uint32_t done = 0;
@@ -145,7 +129,10 @@ __global__ void __launch_bounds__(TC_M + TN, KC == 16 ? (TN == 128 ? 3 : 2) : 1)
           : "r"(smem_u32(&mbar[s])), "r"(phase[s]));
       if (++it > WAIT_LIMIT) break;
     }
-    phase[s] ^= 1u;
+    if (done) {
+      phase[s] ^= 1u;
+      outstanding[s] = false;
+    }
     return done != 0;
   };
 
@@ -213,6 +200,7 @@ __global__ void __launch_bounds__(TC_M + TN, KC == 16 ? (TN == 128 ? 3 : 2) : 1)
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
               smem_u32(&mbar[s])));
     }
+    outstanding[s] = true;
     return true;
   };
   float va[KC], vb[KC];
@@ -226,6 +214,15 @@ __global__ void __launch_bounds__(TC_M + TN, KC == 16 ? (TN == 128 ? 3 : 2) : 1)
   if (ok) {
     for (int ch = max(0, nchunk - 2); ch < nchunk; ++ch)
       if (!wait_buf(ch & 1)) ok = false;
+  }
+  // one verdict for the whole CTA: the epilogue's tcgen05.ld is warp-collective
+  ok = __syncthreads_and(ok) != 0;
+  if (!ok) {
+    // drain: wait once more (bounded) for every commit this thread has not
+    // seen complete, so that no product is still writing the accumulator
+    // when it is freed below; a commit that never arrives is left behind
+    for (int s = 0; s < 2; ++s)
+      if (outstanding[s]) wait_buf(s);
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n");

@@ -59,13 +59,21 @@ _lib = None
 EXPORTS = ["hif_default_options", "hif_factor", "hif_apply", "hif_apply_noalloc",
            "hif_residual", "hif_solve",
            "hif_query_stats", "hif_predict_bytes", "hif_profile_begin", "hif_profile_end",
-           "hif_destroy", "hif_last_error", "hif_version", "hif_save", "hif_load"]
+           "hif_destroy", "hif_last_error", "hif_version", "hif_save", "hif_load",
+           "hif_measure_peaks", "hif_query_active"]
+
+
+class Peaks(ctypes.Structure):
+    _fields_ = [("sm_count", ctypes.c_int), ("sm_clock_khz", ctypes.c_int),
+                ("fp32_fma_tflops", ctypes.c_double), ("fp64_fma_tflops", ctypes.c_double),
+                ("tf32_mma_tflops", ctypes.c_double), ("bf16_mma_tflops", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
 
 
 class KernelProfile(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
-                ("seconds", ctypes.c_double), ("flops", ctypes.c_double),
-                ("bytes", ctypes.c_double)]
+                ("kernels", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 def library_path() -> str:
@@ -114,6 +122,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.hif_last_error.restype = ctypes.c_char_p
     lib.hif_version.argtypes = []
     lib.hif_version.restype = ctypes.c_char_p
+    lib.hif_query_active.argtypes = [vp, i, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
+                                     ctypes.POINTER(ctypes.c_int64)]
+    lib.hif_query_active.restype = i
+    lib.hif_measure_peaks.argtypes = [ctypes.POINTER(Peaks), vp]
+    lib.hif_measure_peaks.restype = i
     _lib = lib
     return lib
 
@@ -172,8 +185,16 @@ def profile_end() -> list:
     arr = (KernelProfile * cap)()
     cnt = ctypes.c_int()
     _check(load().hif_profile_end(arr, cap, ctypes.byref(cnt)))
-    return [dict(name=arr[i].name.decode(), launches=arr[i].launches, seconds=arr[i].seconds,
-                 flops=arr[i].flops, bytes=arr[i].bytes) for i in range(min(cnt.value, cap))]
+    return [dict(name=arr[i].name.decode(), launches=arr[i].launches, kernels=arr[i].kernels,
+                 seconds=arr[i].seconds, flops=arr[i].flops, bytes=arr[i].bytes)
+            for i in range(min(cnt.value, cap))]
+
+
+def measure_peaks(stream=None) -> dict:
+    """hif_measure_peaks: measured FP32/FP64 FMA and TF32/BF16 tensor-core rates."""
+    p = Peaks()
+    _check(load().hif_measure_peaks(ctypes.byref(p), _stream(stream)))
+    return {k: getattr(p, k) for k, _ in Peaks._fields_}
 
 
 def predict_bytes(n: int, m: int, **opts) -> int:
@@ -253,6 +274,16 @@ class Handle:
         if check:
             _check(st)
         return list(its), list(rel)
+
+    def active(self, level: int) -> np.ndarray:
+        """hif_query_active: sorted grid indices active after `level`."""
+        cnt = ctypes.c_int64()
+        _check(load().hif_query_active(self._h, level, None, 0, ctypes.byref(cnt)))
+        out = np.empty(cnt.value, dtype=np.int32)
+        _check(load().hif_query_active(self._h, level,
+                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       cnt.value, ctypes.byref(cnt)))
+        return out
 
     def stats(self) -> dict:
         s = Stats()

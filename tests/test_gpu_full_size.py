@@ -16,9 +16,15 @@ GPU results against the oracle's operator instead of its factor:
     dropped, so each product is some 4-8x less accurate than an FP32 FMA
     product; at 64^3 and 128^3 the measured ratio of solve errors is 7-11.
     A lost lo term (plain TF32, 11 bits) raises e_s past 1e-3.
+  * the PCG solution of the benchmark problem against the solution of the
+    discrete problem computed by the oracle alone (Jacobi-preconditioned
+    CG to 1e-14, tests/golden/contrast128_solution.txt, written by the
+    committed script beside it): within 1e-8 relative at 1024 seeded sample
+    points (against ||u||_inf), in 2-norm, and in four seeded projections.
 Inputs are the benchmark's own seeded arrays (128^3: a = 10^U(-1,1),
 b = 0.1, eps = 1e-6, FP32 factor).
 """
+import os
 import numpy as np
 import pytest
 
@@ -80,8 +86,57 @@ def test_contrast128_fp32_bench_configuration(H):
     assert max(cpu_rel) <= 1e-10 + 1e-12
     x = inputs.normal_rhs(n, 1, seed + 7)[0]
     es = _solve_error(h, A, x)
-    assert es < 1e-3, es
+    assert es < 5e-4, es          # 2.3e-4 measured
     h.close()
+
+
+def _golden_solution():
+    path = os.path.join(os.path.dirname(__file__), "golden", "contrast128_solution.txt")
+    meta, dots, samples = {}, {}, []
+    with open(path) as fh:
+        lines = [l for l in fh if not l.startswith("#")]
+    i = 0
+    while not lines[i].startswith("samples"):
+        k, *v = lines[i].split()
+        if k == "dot":
+            dots[int(v[0])] = float(v[1])
+        else:
+            meta[k] = float(v[0])
+        i += 1
+    for l in lines[i + 1:]:
+        j, v = l.split()
+        samples.append((int(j), float(v)))
+    return meta, dots, samples
+
+
+def test_contrast128_solution_matches_the_oracle_solution(H):
+    # the benchmark's factor + PCG (FP32 factor, FP64 residual, 1e-10) against
+    # the oracle's solution of A u = f, no HIF on that side
+    meta, dots, samples = _golden_solution()
+    w = inputs.workload("contrast128")
+    n = w["n"]
+    assert int(meta["n"]) == n and meta["b"] == w["b"] and meta["relres"] <= 1e-14
+    a = inputs.coeff_log_uniform(n, -1.0, 1.0, int(meta["seed_a"]))
+    f = inputs.normal_rhs(n, 1, int(meta["seed_f"]))
+    h = H.factor(n, 4, _dev(a), b_const=w["b"], eps=w["eps"], precision=H.PREC_FP32)
+    fd = _dev(f)
+    ud = torch.zeros_like(fd)
+    its, rel = h.solve(fd, ud)
+    torch.cuda.synchronize()
+    u = ud.cpu().numpy()[0]
+    h.close()
+    assert rel[0] <= 1e-10
+    idx = np.array([j for j, _ in samples])
+    ref = np.array([v for _, v in samples])
+    err_pts = float(np.abs(u[idx] - ref).max() / meta["norminf"])
+    err_2 = abs(float(np.linalg.norm(u)) - meta["norm2"]) / meta["norm2"]
+    err_dot = max(abs(float(u @ inputs.normal_rhs(n, 1, k)[0]) - v) for k, v in dots.items())
+    print(f"\n[contrast128 solution] PCG {its[0]} its, relres {rel[0]:.2e}: sampled "
+          f"{err_pts:.2e}, norm {err_2:.2e}, projections {err_dot / meta['norm2']:.2e}")
+    assert err_pts <= 1e-8, err_pts
+    assert err_2 <= 1e-8, err_2
+    # a projection on an N(0,1) vector g moves by about ||u - u_ref||_2
+    assert err_dot <= 4e-8 * meta["norm2"], err_dot
 
 
 @pytest.mark.parametrize("n", [64, 128])

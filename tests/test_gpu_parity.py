@@ -259,3 +259,51 @@ def test_saved_and_loaded_factor_is_bitwise_the_same(H, tmp_path, precision):
     its2, _ = h2.solve(_dev(f), u2)
     torch.cuda.synchronize()
     assert its1 == its2 and torch.equal(u1, u2)
+
+
+def test_load_rejects_inconsistent_factor_files(H, tmp_path):
+    # a file whose sizes are all valid but whose contents disagree with each
+    # other (a stale work stride, a gather index outside the grid) is refused
+    # before any kernel could read out of bounds
+    import ctypes
+    n = 8
+    h = H.factor(n, 4, _dev(_coeff(n, 990)), eps=1e-6, precision=1)
+    path = tmp_path / "f.hiff"
+    h.save(str(path))
+    raw = bytearray(path.read_bytes())
+    head = 4 + 3 * 4                                   # magic, version, two struct sizes
+    scalars = 4 * 4 + 8                                # n, m, L, precision, eps
+    ws_off = head + scalars + ctypes.sizeof(H.Options) + ctypes.sizeof(H.Stats)
+    N = n ** 3
+    stale = bytearray(raw)
+    ws = int.from_bytes(stale[ws_off:ws_off + 8], "little")
+    stale[ws_off:ws_off + 8] = (ws + 2).to_bytes(8, "little")
+    (tmp_path / "stale.hiff").write_bytes(stale)
+    with pytest.raises(H.HifError) as e:
+        H.load_factor(str(tmp_path / "stale.hiff"))
+    assert e.value.status == 1 and "work stride" in str(e.value)
+    # first stage's gather list: after the operator arrays (byte count + data
+    # each), the stage count and the stage's six scalars, and its byte count
+    idx_off = ws_off + 8 + (8 + 24 * N) + (8 + 8 * N) + 8 + (4 + 4 + 4 * 8) + 8
+    bad = bytearray(raw)
+    bad[idx_off:idx_off + 4] = (N + 5).to_bytes(4, "little")
+    (tmp_path / "bad_index.hiff").write_bytes(bad)
+    with pytest.raises(H.HifError) as e:
+        H.load_factor(str(tmp_path / "bad_index.hiff"))
+    assert e.value.status == 1 and "gather index" in str(e.value)
+    # the untouched file still loads and applies exactly as the original
+    h2 = H.load_factor(str(path))
+    f = inputs.normal_rhs(n, 1, 991)
+    assert np.array_equal(_gpu_apply(h, f), _gpu_apply(h2, f))
+
+
+def test_measured_peaks_are_plausible(H):
+    # hif_measure_peaks times FMA and tensor-core loops on this GPU; the
+    # roofline denominators of the benchmark come from it
+    p = H.measure_peaks()
+    assert p["sm_count"] > 0 and p["sm_clock_khz"] > 0
+    assert p["fp32_fma_tflops"] > 5 * p["fp64_fma_tflops"] > 0
+    assert p["tf32_mma_tflops"] > 2 * p["fp32_fma_tflops"]
+    assert p["bf16_mma_tflops"] > 1.5 * p["tf32_mma_tflops"]
+    # FMA: at most 128 lanes x 2 flops x clock per SM
+    assert p["fp32_fma_tflops"] <= 1.05 * p["sm_count"] * 256 * p["sm_clock_khz"] * 1e3 / 1e12

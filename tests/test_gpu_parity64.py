@@ -1,0 +1,148 @@
+"""GPU vs oracle, element by element, at 64^3: the size where every kernel
+path of the 128^3 benchmark runs (the cluster pivoted QR of the level-2/3
+faces, the row reduction before their ID, the shared-memory ID of the small
+fronts, both tensor-core tile shapes of the Schur products).
+
+Workload contrast64: n = 64, m = 4, a = 10^U(-1,1) iid per grid point
+(seed 20260102), b = 0.  The oracle factors it once per eps (1e-4, 1e-6) in
+two spawned processes; every GPU configuration is compared with it on the
+same seeded inputs:
+
+  * solve error e_s = ||x - F^{-1} A x|| / ||x|| (§4, Table 2): FP64 within
+    2x the oracle's; FP32 (rounding-dominated at eps = 1e-6) below 1e-3;
+  * F_gpu^{-1} b against F_oracle^{-1} b element by element (b = A x): both
+    approximate x with relative error e_s, so their difference is at most
+    e_s(gpu) + e_s(oracle) in 2-norm whatever the skeletons; the check is
+    that it is much smaller, ||d||_inf <= C e_s(oracle) ||y||_inf with
+    C = DIFF_C[precision], i.e. the two factors make the same approximation;
+  * the number of DOFs active after every level (the ranks of the level's
+    IDs, Sigma^{l+1} of §2.4) within RANK_BAND[precision] of the oracle's;
+  * identical skeleton sets at level 0 (identical inputs on both sides) for
+    every face and edge whose CPQR decisions are clear by more than the
+    rounding of the precision (oracle decision margin > MARGIN[precision]),
+    and at higher levels for the fronts whose DOF set F is the same on both
+    sides and whose decisions are clear by more than the eps-sized
+    difference of the inputs (margin > MARGIN_UP);
+  * the PCG solution (to 1e-10) equal to the oracle's PCG solution (to
+    1e-12) to 1e-8 relative.
+"""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import _oracle_jobs
+from oracle import geometry as geo
+from oracle import stencil
+from paper_1607_00346_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DIFF_C = {0: 0.5, 1: 20.0}
+RANK_BAND = {0: 0.01, 1: 0.05}
+MARGIN = {0: 1e-8, 1: 1e-3}
+MARGIN_UP = 1e-2
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_00346_gb300 import build, hif
+    build.build_library()
+    hif.load()
+    return hif
+
+
+@pytest.fixture(scope="module")
+def oracle64():
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(2) as pool:
+        res = pool.map(_oracle_jobs.oracle_contrast64, [1e-4, 1e-6])
+    return {r["eps"]: r for r in res}
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _skeleton_agreement(n, m, L, act_g, act_o, ids):
+    """Per level: (fronts with equal F, clear ones among them, mismatches
+    among the clear ones, mismatches among all equal-F fronts)."""
+    out = []
+    for lev in range(L):
+        s = m << lev
+        before_g = np.arange(n ** 3) if lev == 0 else act_g[lev - 1]
+        groups_g = geo.group_active(before_g, n, s)
+        after_g = act_g[lev]
+        thr = MARGIN_UP if lev else None
+        eq = clear = bad_clear = bad_all = 0
+        for (l, kind, F, skel, marg) in ids:
+            if l != lev:
+                continue
+            code = tuple(int(c) for c in geo.slab_codes(F[:1], n, s)[0])
+            Fg = groups_g.get(code)
+            if Fg is None or Fg.size != F.size or not np.array_equal(Fg, F):
+                continue
+            eq += 1
+            sg = F[np.isin(F, after_g)]
+            same = np.array_equal(np.sort(sg), np.sort(skel))
+            bad_all += not same
+            if marg > (thr if thr is not None else -1.0):
+                clear += 1
+                bad_clear += not same
+        out.append((eq, clear, bad_clear, bad_all))
+    return out
+
+
+@pytest.mark.parametrize("precision,tc,eps", [(0, True, 1e-4), (0, True, 1e-6),
+                                              (1, True, 1e-6), (1, False, 1e-6)])
+def test_contrast64_elementwise_against_oracle(H, oracle64, precision, tc, eps):
+    o = oracle64[eps]
+    w = inputs.workload("contrast64")
+    n, m, seed = w["n"], w["m"], w["seed"]
+    L = 4
+    a = inputs.make_coeff(n, w["a"], seed)
+    A = stencil.assemble(a, w["b"], n)
+    h = H.factor(n, m, _dev(a), b_const=w["b"], eps=eps, precision=precision, tensor_cores=tc)
+    st = h.stats()
+    x = inputs.normal_rhs(n, 1, seed + 9)[0]
+    bd = _dev(A @ x)
+    yd = torch.empty_like(bd)
+    h.apply(bd, yd)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy()
+    es_g = float(np.linalg.norm(x - y) / np.linalg.norm(x))
+    es_o = o["es"]
+    d = y - o["y"]
+    ratio_inf = float(np.abs(d).max() / (es_o * np.abs(o["y"]).max()))
+    ratio_2 = float(np.linalg.norm(d) / (es_o * np.linalg.norm(o["y"])))
+    act_g = [h.active(l) for l in range(L)]
+    act_o = o["active"]
+    rank_dev = [abs(len(g) - len(r)) / len(r) for g, r in zip(act_g, act_o)]
+    symdiff = [np.setxor1d(g, r).size / len(r) for g, r in zip(act_g, act_o)]
+    agree = _skeleton_agreement(n, m, L, act_g, act_o, o["ids"])
+    f = inputs.normal_rhs(n, 1, seed + 1)
+    ud = torch.zeros(f.shape, dtype=torch.float64, device="cuda")
+    its, rel = h.solve(_dev(f), ud)
+    u = ud.cpu().numpy()[0]
+    uerr = float(np.linalg.norm(u - o["u"]) / np.linalg.norm(o["u"]))
+    print(f"\n[parity64] prec={precision} tc={tc} eps={eps}: e_s gpu {es_g:.3e} oracle {es_o:.3e}; "
+          f"|d|inf/(e_s|y|inf) {ratio_inf:.3e}, |d|2/(e_s|y|2) {ratio_2:.3e}; "
+          f"rank dev {['%.2e' % r for r in rank_dev]}; symdiff {['%.2e' % r for r in symdiff]}; "
+          f"skeletons (eqF, clear, bad_clear, bad_all) {agree}; "
+          f"root gpu {st['root_size']} oracle {o['root']}; PCG its {its[0]} rel {rel[0]:.2e} "
+          f"|u-u_o|/|u_o| {uerr:.2e}")
+    if precision == 0:
+        assert es_g <= 2.0 * es_o + 1e-12, (es_g, es_o)
+    else:
+        assert es_g < 1e-3, es_g
+    assert ratio_inf <= DIFF_C[precision], ratio_inf
+    assert max(rank_dev) <= RANK_BAND[precision], rank_dev
+    eq0, clear0, bad0, _ = agree[0]
+    assert eq0 > 0 and clear0 > 0.9 * eq0 and bad0 == 0, agree[0]
+    for lev in range(1, L):
+        assert agree[lev][2] == 0, (lev, agree[lev])
+    assert rel[0] <= 1e-10 and uerr <= 1e-8, (rel, uerr)
+    h.close()

@@ -1,4 +1,4 @@
-"""The C ABI library builds, loads and exports every symbol include/hif.h declares (no GPU)."""
+"""The C ABI library builds, loads and exports every symbol include/*.h declares (no GPU)."""
 import ctypes
 import os
 import re
@@ -9,9 +9,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "hif.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = set(re.findall(r"\b(hif_[a-z_]+)\s*\(", src))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in sorted(os.listdir(inc)):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(inc, fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(hif_[a-z_]+)\s*\(", src))
     return sorted(names)
 
 

@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 import scipy.linalg as sla
 
+from oracle import cpqr as cpqr_mod
 from oracle.cpqr import cpqr, interpolative_decomposition
 
 
@@ -65,3 +66,36 @@ def test_tie_breaks_to_lowest_index():
     k, skel, red, T = interpolative_decomposition(M, 1e-12)
     assert list(skel) == [2, 1] and list(red) == [0]
     assert np.allclose(T, [[0.0], [1.0]])
+
+
+def test_trace_records_the_pivot_norms_and_their_runner_up():
+    # the trace's chosen norms are LAPACK's |R_ii| (dgeqp3); the runner-up is
+    # the second largest column norm of the matrix with the chosen pivots'
+    # directions projected out, computed here by brute force
+    rng = np.random.default_rng(71)
+    M = rng.standard_normal((40, 12)) @ np.diag(10.0 ** -np.arange(12))
+    eps = 1e-7
+    trace = []
+    k, perm, R = cpqr(M, eps, trace)
+    _, Rl, pl = sla.qr(M, pivoting=True, mode="economic")
+    assert np.allclose([t[0] for t in trace[:k]], np.abs(np.diag(Rl))[:k], rtol=1e-10)
+    for i in range(k):
+        Q, _ = np.linalg.qr(M[:, perm[:i]]) if i else (np.zeros((40, 0)), None)
+        P = M - Q @ (Q.T @ M)
+        rest = [c for c in range(12) if c not in perm[:i]]
+        nrm = np.sort(np.linalg.norm(P[:, rest], axis=0))[::-1]
+        assert np.isclose(trace[i][0], nrm[0], rtol=1e-9)
+        assert np.isclose(trace[i][1], nrm[1] if nrm.size > 1 else 0.0, rtol=1e-8, atol=1e-300)
+        assert trace[i][2] == eps * trace[0][0]
+    # the stop: the step after the last pivot saw a norm at or below eps |R_11|
+    assert len(trace) == k + 1 and trace[k][0] <= trace[k][2]
+    m = cpqr_mod.decision_margin(trace)
+    assert 0.0 < m < 1.0
+
+
+def test_decision_margin_is_zero_on_a_tie():
+    # two columns of equal norm: the first pivot is a tie
+    M = np.array([[3.0, 0.0, 1.0], [0.0, 3.0, 0.0], [0.0, 0.0, 0.5]])
+    trace = []
+    cpqr(M, 1e-12, trace)
+    assert cpqr_mod.decision_margin(trace) == 0.0

@@ -153,8 +153,8 @@ def test_planted_transposed_interpolation_is_caught(monkeypatch):
     import oracle.hif as H
     real = H.interpolative_decomposition
 
-    def bad(M, eps):
-        k, s, r, T = real(M, eps)
+    def bad(M, eps, trace=None):
+        k, s, r, T = real(M, eps, trace)
         if T.size and T.shape[0] == T.shape[1]:
             T = T.T
         elif T.size:
@@ -241,3 +241,51 @@ def test_periodic_example1_matches_the_papers_table():
     x = np.random.default_rng(2).standard_normal(n ** 3)
     es = np.linalg.norm(x - hif.hif_apply(fac, A @ x)) / np.linalg.norm(x)
     assert g["es_min"] <= es <= g["es_max"], es
+
+
+def test_recorded_active_sets_follow_the_records():
+    # record=True keeps the active set after every level and every ID's
+    # decision; both must agree with the stored factors: the DOFs active after
+    # level l are those active before it minus the level's eliminated cell
+    # interiors and the redundant DOFs of its faces and edges
+    n, eps = 16, 1e-4
+    A = _problem(n, 91)
+    fac = hif.hif_factor(A, n, 4, eps, record=True)
+    before = np.arange(n ** 3)
+    for lev, act in enumerate(fac.active):
+        gone = [r.I for r in fac.records if isinstance(r, hif.CellRecord) and r.level == lev]
+        gone += [np.setdiff1d(F, skel) for (l, _, F, skel, _) in fac.ids if l == lev]
+        expect = np.setdiff1d(before, np.concatenate(gone))
+        assert np.array_equal(act, expect)
+        assert act.size == fac.ranks[lev][1]
+        before = act
+    assert np.array_equal(fac.active[-1], fac.root.S)
+    for (l, kind, F, skel, marg) in fac.ids:
+        assert np.all(np.isin(skel, F)) and marg >= 0.0
+    # recording changes nothing in the factorization
+    plain = hif.hif_factor(A, n, 4, eps)
+    x = np.random.default_rng(92).standard_normal(n ** 3)
+    assert np.array_equal(hif.hif_apply(plain, x), hif.hif_apply(fac, x))
+
+
+@pytest.mark.parametrize("n,lo,hi", [(8, -2.0, 2.0), (12, -1.0, 1.0)])
+def test_jacobi_cg_matches_dense_solve(n, lo, hi):
+    A = _problem(n, 93 + n, lo=lo, hi=hi, b=0.1)
+    f = np.random.default_rng(94).standard_normal(n ** 3)
+    u, its, rel = krylov.cg_jacobi(A, f, tol=1e-14)
+    ref = sla.cho_solve(sla.cho_factor(A.toarray()), f)
+    assert rel <= 1e-14 and np.linalg.norm(f - A @ u) <= 1e-14 * np.linalg.norm(f)
+    assert np.linalg.norm(u - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_jacobi_cg_solves_an_eigenvector_exactly():
+    # constant a: v_j = prod_d sin(p_d pi (j_d + 1) h) is an eigenvector with
+    # lambda = (4/h^2) sum_d sin^2(p_d pi h / 2), so A u = v gives u = v / lambda
+    n, p = 10, (1, 2, 3)
+    h = 1.0 / (n + 1)
+    A = stencil.assemble(np.ones(n ** 3), 0.0, n)
+    j = np.arange(n)
+    v = np.einsum("k,j,i->kji", *[np.sin(q * np.pi * (j + 1) * h) for q in p[::-1]]).reshape(-1)
+    lam = 4.0 / h ** 2 * sum(np.sin(q * np.pi * h / 2) ** 2 for q in p)
+    u, its, rel = krylov.cg_jacobi(A, v, tol=1e-14)
+    assert np.linalg.norm(u - v / lam) <= 1e-12 * np.linalg.norm(v / lam)
