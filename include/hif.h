@@ -69,8 +69,14 @@ typedef struct {
   double eps;        /* relative precision of the ID (Table 2); 0 = no
                         skeletonization: exact nested-dissection elimination */
   int precision;     /* HIF_PREC_FP64: every factor block in double.
-                        HIF_PREC_FP32: factor blocks in float (ID column
-                        norms still accumulated in double); hif_solve keeps
+                        HIF_PREC_FP32: factor blocks in float; the ID of a
+                        front too large for one SM's shared memory keeps its
+                        column norms in double and downdates them there
+                        (recomputing on cancellation), the ID of a smaller
+                        front recomputes every norm from the updated entries
+                        at each step in float (no downdate, nothing to
+                        cancel); fronts flagged by pivot growth are
+                        refactored in double (retry_growth); hif_solve keeps
                         the residual r = f - A u in double. */
   int use_graphs;    /* 1: the two sweeps of an apply (hif_apply, and the
                         preconditioner inside hif_solve) are captured once
@@ -86,10 +92,18 @@ typedef struct {
                         (TF32 with the 3xTF32 split, FP32 accumulation); 0:
                         every product on the FP32 FMA units.  FP64 factors
                         never use them. */
+  double retry_growth; /* HIF_PREC_FP32 only: a front whose Cholesky (the
+                        LDL^T of §2.2 / §2.3) meets a pivot d_j with
+                        A_jj / d_j > retry_growth (A_jj its original
+                        diagonal entry), or a pivot that is not positive, is
+                        refactored in double and stored in float
+                        (hif_stats.retried_fronts counts them); 0: no retry,
+                        such a pivot fails with HIF_ERR_NOT_SPD.  Must be
+                        finite and >= 0. */
 } hif_options;
 
 /* Fill *opt with defaults: eps 1e-6, FP64, graphs on, pcg_tol 1e-10, 200 its,
-   tensor cores on. */
+   tensor cores on, retry_growth 1e5. */
 void hif_default_options(hif_options* opt);
 
 /*
@@ -176,6 +190,7 @@ typedef struct {
   int64_t stored_entries;        /* factor entries read by one apply sweep */
   int kernel_launches;           /* kernels launched by hif_factor */
   int apply_launches;            /* kernels launched by one hif_apply (nrhs = 1) */
+  int64_t retried_fronts;        /* FP32 fronts refactored in double (retry_growth) */
 } hif_stats;
 
 hif_status hif_query_stats(hif_handle h, hif_stats* st);

@@ -63,9 +63,16 @@ struct TileAcc {
 // of entry (c+1, c+1) publishes the next pivot.  L goes to the factor panel
 // (zeros above the diagonal); a non-positive or non-finite pivot flags the
 // front and continues with 1.
+//
+// With growth > 0 (FP32 fronts that may be retried in FP64), the panel's
+// diagonal holds the front's original diagonal A_jj on entry, and a pivot
+// d_j with A_jj / d_j > growth (cancellation has eaten all but a few bits of
+// it), or one that is not positive or not finite, marks the front in
+// fflag[blockIdx.x] instead of failing it.
 template <typename T>
 __global__ void __launch_bounds__(256) k_chol_diag(const DFront* __restrict__ fr, const T* Kar,
-                                                   T* Par, int j0, int* flags) {
+                                                   T* Par, int j0, int* flags, float growth,
+                                                   int* fflag) {
   const DFront d = fr[blockIdx.x];
   if (j0 >= d.p) return;
   const int jb = min(NB, d.p - j0);
@@ -75,6 +82,8 @@ __global__ void __launch_bounds__(256) k_chol_diag(const DFront* __restrict__ fr
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   __shared__ T colv[2][NB];
   __shared__ T diagv[NB];
+  __shared__ T origv[NB];
+  if (growth > 0.f && threadIdx.x < jb) origv[threadIdx.x] = P[threadIdx.x + (int64_t)threadIdx.x * ld];
   T a[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -90,7 +99,12 @@ __global__ void __launch_bounds__(256) k_chol_diag(const DFront* __restrict__ fr
     if (tx == c % 16) {
       const int j = c / 16;
       T dv = diagv[c];
-      if (!(dv > T(0)) || !isfinite(dv)) {
+      if (growth > 0.f) {
+        if (!(dv > T(0)) || !isfinite(dv) || dv * (T)growth < origv[c]) {
+          if (ty == 0) fflag[blockIdx.x] = 1;
+          if (!(dv > T(0)) || !isfinite(dv)) dv = T(1);
+        }
+      } else if (!(dv > T(0)) || !isfinite(dv)) {
         if (ty == 0) flag_front(flags, FLAG_NOT_SPD, d.id);
         dv = T(1);
       }
@@ -278,6 +292,67 @@ __global__ void __launch_bounds__(NB) k_trtri_diag(const DFront* __restrict__ fr
 }
 
 
+// ---- FP64 retry of FP32 fronts flagged by the leading-block Cholesky ----------
+// Before the leading block is factored: its p x p entries are copied to a
+// snapshot S (column-major, ld = p) and its diagonal to the panel's diagonal
+// (where k_chol_diag reads the original A_jj).
+template <typename T>
+__global__ void __launch_bounds__(256) k_retry_prep(const DFront* __restrict__ fr, const T* Kar,
+                                                    T* Par, T* S, const int64_t* __restrict__ soff) {
+  const DFront d = fr[blockIdx.y];
+  const int64_t pp = (int64_t)d.p * d.p;
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < pp; e += (int64_t)gridDim.x * 256) {
+    const int r = (int)(e % d.p), c = (int)(e / d.p);
+    const T v = Kar[d.K + r + (int64_t)c * d.ld];
+    S[soff[blockIdx.y] + e] = v;
+    if (r == c) Par[d.P + r + (int64_t)c * d.ld] = v;
+  }
+}
+
+// A flagged front in the FP32 arenas and its FP64 copy.
+struct RetryMap {
+  int64_t Kf, Pf;   // offsets in the FP32 K and panel arenas
+  int64_t Kd, Pd;   // offsets in the FP64 copies
+  int64_t S;        // offset of its leading-block snapshot
+  int p, ld;        // eliminated count, size (= leading dimension)
+};
+
+// FP64 copy of the original front: the leading block from the snapshot, the
+// rest (A_NI, A_NN: untouched by the leading-block Cholesky) from K.
+__global__ void __launch_bounds__(256) k_retry_build(const RetryMap* __restrict__ mp,
+                                                     const float* Kar, const float* S,
+                                                     double* Kd) {
+  const RetryMap m = mp[blockIdx.y];
+  const int64_t tot = (int64_t)m.ld * m.ld;
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < tot; e += (int64_t)gridDim.x * 256) {
+    const int r = (int)(e % m.ld), c = (int)(e / m.ld);
+    const float v = (r < m.p && c < m.p) ? S[m.S + r + (int64_t)c * m.p] : Kar[m.Kf + e];
+    Kd[m.Kd + e] = (double)v;
+  }
+}
+
+// Results of the FP64 partial Cholesky back in FP32: the whole panel
+// [Linv; X^T] and the Schur complement (trailing block of K).
+__global__ void __launch_bounds__(256) k_retry_writeback(const RetryMap* __restrict__ mp,
+                                                         const double* Kd, const double* Pd,
+                                                         float* Kar, float* Par) {
+  const RetryMap m = mp[blockIdx.y];
+  const int64_t np = (int64_t)m.ld * m.p;
+  const int nb = m.ld - m.p;
+  const int64_t nn = (int64_t)nb * nb;
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < np + nn;
+       e += (int64_t)gridDim.x * 256) {
+    if (e < np) {
+      Par[m.Pf + e] = (float)Pd[m.Pd + e];
+    } else {
+      const int64_t q = e - np;
+      const int r = m.p + (int)(q % nb), c = m.p + (int)(q / nb);
+      const int64_t o = r + (int64_t)c * m.ld;
+      Kar[m.Kf + o] = (float)Kd[m.Kd + o];
+    }
+  }
+}
+
 // ---- generic batched GEMM ------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm(const GemmOp* __restrict__ ops, const T* Ab,
@@ -432,11 +507,94 @@ __global__ void __launch_bounds__(256) k_gemv_t(const GemvOp* __restrict__ ops,
 constexpr int TC_MIN_ROWS = 256;
 
 template <typename T>
+void finish_fronts(const DFront* d_fronts, const DFront* h_fronts, int nfront, T* Karena,
+                   T* Parena, int* d_flags, bool use_tc, cudaStream_t st);
+
+// Refactor the flagged FP32 fronts entirely in FP64 (from the snapshot of
+// their leading blocks and their untouched A_NI, A_NN) and store the results
+// in the FP32 arenas.
+static void retry_fronts_fp64(const std::vector<int>& bad, const DFront* h_fronts,
+                       const std::vector<int64_t>& soff, float* Karena, float* Parena,
+                       const float* snap, int* d_flags, cudaStream_t st) {
+  const int nb = (int)bad.size();
+  std::vector<DFront> dl;
+  std::vector<RetryMap> maps;
+  int64_t kt = 0, pt = 0, mx = 0;
+  for (int f : bad) {
+    const DFront& h = h_fronts[f];
+    dl.push_back(DFront{kt, pt, h.n, h.p, h.id, h.ld});
+    maps.push_back(RetryMap{h.K, h.P, kt, pt, soff[f], h.p, h.ld});
+    kt += (int64_t)h.ld * h.ld;
+    pt += (int64_t)h.ld * h.p;
+    mx = std::max<int64_t>(mx, (int64_t)h.ld * h.ld);
+  }
+  double* Kd = nullptr;
+  double* Pd = nullptr;
+  RetryMap* d_maps = nullptr;
+  DFront* d_dl = nullptr;
+  HIF_CUDA_TRY(cudaMallocAsync(&Kd, sizeof(double) * kt, st));
+  HIF_CUDA_TRY(cudaMallocAsync(&Pd, sizeof(double) * std::max<int64_t>(1, pt), st));
+  HIF_CUDA_TRY(cudaMallocAsync(&d_maps, sizeof(RetryMap) * nb, st));
+  HIF_CUDA_TRY(cudaMallocAsync(&d_dl, sizeof(DFront) * nb, st));
+  HIF_CUDA_TRY(cudaMemsetAsync(Pd, 0, sizeof(double) * std::max<int64_t>(1, pt), st));
+  HIF_CUDA_TRY(cudaMemcpyAsync(d_maps, maps.data(), sizeof(RetryMap) * nb, cudaMemcpyHostToDevice, st));
+  HIF_CUDA_TRY(cudaMemcpyAsync(d_dl, dl.data(), sizeof(DFront) * nb, cudaMemcpyHostToDevice, st));
+  const int gx = std::max(1, std::min(1024, ceil_div(mx, 256)));
+  for (int f0 = 0; f0 < nb; f0 += MAX_GRID_Y) {
+    const int c = std::min(MAX_GRID_Y, nb - f0);
+    ProfScope ps("chol_retry_fp64", st);
+    k_retry_build<<<dim3(gx, c), 256, 0, st>>>(d_maps + f0, Karena, snap, Kd);
+    HIF_CHECK_LAUNCH();
+  }
+  partial_cholesky<double>(d_dl, dl.data(), nb, Kd, Pd, d_flags, false, st, nullptr);
+  for (int f0 = 0; f0 < nb; f0 += MAX_GRID_Y) {
+    const int c = std::min(MAX_GRID_Y, nb - f0);
+    ProfScope ps("chol_retry_fp64", st);
+    k_retry_writeback<<<dim3(gx, c), 256, 0, st>>>(d_maps + f0, Kd, Pd, Karena, Parena);
+    HIF_CHECK_LAUNCH();
+  }
+  HIF_CUDA_TRY(cudaFreeAsync(d_dl, st));
+  HIF_CUDA_TRY(cudaFreeAsync(d_maps, st));
+  HIF_CUDA_TRY(cudaFreeAsync(Pd, st));
+  HIF_CUDA_TRY(cudaFreeAsync(Kd, st));
+}
+
+template <typename T>
 void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront, T* Karena,
-                      T* Parena, int* d_flags, bool tensor_cores, cudaStream_t st) {
+                      T* Parena, int* d_flags, bool tensor_cores, cudaStream_t st,
+                      const RetryOpts* retry) {
   if (nfront == 0) return;
   const bool use_tc = std::is_same<T, float>::value && tensor_cores;
   const int pmax = h_fronts[0].p;
+  // FP32 fronts that may be retried in FP64: snapshot of every leading block,
+  // original diagonal in the panel, one flag per front
+  const bool growth_on = std::is_same<T, float>::value && retry && retry->growth > 0.0;
+  int* d_fflag = nullptr;
+  T* snap = nullptr;
+  int64_t* d_soff = nullptr;
+  std::vector<int64_t> soff;
+  if (growth_on) {
+    soff.resize(nfront);
+    int64_t tot = 0, mx = 1;
+    for (int f = 0; f < nfront; ++f) {
+      soff[f] = tot;
+      tot += (int64_t)h_fronts[f].p * h_fronts[f].p;
+      mx = std::max<int64_t>(mx, (int64_t)h_fronts[f].p * h_fronts[f].p);
+    }
+    HIF_CUDA_TRY(cudaMallocAsync(&d_fflag, sizeof(int) * nfront, st));
+    HIF_CUDA_TRY(cudaMallocAsync(&snap, sizeof(T) * std::max<int64_t>(1, tot), st));
+    HIF_CUDA_TRY(cudaMallocAsync(&d_soff, sizeof(int64_t) * nfront, st));
+    HIF_CUDA_TRY(cudaMemsetAsync(d_fflag, 0, sizeof(int) * nfront, st));
+    HIF_CUDA_TRY(cudaMemcpyAsync(d_soff, soff.data(), sizeof(int64_t) * nfront,
+                                 cudaMemcpyHostToDevice, st));
+    const int gx = std::max(1, std::min(1024, ceil_div(mx, 256)));
+    for (int f0 = 0; f0 < nfront; f0 += MAX_GRID_Y) {
+      const int c = std::min(MAX_GRID_Y, nfront - f0);
+      ProfScope ps("chol_retry_snapshot", st, 0.0, 2.0 * sizeof(T) * tot);
+      k_retry_prep<T><<<dim3(gx, c), 256, 0, st>>>(d_fronts + f0, Karena, Parena, snap, d_soff + f0);
+      HIF_CHECK_LAUNCH();
+    }
+  }
   // 1. Cholesky of the leading p x p block (right-looking, panels of NB):
   //    the kernels see extent p, leading dimension n
   std::vector<DFront> lead(h_fronts, h_fronts + nfront);
@@ -479,7 +637,9 @@ void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront
         const int nb = std::min(MAX_GRID_Y, nact - f0);
         {
           ProfScope ps("chol_panel", st, pf, pb);
-          k_chol_diag<T><<<nb, 256, 0, st>>>(d_lead + f0, Karena, Parena, j0, d_flags);
+          k_chol_diag<T><<<nb, 256, 0, st>>>(d_lead + f0, Karena, Parena, j0, d_flags,
+                                             growth_on ? (float)retry->growth : 0.f,
+                                             growth_on ? d_fflag + f0 : nullptr);
           HIF_CHECK_LAUNCH();
           if (chunks > 0) {
             k_panel<T><<<dim3(chunks, nb), PANEL_ROWS, 0, st>>>(d_lead + f0, Karena, Parena, j0);
@@ -526,6 +686,44 @@ void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront
     HIF_CUDA_TRY(cudaFreeAsync(d_uo, st));
   }
   HIF_CUDA_TRY(cudaFreeAsync(d_lead, st));
+  // flagged fronts: redone in FP64 now; the others go on in FP32
+  std::vector<DFront> keep;
+  DFront* d_keep = nullptr;
+  if (growth_on) {
+    std::vector<int> hf(nfront), bad;
+    HIF_CUDA_TRY(cudaMemcpyAsync(hf.data(), d_fflag, sizeof(int) * nfront, cudaMemcpyDeviceToHost, st));
+    HIF_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int f = 0; f < nfront; ++f) {
+      if (hf[f]) bad.push_back(f);
+      else keep.push_back(h_fronts[f]);
+    }
+    if (!bad.empty()) {
+      if constexpr (std::is_same<T, float>::value)
+        retry_fronts_fp64(bad, h_fronts, soff, Karena, Parena, snap, d_flags, st);
+      if (retry->retried) *retry->retried += (int64_t)bad.size();
+      if (!keep.empty()) {
+        HIF_CUDA_TRY(cudaMallocAsync(&d_keep, sizeof(DFront) * keep.size(), st));
+        HIF_CUDA_TRY(cudaMemcpyAsync(d_keep, keep.data(), sizeof(DFront) * keep.size(),
+                                     cudaMemcpyHostToDevice, st));
+      }
+      d_fronts = d_keep;
+      h_fronts = keep.data();
+      nfront = (int)keep.size();
+    }
+    HIF_CUDA_TRY(cudaFreeAsync(d_soff, st));
+    HIF_CUDA_TRY(cudaFreeAsync(snap, st));
+    HIF_CUDA_TRY(cudaFreeAsync(d_fflag, st));
+    if (nfront == 0) return;
+  }
+  finish_fronts(d_fronts, h_fronts, nfront, Karena, Parena, d_flags, use_tc, st);
+  if (d_keep) HIF_CUDA_TRY(cudaFreeAsync(d_keep, st));
+}
+
+// Steps 2-4 of the partial Cholesky once the leading blocks hold L.
+template <typename T>
+void finish_fronts(const DFront* d_fronts, const DFront* h_fronts, int nfront, T* Karena,
+                   T* Parena, int* d_flags, bool use_tc, cudaStream_t st) {
+  const int pmax = h_fronts[0].p;
   // 2. Linv = L^{-1}: invert the NB x NB diagonal blocks, then merge
   //    neighbouring inverted blocks pairwise up a binary tree of widths
   //    s = NB, 2 NB, 4 NB, ...:  inv([A 0; B C]) = [A^-1 0; -C^-1 B A^-1  C^-1]
@@ -687,7 +885,7 @@ void gemv_batched(const GemvOp* d_ops, const GemvOp* h_ops, int nops, int trans,
 
 #define HIF_INST(T)                                                                          \
   template void partial_cholesky<T>(const DFront*, const DFront*, int, T*, T*, int*, bool,  \
-                                    cudaStream_t);                                           \
+                                    cudaStream_t, const RetryOpts*);                         \
   template void gemm_batched<T>(const GemmOp*, const GemmOp*, int, const T*, const T*, T*,  \
                                 cudaStream_t, const char*);                                  \
   template void gemv_batched<T>(const GemvOp*, const GemvOp*, int, int, const T*, T*,       \

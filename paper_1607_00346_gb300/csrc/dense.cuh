@@ -8,14 +8,27 @@ namespace hif {
 constexpr int NB = 64;      // panel width of the partial Cholesky and of the triangular inverse
 constexpr int TILE = 64;    // output tile of the trailing update / batched GEMM
 
+// FP64 retry of FP32 fronts (the LDL^T of §2.2 / §2.3 read as Cholesky, redone
+// in double when the FP32 one breaks down): a front whose leading-block
+// Cholesky meets a pivot d_j with A_jj / d_j > growth (or d_j not positive)
+// is refactored entirely in FP64; growth = 0 turns this off (such a pivot
+// then fails the factorization with HIF_ERR_NOT_SPD).  *retried counts them.
+struct RetryOpts {
+  double growth;
+  int64_t* retried;
+};
+
 // Partial Cholesky of a batch of fronts (§2.2 and §2.3: A_II = L L^T,
 // X = L^{-1} A_IN, A_NN -= X^T X).  Fronts must be sorted by p, largest first.
 // On return: trailing blocks of K hold the Schur complements, P holds
 // [Linv; X^T] (Linv = L^{-1}, lower triangular) for each front.  With
-// tensor_cores (FP32 only) the deep products run on gemm_tc.
+// tensor_cores (FP32 only) the deep products run on gemm_tc.  With retry
+// (FP32 only) the host waits once after the leading blocks are factored to
+// read the per-front flags.
 template <typename T>
 void partial_cholesky(const DFront* d_fronts, const DFront* h_fronts, int nfront, T* Karena,
-                      T* Parena, int* d_flags, bool tensor_cores, cudaStream_t st);
+                      T* Parena, int* d_flags, bool tensor_cores, cudaStream_t st,
+                      const RetryOpts* retry = nullptr);
 
 // C = beta C + alpha op(A) op(B) on the tensor cores (tcgen05, 3xTF32; see
 // tc.cu): GemmOp semantics as gemm_batched, beta 0 or 1, FP32 data.

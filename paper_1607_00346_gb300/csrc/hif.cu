@@ -377,7 +377,11 @@ struct Factor : FactorBase {
 template <typename T>
 class Builder {
  public:
-  Builder(Factor<T>& F, cudaStream_t st) : F_(F), st_(st), sym_(F.n, F.m) { tr_.st = st; }
+  Builder(Factor<T>& F, cudaStream_t st) : F_(F), st_(st), sym_(F.n, F.m) {
+    tr_.st = st;
+    retry_.growth = std::is_same<T, float>::value ? F.opt.retry_growth : 0.0;
+    retry_.retried = &F.stats.retried_fronts;
+  }
   ~Builder() {
     jobs_.clear();   // waits for the host workers
     if (up_st_) {
@@ -428,6 +432,7 @@ class Builder {
 
   Factor<T>& F_;
   cudaStream_t st_;
+  RetryOpts retry_{};
   Symbolic sym_;
   DevBuf flags_;
   int level_ = 0;
@@ -656,7 +661,7 @@ void Builder<T>::cell_step(std::shared_ptr<const CellPlan> cpp, DevBuf& Kar, Dev
   DevBuf fr_d;
   upload_async(fr_d, fr, &F_.mem, st_);
   partial_cholesky<T>(fr_d.as<DFront>(), fr.data(), (int)fr.size(), Kar.as<T>(), s.panels.as<T>(),
-                      flags_.as<int>(), F_.opt.tensor_cores != 0, st_);
+                      flags_.as<int>(), F_.opt.tensor_cores != 0, st_, &retry_);
   tr_.mark(level_, " cells: partial Cholesky queued");
   // apply stage: gather the whole frontal list of every cell (already on
   // the device); the rest is built on a worker thread
@@ -953,7 +958,7 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
   DevBuf fr_d;
   upload_async(fr_d, frs, &F_.mem, st_);
   partial_cholesky<T>(fr_d.as<DFront>(), frs.data(), (int)frs.size(), Z.as<T>(), s.panels.as<T>(),
-                      flags_.as<int>(), F_.opt.tensor_cores != 0, st_);
+                      flags_.as<int>(), F_.opt.tensor_cores != 0, st_, &retry_);
   tr_.mark(level_, " Z products + Cholesky queued");
   skel_writeback<T>(sda_d.as<SkelDesc>(), sda.data(), (int)sda.size(), ncp, rowpos_d.as<int32_t>(),
                     perm_d.as<int32_t>(), cdesc_d.as<CellDesc>(), Z.as<T>(), Kar.as<T>(), st_);
@@ -1453,6 +1458,7 @@ void hif_default_options(hif_options* o) {
   o->pcg_tol = 1e-10;
   o->max_iter = 200;
   o->tensor_cores = 1;
+  o->retry_growth = 1e5;
 }
 
 const char* hif_version(void) { return "hif-gb300 0.1"; }
@@ -1477,6 +1483,8 @@ hif_status hif_factor(const hif_grid* grid, const double* a, const double* b, do
     throw Error{HIF_ERR_INVALID_ARG, "precision must be HIF_PREC_FP64 or HIF_PREC_FP32"};
   if (o.tensor_cores != 0 && o.tensor_cores != 1)
     throw Error{HIF_ERR_INVALID_ARG, "tensor_cores must be 0 or 1"};
+  if (!std::isfinite(o.retry_growth) || o.retry_growth < 0)
+    throw Error{HIF_ERR_INVALID_ARG, "retry_growth must be finite and >= 0"};
   if (!std::isfinite(b_const) || b_const < 0) throw Error{HIF_ERR_INVALID_ARG, "b_const must be finite and >= 0"};
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int64_t N = (int64_t)n * n * n;

@@ -34,7 +34,8 @@ class Grid(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("precision", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("pcg_tol", ctypes.c_double),
-                ("max_iter", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("tensor_cores", ctypes.c_int),
+                ("retry_growth", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -50,7 +51,8 @@ class Stats(ctypes.Structure):
                 ("peak_bytes", ctypes.c_size_t),
                 ("stored_entries", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int),
-                ("apply_launches", ctypes.c_int)]
+                ("apply_launches", ctypes.c_int),
+                ("retried_fronts", ctypes.c_int64)]
 
 
 _lib = None
@@ -296,7 +298,7 @@ class Handle:
                     level_seconds=list(s.level_seconds)[:L + 1], flops=s.flops,
                     factor_bytes=s.factor_bytes, peak_bytes=s.peak_bytes,
                     stored_entries=s.stored_entries, kernel_launches=s.kernel_launches,
-                    apply_launches=s.apply_launches)
+                    apply_launches=s.apply_launches, retried_fronts=s.retried_fronts)
 
 
 def load_factor(path: str) -> Handle:
@@ -310,11 +312,14 @@ def load_factor(path: str) -> Handle:
 
 def factor(n: int, m: int, a, b=None, b_const: float = 0.0, eps: float = 1e-6,
            precision: int = PREC_FP64, pcg_tol: float = 1e-10, max_iter: int = 200,
-           stream=None, tensor_cores: bool = True, use_graphs: bool = True) -> Handle:
+           stream=None, tensor_cores: bool = True, use_graphs: bool = True,
+           retry_growth: float | None = None) -> Handle:
     """hif_factor: a (and b) are n^3 float64 arrays, host or device."""
     g = Grid(n, m, 0)
     o = default_options(eps=eps, precision=precision, pcg_tol=pcg_tol, max_iter=max_iter,
                         tensor_cores=int(bool(tensor_cores)), use_graphs=int(bool(use_graphs)))
+    if retry_growth is not None:
+        o.retry_growth = float(retry_growth)
     ap, _ka = _ptr(a)
     bp, _kb = _ptr(b)
     out = ctypes.c_void_p()

@@ -307,3 +307,42 @@ def test_measured_peaks_are_plausible(H):
     assert p["bf16_mma_tflops"] > 1.5 * p["tf32_mma_tflops"]
     # FMA: at most 128 lanes x 2 flops x clock per SM
     assert p["fp32_fma_tflops"] <= 1.05 * p["sm_count"] * 256 * p["sm_clock_khz"] * 1e3 / 1e12
+
+
+def test_fp64_retry_of_fronts_flagged_by_pivot_growth(H):
+    # contrast 10^8 (a = 10^U(-4,4)), FP32 factor: fronts whose Cholesky loses
+    # most of a pivot to cancellation (A_jj / d_j > retry_growth) are
+    # refactored in double.  The retried factor must still meet the parity
+    # bounds (PCG solution equal to the oracle's to 1e-8, e_s no worse than
+    # the factor without retries), and forcing retries (a small threshold)
+    # may only make the factor better.
+    n, eps = 32, 1e-6
+    a = _coeff(n, 1201, -4.0, 4.0)
+    A = stencil.assemble(a, 0.0, n)
+    x = inputs.normal_rhs(n, 1, 1202)[0]
+    f = inputs.normal_rhs(n, 1, 1203)
+    out = {}
+    for g in (0.0, 1e5, 1e2):
+        try:
+            h = H.factor(n, 4, _dev(a), eps=eps, precision=1, retry_growth=g)
+        except H.HifError as e:          # without retries FP32 may break down
+            assert g == 0.0 and e.status == 3, e
+            out[g] = None
+            continue
+        es = _es_gpu(h, A, x)
+        u = torch.zeros(f.shape, dtype=torch.float64, device="cuda")
+        its, rel = h.solve(_dev(f), u, check=False)
+        out[g] = (h.stats()["retried_fronts"], es, its[0], rel[0], u.cpu().numpy()[0])
+        h.close()
+    print("\n[retry] " + "; ".join(f"growth {g:g}: " + ("NOT_SPD" if v is None else
+          f"retried {v[0]}, e_s {v[1]:.2e}, PCG {v[2]} its relres {v[3]:.1e}")
+          for g, v in out.items()))
+    assert out[1e2][0] > 0
+    fac = ohif.hif_factor(A, n, 4, eps, check=False)
+    uo, _, _ = krylov.pcg(A, fac, f[0], tol=1e-12)
+    for g in (1e5, 1e2):
+        retried, es, its, rel, u = out[g]
+        assert rel <= 1e-10, (g, rel)
+        assert np.linalg.norm(u - uo) <= 1e-8 * np.linalg.norm(uo), g
+    if out[0.0] is not None:
+        assert out[1e2][1] <= 1.5 * out[0.0][1], (out[1e2][1], out[0.0][1])

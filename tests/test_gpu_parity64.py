@@ -9,20 +9,23 @@ two spawned processes; every GPU configuration is compared with it on the
 same seeded inputs:
 
   * solve error e_s = ||x - F^{-1} A x|| / ||x|| (§4, Table 2): FP64 within
-    2x the oracle's; FP32 (rounding-dominated at eps = 1e-6) below 1e-3;
+    2x the oracle's; FP32 below ES_FP32[tensor_cores] (the FP32 factor's
+    rounding, not eps = 1e-6, sets its error: measured 2.6e-5 with the
+    3xTF32 products, 2.8e-6 with FMA products; a plain TF32 product, 11
+    bits, would give ~1e-3);
   * F_gpu^{-1} b against F_oracle^{-1} b element by element (b = A x): both
-    approximate x with relative error e_s, so their difference is at most
-    e_s(gpu) + e_s(oracle) in 2-norm whatever the skeletons; the check is
-    that it is much smaller, ||d||_inf <= C e_s(oracle) ||y||_inf with
-    C = DIFF_C[precision], i.e. the two factors make the same approximation;
-  * the number of DOFs active after every level (the ranks of the level's
-    IDs, Sigma^{l+1} of §2.4) within RANK_BAND[precision] of the oracle's;
-  * identical skeleton sets at level 0 (identical inputs on both sides) for
-    every face and edge whose CPQR decisions are clear by more than the
-    rounding of the precision (oracle decision margin > MARGIN[precision]),
-    and at higher levels for the fronts whose DOF set F is the same on both
-    sides and whose decisions are clear by more than the eps-sized
-    difference of the inputs (margin > MARGIN_UP);
+    approximate x with relative error e_s, so any two factors differ by up to
+    e_s(gpu) + e_s(oracle); factors that make the same approximation differ
+    by rounding only.  FP64: ||d||_inf <= 1e-11 ||y||_inf (measured 3e-14,
+    while e_s is 1e-6 .. 1e-4); FP32: ||d||_inf <= 10 e_s(gpu) ||y||_inf
+    (measured 3-6);
+  * the DOFs active after every level (Sigma^{l+1} of §2.4): the same sets
+    on both sides, up to RANK_BAND[precision] of their size (measured: equal);
+  * identical skeleton sets for every face and edge whose DOF set F is the
+    same on both sides and whose CPQR decisions are clear by more than the
+    input difference (oracle decision margin > MARGIN_UP; at level 0 the
+    inputs are identical, so every front counts), and at most 0.5% of the
+    others different (measured: none);
   * the PCG solution (to 1e-10) equal to the oracle's PCG solution (to
     1e-12) to 1e-8 relative.
 """
@@ -39,9 +42,8 @@ from paper_1607_00346_gb300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-DIFF_C = {0: 0.5, 1: 20.0}
-RANK_BAND = {0: 0.01, 1: 0.05}
-MARGIN = {0: 1e-8, 1: 1e-3}
+ES_FP32 = {True: 1e-4, False: 1.2e-5}
+RANK_BAND = {0: 0.0, 1: 1e-3}
 MARGIN_UP = 1e-2
 
 
@@ -76,7 +78,7 @@ def _skeleton_agreement(n, m, L, act_g, act_o, ids):
         before_g = np.arange(n ** 3) if lev == 0 else act_g[lev - 1]
         groups_g = geo.group_active(before_g, n, s)
         after_g = act_g[lev]
-        thr = MARGIN_UP if lev else None
+        thr = MARGIN_UP if lev else None   # level 0: identical inputs
         eq = clear = bad_clear = bad_all = 0
         for (l, kind, F, skel, marg) in ids:
             if l != lev:
@@ -134,15 +136,18 @@ def test_contrast64_elementwise_against_oracle(H, oracle64, precision, tc, eps):
           f"skeletons (eqF, clear, bad_clear, bad_all) {agree}; "
           f"root gpu {st['root_size']} oracle {o['root']}; PCG its {its[0]} rel {rel[0]:.2e} "
           f"|u-u_o|/|u_o| {uerr:.2e}")
+    dinf = float(np.abs(d).max() / np.abs(o["y"]).max())
     if precision == 0:
         assert es_g <= 2.0 * es_o + 1e-12, (es_g, es_o)
+        assert dinf <= 1e-11, dinf
     else:
-        assert es_g < 1e-3, es_g
-    assert ratio_inf <= DIFF_C[precision], ratio_inf
+        assert es_g < ES_FP32[tc], es_g
+        assert dinf <= 10.0 * es_g, (dinf, es_g)
     assert max(rank_dev) <= RANK_BAND[precision], rank_dev
-    eq0, clear0, bad0, _ = agree[0]
-    assert eq0 > 0 and clear0 > 0.9 * eq0 and bad0 == 0, agree[0]
-    for lev in range(1, L):
-        assert agree[lev][2] == 0, (lev, agree[lev])
+    assert max(symdiff) <= 2 * RANK_BAND[precision] + 1e-3, symdiff
+    assert agree[0][0] == len([i for i in o["ids"] if i[0] == 0]), agree[0]
+    for lev in range(L):
+        eq, clear, bad_clear, bad_all = agree[lev]
+        assert eq > 0 and bad_clear == 0 and bad_all <= 0.005 * eq, (lev, agree[lev])
     assert rel[0] <= 1e-10 and uerr <= 1e-8, (rel, uerr)
     h.close()
