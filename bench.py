@@ -300,7 +300,8 @@ def contrast256_record(hif, torch):
                    "peak_bytes": stt["peak_bytes"], "factor_bytes": stt["factor_bytes"],
                    "predicted_bytes": hif.predict_bytes(n, w["m"], eps=w["eps"],
                                                         precision=hif.PREC_FP32),
-                   "hbm_budget_bytes": 180 * 10 ** 9, "root_size": stt["root_size"]}
+                   "hbm_budget_bytes": 180 * 10 ** 9, "root_size": stt["root_size"],
+                   "retried_fronts": stt["retried_fronts"]}
     del a, f, u
     torch.cuda.empty_cache()
     return rec
@@ -522,6 +523,7 @@ def main():
             "solve_mdofs": N * nrhs / statistics.median(sol_s) / 1e6,
             "pcg_iters": its_all[-1], "relres": rel_all[-1], "relres_check": relres_chk,
             "root_size": stats["root_size"], "factor_gflop": stats["flops"] / 1e9,
+            "retried_fronts": stats["retried_fronts"],
             "factor_bytes": stats["factor_bytes"], "peak_bytes": stats["peak_bytes"],
             "clocks": clocks, "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N * (1 + nrhs),

@@ -9,7 +9,8 @@
  *
  * on an n x n x n interior grid of the unit cube with zero Dirichlet
  * boundary (h = 1/(n+1); half-point coefficients are harmonic means of the
- * grid values, a_j towards the boundary), as A ~= F with
+ * grid values, a_j towards the boundary), or on the periodic n^3 grid of the
+ * unit torus (h = 1/n; hif_grid.bc), as A ~= F with
  *
  *     F^{-1} = W^0 ... W^{L-1} W^L D^{-1} W^{L T} ... W^{0 T}     (§2.4)
  *
@@ -60,7 +61,11 @@ typedef enum {
 typedef struct {
   int n;
   int m;
-  int bc;        /* 0 = zero Dirichlet (the only value accepted) */
+  int bc;        /* 0: zero Dirichlet boundary on the n^3 interior grid,
+                    h = 1/(n+1).  1: periodic, the paper's own setting (§2.1,
+                    §4): grid points j/n of the unit torus, h = 1/n, every
+                    multiple of the cell side a separator; the operator is
+                    singular for b = 0, so b must be > 0 everywhere. */
 } hif_grid;
 
 enum { HIF_PREC_FP64 = 0, HIF_PREC_FP32 = 1 };
@@ -111,7 +116,7 @@ void hif_default_options(hif_options* opt);
  *   grid:  n, m with n = m 2^L, L >= 1, n <= 1024.
  *   a:     n^3 doubles, every value finite and > 0 (host or device).
  *   b:     n^3 doubles (host or device), or NULL to use b_const everywhere;
- *          every value finite and >= 0.
+ *          every value finite and >= 0 (> 0 on the periodic grid).
  *   opt:   options (NULL = defaults).
  *   out:   receives the handle; the handle owns every device buffer of the
  *          factor until hif_destroy.

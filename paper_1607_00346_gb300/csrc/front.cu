@@ -17,52 +17,74 @@ constexpr int MAX_GRID_Y = 65535;
 
 __device__ __forceinline__ double harmonic(double p, double q) { return 2.0 * p * q / (p + q); }
 
+// Dirichlet: h = 1/(n+1), a neighbour outside the grid adds its coupling
+// (a_j) to the diagonal only.  Periodic: h = 1/n, the last plane couples to
+// the first, and b must be positive (otherwise the constant is a null vector).
 __global__ void k_stencil(const double* __restrict__ a, const double* __restrict__ b,
-                          double b_const, int n, double* cpl, double* diag, int* bad) {
+                          double b_const, int n, int periodic, double* cpl, double* diag,
+                          int* bad) {
   const int64_t N = (int64_t)n * n * n;
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N) return;
   const int x[3] = {(int)(j % n), (int)((j / n) % n), (int)(j / ((int64_t)n * n))};
   const int64_t stride[3] = {1, n, (int64_t)n * n};
-  const double h = 1.0 / (n + 1);
+  const double h = periodic ? 1.0 / n : 1.0 / (n + 1);
   const double ih2 = 1.0 / (h * h);
   const double aj = a[j];
   const double bj = b ? b[j] : b_const;
-  if (!(aj > 0.0) || !isfinite(aj) || !(bj >= 0.0) || !isfinite(bj)) atomicExch(bad, 1);
+  if (!(aj > 0.0) || !isfinite(aj) || !(bj >= 0.0) || !isfinite(bj) || (periodic && !(bj > 0.0)))
+    atomicExch(bad, 1);
   double s = 0.0;
   for (int d = 0; d < 3; ++d) {
-    const double cm = x[d] > 0 ? harmonic(a[j - stride[d]], aj) : aj;
-    const double cp = x[d] + 1 < n ? harmonic(aj, a[j + stride[d]]) : aj;
+    double cm, cp;
+    if (periodic) {
+      const int64_t jm = x[d] > 0 ? j - stride[d] : j + (int64_t)(n - 1) * stride[d];
+      const int64_t jp = x[d] + 1 < n ? j + stride[d] : j - (int64_t)(n - 1) * stride[d];
+      cm = harmonic(a[jm], aj);
+      cp = harmonic(aj, a[jp]);
+      cpl[d * N + j] = cp * ih2;
+    } else {
+      cm = x[d] > 0 ? harmonic(a[j - stride[d]], aj) : aj;
+      cp = x[d] + 1 < n ? harmonic(aj, a[j + stride[d]]) : aj;
+      cpl[d * N + j] = x[d] + 1 < n ? cp * ih2 : 0.0;
+    }
     s += cm + cp;
-    cpl[d * N + j] = x[d] + 1 < n ? cp * ih2 : 0.0;
   }
   diag[j] = s * ih2 + bj;
 }
 
-__device__ __forceinline__ int lowcell(int x, int s) {
+// The cell (coordinate along one dimension) that owns point x at cell side
+// s: a separator plane belongs to the cell below it (wrapping to the last
+// cell on the periodic grid, where plane 0 is a separator too).
+__device__ __forceinline__ int lowcell(int x, int s, int C, int periodic) {
+  if (periodic) return x % s == 0 ? (x / s + C - 1) % C : x / s;
   return (x != 0 && x % s == 0) ? x / s - 1 : x / s;
 }
 
+// The cell's closure is the box [s c, s (c+1)] per dimension (clipped to the
+// grid with a Dirichlet boundary, wrapping to plane 0 on the periodic grid);
+// points are addressed by their offset from the box's low corner.
 template <typename T>
 __global__ void k_assemble0(const CellDesc* __restrict__ cells, const int32_t* __restrict__ lists,
-                            int n, int s, const double* __restrict__ cpl,
+                            int n, int s, int periodic, const double* __restrict__ cpl,
                             const double* __restrict__ diag, T* Kar) {
   extern __shared__ int boxmap[];
   const CellDesc cd = cells[blockIdx.x];
   const int C = n / s;
   const int c[3] = {(int)(blockIdx.x % C), (int)((blockIdx.x / C) % C), (int)(blockIdx.x / (C * C))};
-  int lo[3], hi[3], B[3];
+  int lo[3], B[3];
   for (int d = 0; d < 3; ++d) {
     lo[d] = s * c[d];
-    hi[d] = min(s * (c[d] + 1), n - 1);
-    B[d] = hi[d] - lo[d] + 1;
+    B[d] = periodic ? s + 1 : min(s * (c[d] + 1), n - 1) - lo[d] + 1;
   }
   const int32_t* lst = lists + cd.list;
   const int64_t N = (int64_t)n * n * n;
   for (int a = threadIdx.x; a < cd.n; a += blockDim.x) {
     const int g = lst[a];
-    const int x0 = g % n, x1 = (g / n) % n, x2 = g / (n * n);
-    boxmap[(x0 - lo[0]) + B[0] * ((x1 - lo[1]) + B[1] * (x2 - lo[2]))] = a;
+    const int x[3] = {g % n, (g / n) % n, g / (n * n)};
+    int xl[3];
+    for (int d = 0; d < 3; ++d) xl[d] = (x[d] - lo[d] + n) % n;
+    boxmap[xl[0] + B[0] * (xl[1] + B[1] * xl[2])] = a;
   }
   __syncthreads();
   T* K = Kar + cd.K;
@@ -70,18 +92,21 @@ __global__ void k_assemble0(const CellDesc* __restrict__ cells, const int32_t* _
   for (int a = threadIdx.x; a < nc; a += blockDim.x) {
     const int g = lst[a];
     const int x[3] = {g % n, (g / n) % n, g / (n * n)};
+    int xl[3];
+    for (int d = 0; d < 3; ++d) xl[d] = (x[d] - lo[d] + n) % n;
     bool own = true;
-    for (int d = 0; d < 3; ++d) own = own && lowcell(x[d], s) == c[d];
+    for (int d = 0; d < 3; ++d) own = own && lowcell(x[d], s, C, periodic) == c[d];
     if (own) K[(int64_t)a + (int64_t)a * nc] = (T)diag[g];
     for (int d = 0; d < 3; ++d) {
-      if (x[d] + 1 > hi[d]) continue;
+      // the coupling of x with its +e_d neighbour, if the box holds both
+      if (xl[d] + 1 >= B[d]) continue;
       bool ownp = x[d] / s == c[d];
       for (int e = 0; e < 3; ++e)
-        if (e != d) ownp = ownp && lowcell(x[e], s) == c[e];
+        if (e != d) ownp = ownp && lowcell(x[e], s, C, periodic) == c[e];
       if (!ownp) continue;
-      int y[3] = {x[0], x[1], x[2]};
+      int y[3] = {xl[0], xl[1], xl[2]};
       y[d] += 1;
-      const int b = boxmap[(y[0] - lo[0]) + B[0] * ((y[1] - lo[1]) + B[1] * (y[2] - lo[2]))];
+      const int b = boxmap[y[0] + B[0] * (y[1] + B[1] * y[2])];
       const int hi_ = max(a, b), lo_ = min(a, b);
       K[(int64_t)hi_ + (int64_t)lo_ * nc] = (T)(-cpl[d * N + g]);
     }
@@ -232,24 +257,24 @@ __global__ void __launch_bounds__(256) k_skel_writeback(const SkelDesc* __restri
 
 }  // namespace
 
-void stencil_coefficients(const double* a, const double* b, double b_const, int n,
+void stencil_coefficients(const double* a, const double* b, double b_const, int n, int periodic,
                           double* cpl, double* diag, int* d_bad, cudaStream_t st) {
   const int64_t N = (int64_t)n * n * n;
   ProfScope ps("stencil_coefficients", st, 0.0, 8.0 * N * (b ? 6.0 : 5.0));
-  k_stencil<<<ceil_div(N, 256), 256, 0, st>>>(a, b, b_const, n, cpl, diag, d_bad);
+  k_stencil<<<ceil_div(N, 256), 256, 0, st>>>(a, b, b_const, n, periodic, cpl, diag, d_bad);
   HIF_CHECK_LAUNCH();
 }
 
 template <typename T>
 void assemble_level0(const CellDesc* d_cells, int ncell, const int32_t* lists, int n, int s,
-                     const double* cpl, const double* diag, T* Karena, int maxbox,
+                     int periodic, const double* cpl, const double* diag, T* Karena, int maxbox,
                      cudaStream_t st) {
   const size_t smem = (size_t)maxbox * sizeof(int);
   if (smem > 48 * 1024)
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_assemble0<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
   ProfScope ps("assemble_level0", st);
-  k_assemble0<T><<<ncell, 128, smem, st>>>(d_cells, lists, n, s, cpl, diag, Karena);
+  k_assemble0<T><<<ncell, 128, smem, st>>>(d_cells, lists, n, s, periodic, cpl, diag, Karena);
   HIF_CHECK_LAUNCH();
 }
 
@@ -319,7 +344,7 @@ void skel_writeback(const SkelDesc* d_f, const SkelDesc* h_f, int nf, int ncp,
 }
 
 #define HIF_INST(T)                                                                          \
-  template void assemble_level0<T>(const CellDesc*, int, const int32_t*, int, int,          \
+  template void assemble_level0<T>(const CellDesc*, int, const int32_t*, int, int, int,     \
                                    const double*, const double*, T*, int, cudaStream_t);    \
   template void merge_children<T>(const MergeDesc*, const MergeDesc*, int, const CellDesc*, \
                                   const int32_t*, const T*, T*, cudaStream_t);              \

@@ -14,14 +14,17 @@ struct CellDesc {
 };
 
 // Seven-point operator (§2.4): coupling to +e_d neighbours and diagonal.
-// cpl[d*N + j] = a_{j+e_d/2}/h^2 (0 on the last plane), diag[j] = sum/h^2 + b_j.
-void stencil_coefficients(const double* a, const double* b, double b_const, int n,
+// cpl[d*N + j] = a_{j+e_d/2}/h^2 (Dirichlet: 0 on the last plane; periodic:
+// the coupling to the first plane), diag[j] = sum/h^2 + b_j.  *d_bad is set
+// for a <= 0, b < 0 (b <= 0 when periodic) or non-finite values.
+void stencil_coefficients(const double* a, const double* b, double b_const, int n, int periodic,
                           double* cpl, double* diag, int* d_bad, cudaStream_t st);
 
 // Level-0 frontal matrices from the stencil (each coupling counted in exactly
 // one cell: the lowest cell whose closure holds both points).
 template <typename T>
 void assemble_level0(const CellDesc* d_cells, int ncell, const int32_t* lists, int n, int s,
+                     int periodic,
                      const double* cpl, const double* diag, T* Karena, int maxbox,
                      cudaStream_t st);
 

@@ -221,6 +221,7 @@ struct FactorBase {
   virtual void apply_in_scratch(const double* f_dev, double* u_dev, int nrhs, void* scratch,
                                 cudaStream_t st) = 0;
   int n = 0, m = 0, L = 0, precision = 0;
+  int bc = 0;                   // 0: zero Dirichlet, 1: periodic
   int device = -1;              // CUDA device holding every buffer of the factor
   double eps = 0;
   MemStats mem;
@@ -377,7 +378,7 @@ struct Factor : FactorBase {
 template <typename T>
 class Builder {
  public:
-  Builder(Factor<T>& F, cudaStream_t st) : F_(F), st_(st), sym_(F.n, F.m) {
+  Builder(Factor<T>& F, cudaStream_t st) : F_(F), st_(st), sym_(F.n, F.m, F.bc == 1) {
     tr_.st = st;
     retry_.growth = std::is_same<T, float>::value ? F.opt.retry_growth : 0.0;
     retry_.retried = &F.stats.retried_fronts;
@@ -481,12 +482,14 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
   DevBuf bad;
   bad.alloc_async(sizeof(int), &F_.mem, st_);
   HIF_CUDA_TRY(cudaMemsetAsync(bad.as<int>(), 0, sizeof(int), st_));
-  stencil_coefficients(a_dev, b_dev, b_const, n, F_.cpl.template as<double>(), F_.diag.template as<double>(),
+  stencil_coefficients(a_dev, b_dev, b_const, n, F_.bc, F_.cpl.template as<double>(), F_.diag.template as<double>(),
                        bad.as<int>(), st_);
   int hbad = 0;
   HIF_CUDA_TRY(cudaMemcpyAsync(&hbad, bad.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st_));
   HIF_CUDA_TRY(cudaStreamSynchronize(st_));
-  if (hbad) throw Error{HIF_ERR_INVALID_ARG, "a must be finite and > 0, b finite and >= 0"};
+  if (hbad)
+    throw Error{HIF_ERR_INVALID_ARG, F_.bc ? "a must be finite and > 0, b finite and > 0 (periodic grid)"
+                                           : "a must be finite and > 0, b finite and >= 0"};
   flags_.alloc_async(sizeof(int) * FLAG_COUNT, &F_.mem, st_);
   HIF_CUDA_TRY(cudaMemsetAsync(flags_.as<int>(), 0xff, sizeof(int) * FLAG_COUNT, st_));
 
@@ -527,7 +530,7 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
     if (level == 0) {
       HIF_CUDA_TRY(cudaMemsetAsync(Kar.as<T>(), 0, sizeof(T) * koff, st_));
       const int maxbox = (cp.s + 1) * (cp.s + 1) * (cp.s + 1);
-      assemble_level0<T>(cdesc_d.as<CellDesc>(), cp.ncell, lists_d.as<int32_t>(), n, cp.s,
+      assemble_level0<T>(cdesc_d.as<CellDesc>(), cp.ncell, lists_d.as<int32_t>(), n, cp.s, F_.bc,
                          F_.cpl.template as<double>(), F_.diag.template as<double>(), Kar.as<T>(), maxbox, st_);
     } else {
       DevBuf map_d, mdesc_d;
@@ -1061,7 +1064,7 @@ hif_status do_solve(FactorBase& F, const double* f, double* u, int nrhs, cudaStr
   bool all = std::all_of(done.begin(), done.end(), [](int x) { return x; });
   while (!all && k < maxit) {
     ++k;
-    matvec(cpl, dg, F.n, p, q, nrhs, st);
+    matvec(cpl, dg, F.n, F.bc, p, q, nrhs, st);
     hdots(p, q, tmp);
     for (int c = 0; c < nrhs; ++c) al[c] = done[c] || tmp[c] == 0 ? 0.0 : rz[c] / tmp[c];
     put(al);
@@ -1282,6 +1285,7 @@ void save_factor(const Factor<T>& F, FileOut& o) {
   o.put(F.L);
   o.put(F.precision);
   o.put(F.eps);
+  o.put(F.bc);
   o.put(F.opt);
   o.put(F.stats);
   o.put(F.work_stride);
@@ -1389,6 +1393,8 @@ void load_factor(Factor<T>& F, FileIn& in) {
   F.L = in.get<int>();
   F.precision = in.get<int>();
   F.eps = in.get<double>();
+  F.bc = in.get<int>();
+  if (F.bc != 0 && F.bc != 1) corrupt("boundary condition");
   F.opt = in.get<hif_options>();
   F.stats = in.get<hif_stats>();
   const int64_t stride_in_file = in.get<int64_t>();
@@ -1475,7 +1481,8 @@ hif_status hif_factor(const hif_grid* grid, const double* a, const double* b, do
   if (opt) o = *opt;
   const int n = grid->n, m = grid->m;
   const int L = hif::hif_num_levels(n, m);
-  if (grid->bc != 0) throw Error{HIF_ERR_INVALID_ARG, "only the zero Dirichlet boundary (bc = 0) is supported"};
+  if (grid->bc != 0 && grid->bc != 1)
+    throw Error{HIF_ERR_INVALID_ARG, "bc must be 0 (zero Dirichlet) or 1 (periodic)"};
   if (m < 2 || L < 0 || n > 1024)
     throw Error{HIF_ERR_INVALID_ARG, "need n = m 2^L with m >= 2 and n <= 1024"};
   if (!(o.eps >= 0.0) || !(o.eps < 1.0)) throw Error{HIF_ERR_INVALID_ARG, "eps must be in [0, 1)"};
@@ -1500,6 +1507,7 @@ hif_status hif_factor(const hif_grid* grid, const double* a, const double* b, do
     F->n = n;
     F->m = m;
     F->L = L;
+    F->bc = grid->bc;
     F->eps = o.eps;
     F->precision = o.precision;
     F->opt = o;
@@ -1593,7 +1601,8 @@ hif_status hif_residual(hif_handle h, const double* f, const double* u, double* 
   uin.set(u, N * nrhs, st);
   OutArray ro;
   ro.set(r, N * nrhs);
-  hif::residual(h->f->cpl.as<double>(), h->f->diag.as<double>(), h->f->n, fin.p, uin.p, ro.p, nrhs, st);
+  hif::residual(h->f->cpl.as<double>(), h->f->diag.as<double>(), h->f->n, h->f->bc, fin.p, uin.p,
+                ro.p, nrhs, st);
   ro.finish(st);
   HIF_CUDA_TRY(cudaStreamSynchronize(st));
   return HIF_OK;

@@ -56,24 +56,44 @@ __global__ void k_cout(const T* __restrict__ y, double* x, int64_t cnt) {
   if (i < cnt) x[i] = (double)y[i];
 }
 
-// y = A u (mode 0) or y = f - A u (mode 1)
+// y = A u (mode 0) or y = f - A u (mode 1).  Dirichlet: neighbours outside
+// the grid are zero; periodic: index arithmetic wraps around every dimension.
 __global__ void k_stencil_apply(const double* __restrict__ cpl, const double* __restrict__ diag,
-                                int n, const double* __restrict__ f, const double* __restrict__ u,
-                                double* out, int nrhs, int mode) {
+                                int n, int periodic, const double* __restrict__ f,
+                                const double* __restrict__ u, double* out, int nrhs, int mode) {
   const int64_t N = (int64_t)n * n * n;
   const int64_t j = (int64_t)blockIdx.x * VT + threadIdx.x;
   if (j >= N) return;
   const int x0 = (int)(j % n), x1 = (int)((j / n) % n), x2 = (int)(j / ((int64_t)n * n));
   const int64_t nn = (int64_t)n * n;
+  if (!periodic) {
+    for (int q = 0; q < nrhs; ++q) {
+      const double* uq = u + q * N;
+      double s = diag[j] * uq[j];
+      if (x0 + 1 < n) s -= cpl[j] * uq[j + 1];
+      if (x0 > 0) s -= cpl[j - 1] * uq[j - 1];
+      if (x1 + 1 < n) s -= cpl[N + j] * uq[j + n];
+      if (x1 > 0) s -= cpl[N + j - n] * uq[j - n];
+      if (x2 + 1 < n) s -= cpl[2 * N + j] * uq[j + nn];
+      if (x2 > 0) s -= cpl[2 * N + j - nn] * uq[j - nn];
+      out[q * N + j] = mode ? f[q * N + j] - s : s;
+    }
+    return;
+  }
+  // neighbour offsets with wrap-around
+  const int64_t p0 = x0 + 1 < n ? 1 : -(int64_t)(n - 1), m0 = x0 > 0 ? -1 : (int64_t)(n - 1);
+  const int64_t p1 = x1 + 1 < n ? n : -(int64_t)(n - 1) * n, m1 = x1 > 0 ? -n : (int64_t)(n - 1) * n;
+  const int64_t p2 = x2 + 1 < n ? nn : -(int64_t)(n - 1) * nn,
+                m2 = x2 > 0 ? -nn : (int64_t)(n - 1) * nn;
   for (int q = 0; q < nrhs; ++q) {
     const double* uq = u + q * N;
     double s = diag[j] * uq[j];
-    if (x0 + 1 < n) s -= cpl[j] * uq[j + 1];
-    if (x0 > 0) s -= cpl[j - 1] * uq[j - 1];
-    if (x1 + 1 < n) s -= cpl[N + j] * uq[j + n];
-    if (x1 > 0) s -= cpl[N + j - n] * uq[j - n];
-    if (x2 + 1 < n) s -= cpl[2 * N + j] * uq[j + nn];
-    if (x2 > 0) s -= cpl[2 * N + j - nn] * uq[j - nn];
+    s -= cpl[j] * uq[j + p0];
+    s -= cpl[j + m0] * uq[j + m0];
+    s -= cpl[N + j] * uq[j + p1];
+    s -= cpl[N + j + m1] * uq[j + m1];
+    s -= cpl[2 * N + j] * uq[j + p2];
+    s -= cpl[2 * N + j + m2] * uq[j + m2];
     out[q * N + j] = mode ? f[q * N + j] - s : s;
   }
 }
@@ -175,19 +195,19 @@ void vec_convert_out(const T* y, double* x, int64_t cnt, cudaStream_t st) {
   HIF_CHECK_LAUNCH();
 }
 
-void residual(const double* cpl, const double* diag, int n, const double* f, const double* u,
-              double* r, int nrhs, cudaStream_t st) {
+void residual(const double* cpl, const double* diag, int n, int periodic, const double* f,
+              const double* u, double* r, int nrhs, cudaStream_t st) {
   const int64_t N = (int64_t)n * n * n;
   ProfScope ps("residual", st, 14.0 * N * nrhs, 8.0 * N * (4.0 + 3.0 * nrhs));
-  k_stencil_apply<<<grid1(N), VT, 0, st>>>(cpl, diag, n, f, u, r, nrhs, 1);
+  k_stencil_apply<<<grid1(N), VT, 0, st>>>(cpl, diag, n, periodic, f, u, r, nrhs, 1);
   HIF_CHECK_LAUNCH();
 }
 
-void matvec(const double* cpl, const double* diag, int n, const double* p, double* q, int nrhs,
-            cudaStream_t st) {
+void matvec(const double* cpl, const double* diag, int n, int periodic, const double* p,
+            double* q, int nrhs, cudaStream_t st) {
   const int64_t N = (int64_t)n * n * n;
   ProfScope ps("spmv", st, 13.0 * N * nrhs, 8.0 * N * (4.0 + 2.0 * nrhs));
-  k_stencil_apply<<<grid1(N), VT, 0, st>>>(cpl, diag, n, nullptr, p, q, nrhs, 0);
+  k_stencil_apply<<<grid1(N), VT, 0, st>>>(cpl, diag, n, periodic, nullptr, p, q, nrhs, 0);
   HIF_CHECK_LAUNCH();
 }
 

@@ -24,12 +24,13 @@ void vec_convert_in(const double* x, T* y, int64_t cnt, cudaStream_t st);
 template <typename T>
 void vec_convert_out(const T* y, double* x, int64_t cnt, cudaStream_t st);
 
-// r = f - A u for nrhs columns of length n^3 (seven-point operator, double).
-void residual(const double* cpl, const double* diag, int n, const double* f, const double* u,
-              double* r, int nrhs, cudaStream_t st);
+// r = f - A u for nrhs columns of length n^3 (seven-point operator, double;
+// periodic: neighbours wrap around).
+void residual(const double* cpl, const double* diag, int n, int periodic, const double* f,
+              const double* u, double* r, int nrhs, cudaStream_t st);
 // q = A p
-void matvec(const double* cpl, const double* diag, int n, const double* p, double* q, int nrhs,
-            cudaStream_t st);
+void matvec(const double* cpl, const double* diag, int n, int periodic, const double* p,
+            double* q, int nrhs, cudaStream_t st);
 // out[c] = sum_i x[c*N + i] * y[c*N + i] for c < ncol; `part` holds
 // ncol * 1024 partial sums.
 void dots(const double* x, const double* y, int64_t N, int ncol, double* part, double* out,

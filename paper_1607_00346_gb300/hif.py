@@ -313,9 +313,10 @@ def load_factor(path: str) -> Handle:
 def factor(n: int, m: int, a, b=None, b_const: float = 0.0, eps: float = 1e-6,
            precision: int = PREC_FP64, pcg_tol: float = 1e-10, max_iter: int = 200,
            stream=None, tensor_cores: bool = True, use_graphs: bool = True,
-           retry_growth: float | None = None) -> Handle:
-    """hif_factor: a (and b) are n^3 float64 arrays, host or device."""
-    g = Grid(n, m, 0)
+           retry_growth: float | None = None, periodic: bool = False) -> Handle:
+    """hif_factor: a (and b) are n^3 float64 arrays, host or device.
+    periodic=True: the periodic grid (hif_grid.bc = 1), b > 0 required."""
+    g = Grid(n, m, 1 if periodic else 0)
     o = default_options(eps=eps, precision=precision, pcg_tol=pcg_tol, max_iter=max_iter,
                         tensor_cores=int(bool(tensor_cores)), use_graphs=int(bool(use_graphs)))
     if retry_growth is not None:

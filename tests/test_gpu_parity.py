@@ -272,7 +272,7 @@ def test_load_rejects_inconsistent_factor_files(H, tmp_path):
     h.save(str(path))
     raw = bytearray(path.read_bytes())
     head = 4 + 3 * 4                                   # magic, version, two struct sizes
-    scalars = 4 * 4 + 8                                # n, m, L, precision, eps
+    scalars = 4 * 4 + 8 + 4                            # n, m, L, precision, eps, bc
     ws_off = head + scalars + ctypes.sizeof(H.Options) + ctypes.sizeof(H.Stats)
     N = n ** 3
     stale = bytearray(raw)
