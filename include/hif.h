@@ -180,6 +180,40 @@ hif_status hif_residual(hif_handle h, const double* f, const double* u,
 hif_status hif_solve(hif_handle h, const double* f, double* u, int nrhs,
                      hif_stream stream, int* iters, double* relres);
 
+/*
+ * hif_apply_batch -- u_i = F_i^{-1} f_i for nh factors at once (a serving
+ * process holding factors of different grids answers their requests
+ * together; the paper has no counterpart).  The sweeps of all the factors
+ * run in shared launches: at each step every factor that has a stage there
+ * adds its gathers, mat-vecs and scatters to one launch per kind, the
+ * backward sweep aligned at each factor's last stage.  Every factor keeps
+ * its own work buffers and the arithmetic of its own apply, so u_i is bit
+ * for bit what hif_apply(h[i], f[i], u[i], nrhs[i]) gives.
+ *   h:     nh distinct handles of one precision, on the current device.
+ *   f, u:  arrays of nh pointers; f[i], u[i] hold nrhs[i] * n_i^3 doubles
+ *          (host or device, as for hif_apply).
+ * Errors: INVALID_ARG (nh < 1, NULL or repeated handles, mixed precision or
+ * device, nrhs < 1), OOM, CUDA.
+ */
+hif_status hif_apply_batch(const hif_handle* h, int nh, const double* const* f,
+                           double* const* u, const int* nrhs, hif_stream stream);
+
+/*
+ * hif_solve_batch -- hif_solve for nh factors at once: the conjugate
+ * gradients of all the systems advance in lockstep and every
+ * preconditioner application is one hif_apply_batch of the systems still
+ * iterating.  Each system's iteration is the one hif_solve runs (same
+ * kernels, same scalar arithmetic, its own pcg_tol and max_iter), so its
+ * u, iteration counts and residuals are bitwise those of hif_solve alone.
+ * iters and relres (host, optional) receive sum(nrhs) entries, the columns
+ * of the systems in order.
+ * Errors: as hif_apply_batch, and NO_CONVERGENCE if any column did not
+ * converge.
+ */
+hif_status hif_solve_batch(const hif_handle* h, int nh, const double* const* f,
+                           double* const* u, const int* nrhs, hif_stream stream, int* iters,
+                           double* relres);
+
 /* Per-factorization statistics, filled by hif_query_stats. */
 typedef struct {
   int n, m, levels, precision;

@@ -415,39 +415,40 @@ constexpr int GEMV_WARPS = 8;    // column classes per CTA (N form)
 // y = alpha M x (+ y): a CTA owns 128 rows; its 8 warps take the columns
 // c = w, w + 8, ... (each warp reads 128 contiguous rows of a column, 4 per
 // lane), and the 8 partial sums are added in warp order in shared memory,
-// so the result does not depend on timing.
+// so the result does not depend on timing.  x and y hold R right-hand sides
+// vs apart.  The same body serves one handle's ops (offsets from the
+// factor's arenas) and grouped ops of several handles (absolute pointers),
+// so a grouped apply is bitwise the handle's own.
 template <typename T, int R>
-__global__ void __launch_bounds__(GEMV_ROWS * 2) k_gemv_n(const GemvOp* __restrict__ ops,
-                                                          const T* __restrict__ Mar, T* work,
-                                                          int64_t vs) {
-  const GemvOp o = ops[blockIdx.y];
+__device__ __forceinline__ void gemv_n_body(const T* __restrict__ M, const T* xw, T* yw, int64_t vs,
+                                            int rows, int cols, int ld, int tri, float alpha,
+                                            int beta_one) {
   const int r0 = blockIdx.x * GEMV_ROWS;
-  if (r0 >= o.rows) return;
+  if (r0 >= rows) return;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const T* M = Mar + o.M;
   __shared__ T red[GEMV_WARPS][GEMV_ROWS];
   T acc[4][R];
 #pragma unroll
   for (int j = 0; j < 4; ++j)
 #pragma unroll
     for (int q = 0; q < R; ++q) acc[j][q] = T(0);
-  const int cend = o.tri ? min(o.cols, r0 + GEMV_ROWS) : o.cols;
+  const int cend = tri ? min(cols, r0 + GEMV_ROWS) : cols;
   for (int c = warp; c < cend; c += GEMV_WARPS) {
     T xv[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) xv[q] = work[o.x + q * vs + c];
-    const T* mc = M + (int64_t)c * o.ld;
+    for (int q = 0; q < R; ++q) xv[q] = xw[q * vs + c];
+    const T* mc = M + (int64_t)c * ld;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int r = r0 + lane + 32 * j;
-      if (r < o.rows && (!o.tri || c <= r)) {
+      if (r < rows && (!tri || c <= r)) {
         const T mv = mc[r];
 #pragma unroll
         for (int q = 0; q < R; ++q) acc[j][q] = fma(mv, xv[q], acc[j][q]);
       }
     }
   }
-  const T al = (T)o.alpha;
+  const T al = (T)alpha;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
 #pragma unroll
@@ -458,30 +459,32 @@ __global__ void __launch_bounds__(GEMV_ROWS * 2) k_gemv_n(const GemvOp* __restri
       T s = red[0][threadIdx.x];
 #pragma unroll
       for (int w = 1; w < GEMV_WARPS; ++w) s += red[w][threadIdx.x];
-      if (r < o.rows) {
-        T* yp = &work[o.y + q * vs + r];
-        *yp = (o.beta_one ? *yp : T(0)) + al * s;
+      if (r < rows) {
+        T* yp = &yw[q * vs + r];
+        *yp = (beta_one ? *yp : T(0)) + al * s;
       }
     }
     __syncthreads();
   }
 }
 
+// y = alpha M^T x (+ y): one warp per output column, lanes stride the rows,
+// butterfly reduction.
 template <typename T, int R>
-__global__ void __launch_bounds__(256) k_gemv_t(const GemvOp* __restrict__ ops,
-                                                const T* __restrict__ Mar, T* work, int64_t vs) {
-  const GemvOp o = ops[blockIdx.y];
+__device__ __forceinline__ void gemv_t_body(const T* __restrict__ M, const T* xw, T* yw, int64_t vs,
+                                            int rows, int cols, int ld, int tri, float alpha,
+                                            int beta_one) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int c = blockIdx.x * 8 + warp;
-  if (c >= o.cols) return;
-  const T* M = Mar + o.M + (int64_t)c * o.ld;
+  if (c >= cols) return;
+  const T* Mc = M + (int64_t)c * ld;
   T acc[R];
 #pragma unroll
   for (int q = 0; q < R; ++q) acc[q] = T(0);
-  for (int r = (o.tri ? c : 0) + lane; r < o.rows; r += 32) {
-    const T mv = M[r];
+  for (int r = (tri ? c : 0) + lane; r < rows; r += 32) {
+    const T mv = Mc[r];
 #pragma unroll
-    for (int q = 0; q < R; ++q) acc[q] = fma(mv, work[o.x + q * vs + r], acc[q]);
+    for (int q = 0; q < R; ++q) acc[q] = fma(mv, xw[q * vs + r], acc[q]);
   }
 #pragma unroll
   for (int q = 0; q < R; ++q) {
@@ -490,13 +493,60 @@ __global__ void __launch_bounds__(256) k_gemv_t(const GemvOp* __restrict__ ops,
     acc[q] = v;
   }
   if (lane == 0) {
-    const T al = (T)o.alpha;
+    const T al = (T)alpha;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      T* yp = &work[o.y + q * vs + c];
-      *yp = (o.beta_one ? *yp : T(0)) + al * acc[q];
+      T* yp = &yw[q * vs + c];
+      *yp = (beta_one ? *yp : T(0)) + al * acc[q];
     }
   }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(GEMV_ROWS * 2) k_gemv_n(const GemvOp* __restrict__ ops,
+                                                          const T* __restrict__ Mar, T* work,
+                                                          int64_t vs) {
+  const GemvOp o = ops[blockIdx.y];
+  gemv_n_body<T, R>(Mar + o.M, work + o.x, work + o.y, vs, o.rows, o.cols, o.ld, o.tri, o.alpha,
+                    o.beta_one);
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_gemv_t(const GemvOp* __restrict__ ops,
+                                                const T* __restrict__ Mar, T* work, int64_t vs) {
+  const GemvOp o = ops[blockIdx.y];
+  gemv_t_body<T, R>(Mar + o.M, work + o.x, work + o.y, vs, o.rows, o.cols, o.ld, o.tri, o.alpha,
+                    o.beta_one);
+}
+
+// Grouped launches: blockIdx.y (plus y0) runs op j of the launch, which is op
+// j - first of the segment that holds it (one factor's mat-vec list for one
+// block of right-hand sides).
+template <typename T>
+__device__ __forceinline__ const GemvSeg<T>& find_seg(const GemvSeg<T>* segs, int nseg, int64_t j) {
+  int k = 0;
+  while (k + 1 < nseg && segs[k + 1].first <= j) ++k;
+  return segs[k];
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(GEMV_ROWS * 2) k_gemv_n_seg(const GemvSeg<T>* __restrict__ segs,
+                                                              int nseg, int64_t y0) {
+  const int64_t j = y0 + blockIdx.y;
+  const GemvSeg<T> sg = find_seg(segs, nseg, j);
+  const GemvOp o = sg.ops[j - sg.first];
+  gemv_n_body<T, R>(sg.M + o.M, sg.w + o.x, sg.w + o.y, sg.vs, o.rows, o.cols, o.ld, o.tri,
+                    o.alpha, o.beta_one);
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_gemv_t_seg(const GemvSeg<T>* __restrict__ segs, int nseg,
+                                                    int64_t y0) {
+  const int64_t j = y0 + blockIdx.y;
+  const GemvSeg<T> sg = find_seg(segs, nseg, j);
+  const GemvOp o = sg.ops[j - sg.first];
+  gemv_t_body<T, R>(sg.M + o.M, sg.w + o.x, sg.w + o.y, sg.vs, o.rows, o.cols, o.ld, o.tri,
+                    o.alpha, o.beta_one);
 }
 
 }  // namespace
@@ -883,13 +933,51 @@ void gemv_batched(const GemvOp* d_ops, const GemvOp* h_ops, int nops, int trans,
   }
 }
 
+template <typename T>
+void gemv_segments(const GemvSeg<T>* d_segs, int nseg, int64_t nops, int mx, int trans, int R,
+                   double flops, double bytes, cudaStream_t st) {
+  if (nops == 0) return;
+  ProfScope ps(trans ? "apply_grouped_gemv_t" : "apply_grouped_gemv_n", st, flops, bytes);
+  for (int64_t f0 = 0; f0 < nops; f0 += MAX_GRID_Y) {
+    const dim3 grid(std::max(1, mx), (unsigned)std::min<int64_t>(MAX_GRID_Y, nops - f0));
+    if (trans) {
+      switch (R) {
+        case 16: k_gemv_t_seg<T, 16><<<grid, 256, 0, st>>>(d_segs, nseg, f0); break;
+        case 8: k_gemv_t_seg<T, 8><<<grid, 256, 0, st>>>(d_segs, nseg, f0); break;
+        case 4: k_gemv_t_seg<T, 4><<<grid, 256, 0, st>>>(d_segs, nseg, f0); break;
+        case 2: k_gemv_t_seg<T, 2><<<grid, 256, 0, st>>>(d_segs, nseg, f0); break;
+        default: k_gemv_t_seg<T, 1><<<grid, 256, 0, st>>>(d_segs, nseg, f0);
+      }
+    } else {
+      constexpr int TH = GEMV_ROWS * 2;
+      switch (R) {
+        case 16: k_gemv_n_seg<T, 16><<<grid, TH, 0, st>>>(d_segs, nseg, f0); break;
+        case 8: k_gemv_n_seg<T, 8><<<grid, TH, 0, st>>>(d_segs, nseg, f0); break;
+        case 4: k_gemv_n_seg<T, 4><<<grid, TH, 0, st>>>(d_segs, nseg, f0); break;
+        case 2: k_gemv_n_seg<T, 2><<<grid, TH, 0, st>>>(d_segs, nseg, f0); break;
+        default: k_gemv_n_seg<T, 1><<<grid, TH, 0, st>>>(d_segs, nseg, f0);
+      }
+    }
+    HIF_CHECK_LAUNCH();
+  }
+}
+
+int gemv_tiles(const GemvOp* h_ops, int nops, int trans) {
+  int mx = 1;
+  for (int i = 0; i < nops; ++i)
+    mx = std::max(mx, trans ? ceil_div(h_ops[i].cols, 8) : ceil_div(h_ops[i].rows, GEMV_ROWS));
+  return mx;
+}
+
 #define HIF_INST(T)                                                                          \
   template void partial_cholesky<T>(const DFront*, const DFront*, int, T*, T*, int*, bool,  \
                                     cudaStream_t, const RetryOpts*);                         \
   template void gemm_batched<T>(const GemmOp*, const GemmOp*, int, const T*, const T*, T*,  \
                                 cudaStream_t, const char*);                                  \
   template void gemv_batched<T>(const GemvOp*, const GemvOp*, int, int, const T*, T*,       \
-                                int64_t, int, cudaStream_t);
+                                int64_t, int, cudaStream_t);                                 \
+  template void gemv_segments<T>(const GemvSeg<T>*, int, int64_t, int, int, int, double,     \
+                                 double, cudaStream_t);
 HIF_INST(float)
 HIF_INST(double)
 #undef HIF_INST

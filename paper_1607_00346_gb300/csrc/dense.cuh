@@ -48,4 +48,28 @@ template <typename T>
 void gemv_batched(const GemvOp* d_ops, const GemvOp* h_ops, int nops, int trans,
                   const T* Marena, T* work, int64_t vstride, int nrhs, cudaStream_t st);
 
+// Grouped apply: one launch runs the mat-vec lists of several factors (one
+// segment per factor's list and block of right-hand sides).  Segment k owns
+// ops first_k .. first_{k+1}-1 of the launch; op j reads ops[j - first] of
+// its device list, its matrix at M + op.M and its vectors at w + op.x,
+// w + op.y (w already shifted to the block's first column, vs apart).
+template <typename T>
+struct GemvSeg {
+  const GemvOp* ops;
+  const T* M;
+  T* w;
+  int64_t vs;
+  int64_t first;
+};
+
+// gemv_batched over the segments (trans as there, R right-hand sides per op:
+// 16, 8, 4, 2 or 1; nops = all ops of the launch; mx = the widest op's row
+// tiles (trans 0) or column groups (trans 1), from gemv_tiles).  Per op the
+// arithmetic is gemv_batched's, so a grouped apply is bitwise the factor's
+// own apply.
+template <typename T>
+void gemv_segments(const GemvSeg<T>* d_segs, int nseg, int64_t nops, int mx, int trans, int R,
+                   double flops, double bytes, cudaStream_t st);
+int gemv_tiles(const GemvOp* h_ops, int nops, int trans);
+
 }  // namespace hif

@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <future>
 #include <memory>
 #include <mutex>
@@ -195,6 +196,11 @@ struct GemvList {
   DevBuf d;
   int trans = 0;
   int mat = 0;   // 0: panel arena, 1: interpolation-matrix arena
+  int tiles = -1;   // widest op's CTA count along x (cached for grouped launches)
+  int get_tiles() {
+    if (tiles < 0) tiles = gemv_tiles(h.data(), (int)h.size(), trans);
+    return tiles;
+  }
 };
 
 struct Stage {
@@ -335,7 +341,9 @@ struct Factor : FactorBase {
                         s.nacc, yv, ys, w, vs, nrhs, st);
   }
 
-  void apply(const double* f_dev, double* u_dev, int nrhs, cudaStream_t st) override {
+  // the apply's vectors for nrhs right-hand sides (grown on demand; the
+  // captured graphs name them, so they are dropped when the buffers grow)
+  void ensure_apply_buffers(int nrhs) {
     const int64_t N = (int64_t)n * n * n;
     if (y_cap < N * nrhs) {
       drop_graphs();
@@ -347,6 +355,11 @@ struct Factor : FactorBase {
       work.alloc(sizeof(T) * std::max<int64_t>(1, work_stride * nrhs), &mem);
       work_cap = work_stride * nrhs;
     }
+  }
+
+  void apply(const double* f_dev, double* u_dev, int nrhs, cudaStream_t st) override {
+    const int64_t N = (int64_t)n * n * n;
+    ensure_apply_buffers(nrhs);
     T* yv = y.as<T>();
     T* w = work.as<T>();
     vec_convert_in<T>(f_dev, yv, N * nrhs, st);
@@ -372,6 +385,177 @@ struct Factor : FactorBase {
     vec_convert_out<T>(yv, u_dev, N * nrhs, st);
   }
 };
+
+// ---- grouped apply over several factors --------------------------------------
+// The sweeps of several factors of one precision run in shared launches.  At
+// step t of the forward sweep every factor that has a stage t contributes
+// its gather, its mat-vec lists, its set and its accumulate to one launch
+// each (a mat-vec list: one launch per transpose form and block size of
+// right-hand sides); the backward sweep aligns the factors' stages from the
+// last one.  Each factor keeps its own buffers and its own kernels'
+// arithmetic, so its result is bitwise that of its own apply.
+template <typename T>
+void grouped_sweeps(const std::vector<Factor<T>*>& Fs, const std::vector<int>& nrhs,
+                    cudaStream_t st) {
+  struct Launch {
+    int kind;              // 0 gather, 1 set, 2 accumulate, 3 mat-vec
+    int trans, R, count;   // count: jobs or segments
+    size_t off;            // byte offset of the descriptors in the upload
+    int64_t nops;
+    int mx;
+    double fl, by;
+  };
+  std::vector<unsigned char> blob;
+  std::vector<Launch> seq;
+  auto push = [&](const void* p, size_t bytes) {
+    const size_t off = (blob.size() + 255) / 256 * 256;
+    blob.resize(off + bytes);
+    std::memcpy(blob.data() + off, p, bytes);
+    return off;
+  };
+  const int nh = (int)Fs.size();
+  std::vector<T*> yv(nh), wv(nh);
+  std::vector<int64_t> ys(nh), vs(nh);
+  std::vector<std::vector<std::pair<int, int>>> blocks(nh);   // (first column, R)
+  size_t S = 0;
+  for (int h = 0; h < nh; ++h) {
+    yv[h] = Fs[h]->y.template as<T>();
+    wv[h] = Fs[h]->work.template as<T>();
+    ys[h] = (int64_t)Fs[h]->n * Fs[h]->n * Fs[h]->n;
+    vs[h] = Fs[h]->work_stride;
+    for (int q0 = 0; q0 < nrhs[h];) {
+      const int left = nrhs[h] - q0;
+      const int R = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+      blocks[h].push_back({q0, R});
+      q0 += R;
+    }
+    S = std::max(S, Fs[h]->stages.size());
+  }
+  const bool prof = prof_enabled();
+  for (int dir = 0; dir < 2; ++dir) {
+    for (size_t t = 0; t < S; ++t) {
+      std::vector<std::pair<int, Stage*>> at;
+      for (int h = 0; h < nh; ++h) {
+        const size_t sh = Fs[h]->stages.size();
+        if (t < sh) at.push_back({h, &Fs[h]->stages[dir == 0 ? t : sh - 1 - t]});
+      }
+      auto vec_launch = [&](int kind) {
+        std::vector<VecJob<T>> jobs;
+        for (auto& [h, st_] : at) {
+          VecJob<T> j{};
+          j.y = yv[h];
+          j.ys = ys[h];
+          j.w = wv[h];
+          j.vs = vs[h];
+          j.nrhs = nrhs[h];
+          if (kind == 0) {
+            j.a = st_->idx.template as<int32_t>();
+            j.cnt = st_->nidx;
+          } else if (kind == 1) {
+            j.a = st_->set_g.template as<int32_t>();
+            j.b = st_->set_p.template as<int32_t>();
+            j.cnt = st_->nset;
+          } else {
+            j.a = st_->acc_tgt.template as<int32_t>();
+            j.b = st_->acc_src.template as<int32_t>();
+            j.ptr = st_->acc_ptr.template as<int64_t>();
+            j.cnt = st_->nacc;
+          }
+          if (j.cnt) jobs.push_back(j);
+        }
+        if (jobs.empty()) return;
+        Launch l{kind, 0, 0, (int)jobs.size(), push(jobs.data(), sizeof(VecJob<T>) * jobs.size()),
+                 0, 0, 0.0, 0.0};
+        seq.push_back(l);
+      };
+      vec_launch(0);
+      size_t nl = 0;
+      for (auto& [h, st_] : at) nl = std::max(nl, (dir ? st_->bwd : st_->fwd).size());
+      for (size_t i = 0; i < nl; ++i) {
+        std::map<std::pair<int, int>, std::vector<GemvSeg<T>>> buckets;
+        std::map<std::pair<int, int>, Launch> meta;
+        for (auto& [h, st_] : at) {
+          auto& lists = dir ? st_->bwd : st_->fwd;
+          if (i >= lists.size() || lists[i].h.empty()) continue;
+          GemvList& gl = lists[i];
+          const T* M = gl.mat ? st_->tmats.template as<T>() : st_->panels.template as<T>();
+          double ent = 0.0, vecs = 0.0;
+          if (prof)
+            for (const GemvOp& o : gl.h) {
+              ent += o.tri ? 0.5 * (double)o.cols * (o.cols + 1) : (double)o.rows * o.cols;
+              vecs += (double)(o.rows + o.cols) * (o.beta_one ? 1.5 : 1.0);
+            }
+          for (auto [q0, R] : blocks[h]) {
+            const auto key = std::make_pair(gl.trans, R);
+            Launch& l = meta[key];
+            l.kind = 3;
+            l.trans = gl.trans;
+            l.R = R;
+            buckets[key].push_back(
+                GemvSeg<T>{gl.d.as<GemvOp>(), M, wv[h] + (int64_t)q0 * vs[h], vs[h], l.nops});
+            l.nops += (int64_t)gl.h.size();
+            l.mx = std::max(l.mx, gl.get_tiles());
+            l.fl += 2.0 * ent * R;
+            l.by += sizeof(T) * (ent + R * vecs);
+          }
+        }
+        for (auto& [key, segs] : buckets) {
+          Launch l = meta[key];
+          l.count = (int)segs.size();
+          l.off = push(segs.data(), sizeof(GemvSeg<T>) * segs.size());
+          seq.push_back(l);
+        }
+      }
+      vec_launch(1);
+      if (dir == 0) vec_launch(2);
+    }
+  }
+  if (seq.empty()) return;
+  DevBuf d;
+  d.alloc_async(blob.size(), nullptr, st);
+  HIF_CUDA_TRY(cudaMemcpyAsync(d.as<void>(), blob.data(), blob.size(), cudaMemcpyHostToDevice, st));
+  const unsigned char* base = d.as<unsigned char>();
+  for (const Launch& l : seq) {
+    if (l.kind == 3) {
+      gemv_segments<T>(reinterpret_cast<const GemvSeg<T>*>(base + l.off), l.count, l.nops, l.mx,
+                       l.trans, l.R, l.fl, l.by, st);
+    } else {
+      vec_grouped<T>(l.kind, reinterpret_cast<const VecJob<T>*>(base + l.off),
+                     reinterpret_cast<const VecJob<T>*>(blob.data() + l.off), l.count, st);
+    }
+  }
+}
+
+// u_h = F_h^{-1} f_h for several factors of one precision, sweeps grouped.
+template <typename T>
+void grouped_apply(const std::vector<Factor<T>*>& Fs, const std::vector<const double*>& f,
+                   const std::vector<double*>& u, const std::vector<int>& nrhs, cudaStream_t st) {
+  for (size_t h = 0; h < Fs.size(); ++h) {
+    Fs[h]->ensure_apply_buffers(nrhs[h]);
+    const int64_t N = (int64_t)Fs[h]->n * Fs[h]->n * Fs[h]->n;
+    vec_convert_in<T>(f[h], Fs[h]->y.template as<T>(), N * nrhs[h], st);
+  }
+  grouped_sweeps<T>(Fs, nrhs, st);
+  for (size_t h = 0; h < Fs.size(); ++h) {
+    const int64_t N = (int64_t)Fs[h]->n * Fs[h]->n * Fs[h]->n;
+    vec_convert_out<T>(Fs[h]->y.template as<T>(), u[h], N * nrhs[h], st);
+  }
+}
+
+void grouped_apply_any(const std::vector<FactorBase*>& Fs, const std::vector<const double*>& f,
+                       const std::vector<double*>& u, const std::vector<int>& nrhs,
+                       cudaStream_t st) {
+  if (Fs.empty()) return;
+  if (Fs[0]->precision == HIF_PREC_FP32) {
+    std::vector<Factor<float>*> v;
+    for (FactorBase* F : Fs) v.push_back(static_cast<Factor<float>*>(F));
+    grouped_apply<float>(v, f, u, nrhs, st);
+  } else {
+    std::vector<Factor<double>*> v;
+    for (FactorBase* F : Fs) v.push_back(static_cast<Factor<double>*>(F));
+    grouped_apply<double>(v, f, u, nrhs, st);
+  }
+}
 
 // ---- the factorization ---------------------------------------------------------
 
@@ -1020,86 +1204,159 @@ struct SolveBufs {
   DevBuf r, z, p, q, rold, part, dots, scal;
 };
 
-hif_status do_solve(FactorBase& F, const double* f, double* u, int nrhs, cudaStream_t st,
-                    int* iters, double* relres) {
-  const int64_t N = (int64_t)F.n * F.n * F.n;
+// One factor's system in a PCG run: its right-hand sides f (nrhs columns),
+// solution u, work vectors and the per-column state of the iteration.
+struct PcgItem {
+  FactorBase* F = nullptr;
+  const double* f = nullptr;
+  double* u = nullptr;
+  int nrhs = 0;
   SolveBufs b;
-  MemStats* ms = &F.mem;
-  for (DevBuf* x : {&b.r, &b.z, &b.p, &b.q, &b.rold}) x->alloc(sizeof(double) * N * nrhs, ms);
-  b.part.alloc(sizeof(double) * 1024 * nrhs, ms);
-  b.dots.alloc(sizeof(double) * 2 * nrhs, ms);
-  b.scal.alloc(sizeof(double) * nrhs, ms);
-  const double* cpl = F.cpl.as<double>();
-  const double* dg = F.diag.as<double>();
-  std::vector<double> fn(nrhs), rz(nrhs), tmp(nrhs), tmp2(nrhs), al(nrhs), be(nrhs), rel(nrhs);
-  std::vector<int> it(nrhs, 0), done(nrhs, 0);
-  auto hdots = [&](const double* x, const double* y, std::vector<double>& out) {
-    dots(x, y, N, nrhs, b.part.as<double>(), b.dots.as<double>(), st);
-    HIF_CUDA_TRY(cudaMemcpyAsync(out.data(), b.dots.as<double>(), sizeof(double) * nrhs,
+  std::vector<double> fn, rz, tmp, tmp2, al, be, rel;
+  std::vector<int> it, done;
+  bool all = false;
+};
+
+// z = F^{-1} r for the listed items (their b.r into b.z).
+using PcgApply = std::function<void(const std::vector<PcgItem*>&, cudaStream_t)>;
+
+// Preconditioned conjugate gradients for several systems in lockstep
+// (Polak-Ribiere beta; FP64 residual with the seven-point operator).  Every
+// item runs exactly the kernels and the scalar arithmetic it would run alone:
+// the items only share the host waits and, through `apply`, the launches of
+// the preconditioner.  An item stops when all its columns reached its
+// pcg_tol or after its max_iter iterations.  Returns HIF_OK if every column
+// converged.
+hif_status pcg_many(std::vector<PcgItem>& items, cudaStream_t st, const PcgApply& apply) {
+  for (PcgItem& I : items) {
+    const int64_t N = (int64_t)I.F->n * I.F->n * I.F->n;
+    MemStats* ms = &I.F->mem;
+    for (DevBuf* x : {&I.b.r, &I.b.z, &I.b.p, &I.b.q, &I.b.rold}) x->alloc(sizeof(double) * N * I.nrhs, ms);
+    I.b.part.alloc(sizeof(double) * 1024 * I.nrhs, ms);
+    I.b.dots.alloc(sizeof(double) * 2 * I.nrhs, ms);
+    I.b.scal.alloc(sizeof(double) * I.nrhs, ms);
+    for (auto* v : {&I.fn, &I.rz, &I.tmp, &I.tmp2, &I.al, &I.be, &I.rel}) v->assign(I.nrhs, 0.0);
+    I.it.assign(I.nrhs, 0);
+    I.done.assign(I.nrhs, 0);
+  }
+  auto N_of = [](const PcgItem& I) { return (int64_t)I.F->n * I.F->n * I.F->n; };
+  // out[c] = x_c . y_c for each column (queued; read after the next wait)
+  auto qdots = [&](PcgItem& I, const double* x, const double* y, std::vector<double>& out) {
+    dots(x, y, N_of(I), I.nrhs, I.b.part.as<double>(), I.b.dots.as<double>(), st);
+    HIF_CUDA_TRY(cudaMemcpyAsync(out.data(), I.b.dots.as<double>(), sizeof(double) * I.nrhs,
                                  cudaMemcpyDeviceToHost, st));
-    HIF_CUDA_TRY(cudaStreamSynchronize(st));
   };
-  auto put = [&](const std::vector<double>& v) {
-    HIF_CUDA_TRY(cudaMemcpyAsync(b.scal.as<double>(), v.data(), sizeof(double) * nrhs,
+  auto wait = [&]() { HIF_CUDA_TRY(cudaStreamSynchronize(st)); };
+  auto put = [&](PcgItem& I, const std::vector<double>& v) {
+    HIF_CUDA_TRY(cudaMemcpyAsync(I.b.scal.as<double>(), v.data(), sizeof(double) * I.nrhs,
                                  cudaMemcpyHostToDevice, st));
   };
-  double* r = b.r.as<double>();
-  double* z = b.z.as<double>();
-  double* p = b.p.as<double>();
-  double* q = b.q.as<double>();
-  HIF_CUDA_TRY(cudaMemsetAsync(u, 0, sizeof(double) * N * nrhs, st));
-  HIF_CUDA_TRY(cudaMemcpyAsync(r, f, sizeof(double) * N * nrhs, cudaMemcpyDeviceToDevice, st));
-  hdots(r, r, fn);
-  for (int c = 0; c < nrhs; ++c) {
-    fn[c] = std::sqrt(fn[c]);
-    rel[c] = fn[c] > 0 ? 1.0 : 0.0;
-    if (fn[c] == 0) done[c] = 1;
-  }
-  F.apply(r, z, nrhs, st);
-  HIF_CUDA_TRY(cudaMemcpyAsync(p, z, sizeof(double) * N * nrhs, cudaMemcpyDeviceToDevice, st));
-  hdots(r, z, rz);
-  const double tol = F.opt.pcg_tol;
-  const int maxit = F.opt.max_iter;
-  int k = 0;
-  bool all = std::all_of(done.begin(), done.end(), [](int x) { return x; });
-  while (!all && k < maxit) {
-    ++k;
-    matvec(cpl, dg, F.n, F.bc, p, q, nrhs, st);
-    hdots(p, q, tmp);
-    for (int c = 0; c < nrhs; ++c) al[c] = done[c] || tmp[c] == 0 ? 0.0 : rz[c] / tmp[c];
-    put(al);
-    axpy_cols(b.scal.as<double>(), 1.0, p, u, N, nrhs, st);
-    HIF_CUDA_TRY(cudaMemcpyAsync(b.rold.as<double>(), r, sizeof(double) * N * nrhs,
+  auto all_of = [](const std::vector<int>& d) {
+    return std::all_of(d.begin(), d.end(), [](int x) { return x; });
+  };
+  for (PcgItem& I : items) {
+    const int64_t N = N_of(I);
+    HIF_CUDA_TRY(cudaMemsetAsync(I.u, 0, sizeof(double) * N * I.nrhs, st));
+    HIF_CUDA_TRY(cudaMemcpyAsync(I.b.r.as<double>(), I.f, sizeof(double) * N * I.nrhs,
                                  cudaMemcpyDeviceToDevice, st));
-    axpy_cols(b.scal.as<double>(), -1.0, q, r, N, nrhs, st);
-    hdots(r, r, tmp);
-    for (int c = 0; c < nrhs; ++c) {
-      if (done[c]) continue;
-      rel[c] = std::sqrt(tmp[c]) / fn[c];
-      it[c] = k;
-      if (rel[c] <= tol) done[c] = 1;
-    }
-    all = std::all_of(done.begin(), done.end(), [](int x) { return x; });
-    if (all) break;
-    F.apply(r, z, nrhs, st);
-    hdots(r, z, tmp);       // r_new . z
-    hdots(b.rold.as<double>(), z, tmp2);   // r_old . z
-    for (int c = 0; c < nrhs; ++c) {
-      be[c] = done[c] || rz[c] == 0 ? 0.0 : (tmp[c] - tmp2[c]) / rz[c];   // Polak-Ribiere
-      if (!done[c]) rz[c] = tmp[c];
-    }
-    put(be);
-    xpby_cols(z, b.scal.as<double>(), p, N, nrhs, st);
-    // converged columns keep p = 0 so that later updates leave them alone
-    for (int c = 0; c < nrhs; ++c)
-      if (done[c]) HIF_CUDA_TRY(cudaMemsetAsync(p + c * N, 0, sizeof(double) * N, st));
+    qdots(I, I.b.r.as<double>(), I.b.r.as<double>(), I.fn);
   }
-  HIF_CUDA_TRY(cudaStreamSynchronize(st));
+  wait();
+  std::vector<PcgItem*> act;
+  for (PcgItem& I : items) {
+    for (int c = 0; c < I.nrhs; ++c) {
+      I.fn[c] = std::sqrt(I.fn[c]);
+      I.rel[c] = I.fn[c] > 0 ? 1.0 : 0.0;
+      if (I.fn[c] == 0) I.done[c] = 1;
+    }
+    act.push_back(&I);
+  }
+  apply(act, st);
+  for (PcgItem& I : items) {
+    HIF_CUDA_TRY(cudaMemcpyAsync(I.b.p.as<double>(), I.b.z.as<double>(),
+                                 sizeof(double) * N_of(I) * I.nrhs, cudaMemcpyDeviceToDevice, st));
+    qdots(I, I.b.r.as<double>(), I.b.z.as<double>(), I.rz);
+  }
+  wait();
+  for (PcgItem& I : items) I.all = all_of(I.done);
+  for (int k = 1;; ++k) {
+    // the items still iterating at this step
+    act.clear();
+    for (PcgItem& I : items)
+      if (!I.all && k <= I.F->opt.max_iter) act.push_back(&I);
+    if (act.empty()) break;
+    for (PcgItem* I : act) {
+      matvec(I->F->cpl.as<double>(), I->F->diag.as<double>(), I->F->n, I->F->bc,
+             I->b.p.as<double>(), I->b.q.as<double>(), I->nrhs, st);
+      qdots(*I, I->b.p.as<double>(), I->b.q.as<double>(), I->tmp);
+    }
+    wait();
+    for (PcgItem* I : act) {
+      const int64_t N = N_of(*I);
+      for (int c = 0; c < I->nrhs; ++c)
+        I->al[c] = I->done[c] || I->tmp[c] == 0 ? 0.0 : I->rz[c] / I->tmp[c];
+      put(*I, I->al);
+      double* r = I->b.r.as<double>();
+      axpy_cols(I->b.scal.as<double>(), 1.0, I->b.p.as<double>(), I->u, N, I->nrhs, st);
+      HIF_CUDA_TRY(cudaMemcpyAsync(I->b.rold.as<double>(), r, sizeof(double) * N * I->nrhs,
+                                   cudaMemcpyDeviceToDevice, st));
+      axpy_cols(I->b.scal.as<double>(), -1.0, I->b.q.as<double>(), r, N, I->nrhs, st);
+      qdots(*I, r, r, I->tmp);
+    }
+    wait();
+    std::vector<PcgItem*> next;
+    for (PcgItem* I : act) {
+      for (int c = 0; c < I->nrhs; ++c) {
+        if (I->done[c]) continue;
+        I->rel[c] = std::sqrt(I->tmp[c]) / I->fn[c];
+        I->it[c] = k;
+        if (I->rel[c] <= I->F->opt.pcg_tol) I->done[c] = 1;
+      }
+      I->all = all_of(I->done);
+      if (!I->all) next.push_back(I);
+    }
+    if (next.empty()) continue;
+    apply(next, st);
+    for (PcgItem* I : next) {
+      qdots(*I, I->b.r.as<double>(), I->b.z.as<double>(), I->tmp);       // r_new . z
+      qdots(*I, I->b.rold.as<double>(), I->b.z.as<double>(), I->tmp2);   // r_old . z
+    }
+    wait();
+    for (PcgItem* I : next) {
+      const int64_t N = N_of(*I);
+      for (int c = 0; c < I->nrhs; ++c) {
+        I->be[c] = I->done[c] || I->rz[c] == 0 ? 0.0 : (I->tmp[c] - I->tmp2[c]) / I->rz[c];   // Polak-Ribiere
+        if (!I->done[c]) I->rz[c] = I->tmp[c];
+      }
+      put(*I, I->be);
+      double* pp = I->b.p.as<double>();
+      xpby_cols(I->b.z.as<double>(), I->b.scal.as<double>(), pp, N, I->nrhs, st);
+      // converged columns keep p = 0 so that later updates leave them alone
+      for (int c = 0; c < I->nrhs; ++c)
+        if (I->done[c]) HIF_CUDA_TRY(cudaMemsetAsync(pp + c * N, 0, sizeof(double) * N, st));
+    }
+  }
+  wait();
+  bool ok = true;
+  for (PcgItem& I : items) ok = ok && I.all;
+  return ok ? HIF_OK : HIF_ERR_NO_CONVERGENCE;
+}
+
+hif_status do_solve(FactorBase& F, const double* f, double* u, int nrhs, cudaStream_t st,
+                    int* iters, double* relres) {
+  std::vector<PcgItem> items(1);
+  items[0].F = &F;
+  items[0].f = f;
+  items[0].u = u;
+  items[0].nrhs = nrhs;
+  const hif_status s = pcg_many(items, st, [](const std::vector<PcgItem*>& v, cudaStream_t s2) {
+    for (PcgItem* I : v) I->F->apply(I->b.r.as<double>(), I->b.z.as<double>(), I->nrhs, s2);
+  });
   for (int c = 0; c < nrhs; ++c) {
-    if (iters) iters[c] = it[c];
-    if (relres) relres[c] = rel[c];
+    if (iters) iters[c] = items[0].it[c];
+    if (relres) relres[c] = items[0].rel[c];
   }
-  return all ? HIF_OK : HIF_ERR_NO_CONVERGENCE;
+  return s;
 }
 
 }  // namespace
@@ -1621,6 +1878,101 @@ hif_status hif_solve(hif_handle h, const double* f, double* u, int nrhs, hif_str
   uo.set(u, N * nrhs);
   hif_status s = hif::do_solve(*h->f, fin.p, uo.p, nrhs, st, iters, relres);
   uo.finish(st);
+  if (s != HIF_OK) hif::set_last_error("PCG did not reach the tolerance within max_iter");
+  return s;
+  HIF_API_END
+}
+
+namespace {
+
+// Checks shared by the batch entry points; returns the factors.
+std::vector<hif::FactorBase*> batch_factors(const hif_handle* hs, int nh, const int* nrhs) {
+  if (!hs || nh < 1 || !nrhs) throw Error{HIF_ERR_INVALID_ARG, "need nh >= 1 handles and nrhs"};
+  std::vector<hif::FactorBase*> Fs;
+  for (int i = 0; i < nh; ++i) {
+    if (!hs[i] || nrhs[i] < 1) throw Error{HIF_ERR_INVALID_ARG, "bad handle or nrhs in the batch"};
+    hif::FactorBase* F = hs[i]->f.get();
+    if (std::find(Fs.begin(), Fs.end(), F) != Fs.end())
+      throw Error{HIF_ERR_INVALID_ARG, "a handle appears twice in the batch"};
+    if (!Fs.empty() && (F->precision != Fs[0]->precision || F->device != Fs[0]->device))
+      throw Error{HIF_ERR_INVALID_ARG, "the batch's factors must share precision and device"};
+    Fs.push_back(F);
+  }
+  return Fs;
+}
+
+}  // namespace
+
+hif_status hif_apply_batch(const hif_handle* hs, int nh, const double* const* f,
+                           double* const* u, const int* nrhs, hif_stream stream) {
+  HIF_API_BEGIN
+  std::vector<hif::FactorBase*> Fs = batch_factors(hs, nh, nrhs);
+  if (!f || !u) throw Error{HIF_ERR_INVALID_ARG, "f and u must not be NULL"};
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<InArray> fin(nh);
+  std::vector<OutArray> uo(nh);
+  std::vector<const double*> fp(nh);
+  std::vector<double*> up(nh);
+  std::vector<int> nr(nrhs, nrhs + nh);
+  for (int i = 0; i < nh; ++i) {
+    if (!f[i] || !u[i]) throw Error{HIF_ERR_INVALID_ARG, "f and u must not be NULL"};
+    const int64_t N = (int64_t)Fs[i]->n * Fs[i]->n * Fs[i]->n;
+    fin[i].set(f[i], N * nrhs[i], st);
+    uo[i].set(u[i], N * nrhs[i]);
+    fp[i] = fin[i].p;
+    up[i] = uo[i].p;
+  }
+  hif::grouped_apply_any(Fs, fp, up, nr, st);
+  bool staged = false;
+  for (int i = 0; i < nh; ++i) {
+    uo[i].finish(st);
+    staged = staged || fin[i].tmp.bytes();
+  }
+  if (staged) HIF_CUDA_TRY(cudaStreamSynchronize(st));
+  return HIF_OK;
+  HIF_API_END
+}
+
+hif_status hif_solve_batch(const hif_handle* hs, int nh, const double* const* f, double* const* u,
+                           const int* nrhs, hif_stream stream, int* iters, double* relres) {
+  HIF_API_BEGIN
+  std::vector<hif::FactorBase*> Fs = batch_factors(hs, nh, nrhs);
+  if (!f || !u) throw Error{HIF_ERR_INVALID_ARG, "f and u must not be NULL"};
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<InArray> fin(nh);
+  std::vector<OutArray> uo(nh);
+  std::vector<hif::PcgItem> items(nh);
+  for (int i = 0; i < nh; ++i) {
+    if (!f[i] || !u[i]) throw Error{HIF_ERR_INVALID_ARG, "f and u must not be NULL"};
+    const int64_t N = (int64_t)Fs[i]->n * Fs[i]->n * Fs[i]->n;
+    fin[i].set(f[i], N * nrhs[i], st);
+    uo[i].set(u[i], N * nrhs[i]);
+    items[i].F = Fs[i];
+    items[i].f = fin[i].p;
+    items[i].u = uo[i].p;
+    items[i].nrhs = nrhs[i];
+  }
+  const hif_status s = hif::pcg_many(items, st, [](const std::vector<hif::PcgItem*>& v, cudaStream_t s2) {
+    std::vector<hif::FactorBase*> F;
+    std::vector<const double*> r;
+    std::vector<double*> z;
+    std::vector<int> nr;
+    for (hif::PcgItem* I : v) {
+      F.push_back(I->F);
+      r.push_back(I->b.r.as<double>());
+      z.push_back(I->b.z.as<double>());
+      nr.push_back(I->nrhs);
+    }
+    hif::grouped_apply_any(F, r, z, nr, s2);
+  });
+  int col = 0;
+  for (int i = 0; i < nh; ++i) {
+    uo[i].finish(st);
+    for (int c = 0; c < nrhs[i]; ++c, ++col) {
+      if (iters) iters[col] = items[i].it[c];
+      if (relres) relres[col] = items[i].rel[c];
+    }
+  }
   if (s != HIF_OK) hif::set_last_error("PCG did not reach the tolerance within max_iter");
   return s;
   HIF_API_END

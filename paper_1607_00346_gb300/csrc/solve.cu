@@ -44,6 +44,39 @@ __global__ void k_acc(const int32_t* __restrict__ tgt, const int64_t* __restrict
   }
 }
 
+// Grouped forms: blockIdx.y = one factor's part (VecJob), the same
+// per-element work as k_gather, k_set and k_acc.
+template <typename T>
+__global__ void k_gather_grouped(const VecJob<T>* __restrict__ jobs) {
+  const VecJob<T> jb = jobs[blockIdx.y];
+  const int64_t i = (int64_t)blockIdx.x * VT + threadIdx.x;
+  if (i >= jb.cnt) return;
+  const int64_t g = jb.a[i];
+  for (int q = 0; q < jb.nrhs; ++q) jb.w[q * jb.vs + i] = jb.y[q * jb.ys + g];
+}
+
+template <typename T>
+__global__ void k_set_grouped(const VecJob<T>* __restrict__ jobs) {
+  const VecJob<T> jb = jobs[blockIdx.y];
+  const int64_t i = (int64_t)blockIdx.x * VT + threadIdx.x;
+  if (i >= jb.cnt) return;
+  const int64_t g = jb.a[i], p = jb.b[i];
+  for (int q = 0; q < jb.nrhs; ++q) jb.y[q * jb.ys + g] = jb.w[q * jb.vs + p];
+}
+
+template <typename T>
+__global__ void k_acc_grouped(const VecJob<T>* __restrict__ jobs) {
+  const VecJob<T> jb = jobs[blockIdx.y];
+  const int64_t t = (int64_t)blockIdx.x * VT + threadIdx.x;
+  if (t >= jb.cnt) return;
+  const int64_t g = jb.a[t];
+  for (int q = 0; q < jb.nrhs; ++q) {
+    T s = T(0);
+    for (int64_t e = jb.ptr[t]; e < jb.ptr[t + 1]; ++e) s += jb.w[q * jb.vs + jb.b[e]];
+    jb.y[q * jb.ys + g] -= s;
+  }
+}
+
 template <typename T>
 __global__ void k_cin(const double* __restrict__ x, T* y, int64_t cnt) {
   const int64_t i = (int64_t)blockIdx.x * VT + threadIdx.x;
@@ -188,6 +221,28 @@ void vec_convert_in(const double* x, T* y, int64_t cnt, cudaStream_t st) {
 }
 
 template <typename T>
+void vec_grouped(int kind, const VecJob<T>* d_jobs, const VecJob<T>* h_jobs, int njobs,
+                 cudaStream_t st) {
+  int64_t mx = 0;
+  double by = 0;
+  for (int i = 0; i < njobs; ++i) {
+    mx = std::max(mx, h_jobs[i].cnt);
+    by += (double)h_jobs[i].cnt * ((kind == 0 ? 4.0 : 8.0) + 2.0 * sizeof(T) * h_jobs[i].nrhs);
+  }
+  if (mx == 0) return;
+  static const char* names[3] = {"apply_grouped_gather", "apply_grouped_scatter",
+                                 "apply_grouped_accumulate"};
+  ProfScope ps(names[kind], st, 0.0, kind == 2 ? 0.0 : by);
+  for (int f0 = 0; f0 < njobs; f0 += 65535) {
+    const dim3 grid((unsigned)grid1(mx), (unsigned)std::min(65535, njobs - f0));
+    if (kind == 0) k_gather_grouped<T><<<grid, VT, 0, st>>>(d_jobs + f0);
+    else if (kind == 1) k_set_grouped<T><<<grid, VT, 0, st>>>(d_jobs + f0);
+    else k_acc_grouped<T><<<grid, VT, 0, st>>>(d_jobs + f0);
+    HIF_CHECK_LAUNCH();
+  }
+}
+
+template <typename T>
 void vec_convert_out(const T* y, double* x, int64_t cnt, cudaStream_t st) {
   if (cnt == 0) return;
   ProfScope ps("convert", st, 0.0, (double)cnt * (8.0 + sizeof(T)));
@@ -241,7 +296,8 @@ void xpby_cols(const double* z, const double* b, double* p, int64_t N, int ncol,
   template void vec_accumulate<T>(const int32_t*, const int64_t*, const int32_t*, int64_t,   \
                                   T*, int64_t, const T*, int64_t, int, cudaStream_t);        \
   template void vec_convert_in<T>(const double*, T*, int64_t, cudaStream_t);                 \
-  template void vec_convert_out<T>(const T*, double*, int64_t, cudaStream_t);
+  template void vec_convert_out<T>(const T*, double*, int64_t, cudaStream_t);                \
+  template void vec_grouped<T>(int, const VecJob<T>*, const VecJob<T>*, int, cudaStream_t);
 HIF_INST(float)
 HIF_INST(double)
 #undef HIF_INST

@@ -17,6 +17,25 @@ void vec_set(const int32_t* g, const int32_t* pos, int64_t cnt, T* y, int64_t ys
 template <typename T>
 void vec_accumulate(const int32_t* tgt, const int64_t* ptr, const int32_t* src, int64_t ntgt,
                     T* y, int64_t ys, const T* work, int64_t vs, int nrhs, cudaStream_t st);
+// One factor's part of a grouped gather (kind 0: w[q vs + i] = y[q ys + a[i]]),
+// set (kind 1: y[q ys + a[i]] = w[q vs + b[i]]) or accumulate (kind 2:
+// y[q ys + a[t]] -= sum_{e = ptr[t]}^{ptr[t+1]-1} w[q vs + b[e]]), i < cnt,
+// q < nrhs: the parts of several factors in one launch.
+template <typename T>
+struct VecJob {
+  const int32_t* a;
+  const int32_t* b;
+  const int64_t* ptr;
+  int64_t cnt;
+  T* y;
+  int64_t ys;
+  T* w;
+  int64_t vs;
+  int nrhs;
+};
+template <typename T>
+void vec_grouped(int kind, const VecJob<T>* d_jobs, const VecJob<T>* h_jobs, int njobs,
+                 cudaStream_t st);
 // y = (T) x
 template <typename T>
 void vec_convert_in(const double* x, T* y, int64_t cnt, cudaStream_t st);

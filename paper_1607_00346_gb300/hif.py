@@ -62,7 +62,7 @@ EXPORTS = ["hif_default_options", "hif_factor", "hif_apply", "hif_apply_noalloc"
            "hif_residual", "hif_solve",
            "hif_query_stats", "hif_predict_bytes", "hif_profile_begin", "hif_profile_end",
            "hif_destroy", "hif_last_error", "hif_version", "hif_save", "hif_load",
-           "hif_measure_peaks", "hif_query_active"]
+           "hif_measure_peaks", "hif_query_active", "hif_apply_batch", "hif_solve_batch"]
 
 
 class Peaks(ctypes.Structure):
@@ -124,6 +124,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.hif_last_error.restype = ctypes.c_char_p
     lib.hif_version.argtypes = []
     lib.hif_version.restype = ctypes.c_char_p
+    ptrs = ctypes.POINTER(vp)
+    lib.hif_apply_batch.argtypes = [ptrs, i, ptrs, ptrs, ctypes.POINTER(ctypes.c_int), vp]
+    lib.hif_apply_batch.restype = i
+    lib.hif_solve_batch.argtypes = [ptrs, i, ptrs, ptrs, ctypes.POINTER(ctypes.c_int), vp,
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    lib.hif_solve_batch.restype = i
     lib.hif_query_active.argtypes = [vp, i, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
                                      ctypes.POINTER(ctypes.c_int64)]
     lib.hif_query_active.restype = i
@@ -299,6 +305,49 @@ class Handle:
                     factor_bytes=s.factor_bytes, peak_bytes=s.peak_bytes,
                     stored_entries=s.stored_entries, kernel_launches=s.kernel_launches,
                     apply_launches=s.apply_launches, retried_fronts=s.retried_fronts)
+
+
+def _batch_args(handles, fs, us):
+    nh = len(handles)
+    if not (nh == len(fs) == len(us)) or nh == 0:
+        raise ValueError("need as many right-hand sides and outputs as handles")
+    hp = (ctypes.c_void_p * nh)(*[h._h for h in handles])
+    keep = []
+    fp = (ctypes.c_void_p * nh)()
+    up = (ctypes.c_void_p * nh)()
+    nr = (ctypes.c_int * nh)()
+    for k, (h, f, u) in enumerate(zip(handles, fs, us)):
+        a, ka = _ptr(f)
+        b, kb = _ptr(u)
+        keep += [ka, kb]
+        fp[k], up[k] = a.value, b.value
+        nr[k] = h._nrhs(f)
+    return hp, fp, up, nr, keep
+
+
+def apply_batch(handles, fs, us, stream=None):
+    """hif_apply_batch: us[i] = F_i^{-1} fs[i] with the sweeps of every factor in
+    shared launches (bitwise each handle's own apply)."""
+    hp, fp, up, nr, _keep = _batch_args(handles, fs, us)
+    _check(load().hif_apply_batch(hp, len(handles), fp, up, nr, _stream(stream)))
+    return us
+
+
+def solve_batch(handles, fs, us, stream=None, check=True):
+    """hif_solve_batch: PCG of every system in lockstep, preconditioner applied
+    as one grouped apply; returns per system (iterations, relative residuals)."""
+    hp, fp, up, nr, _keep = _batch_args(handles, fs, us)
+    tot = sum(nr)
+    its = (ctypes.c_int * tot)()
+    rel = (ctypes.c_double * tot)()
+    st = load().hif_solve_batch(hp, len(handles), fp, up, nr, _stream(stream), its, rel)
+    if check:
+        _check(st)
+    out, c = [], 0
+    for k in range(len(handles)):
+        out.append((list(its[c:c + nr[k]]), list(rel[c:c + nr[k]])))
+        c += nr[k]
+    return out
 
 
 def load_factor(path: str) -> Handle:

@@ -12,8 +12,11 @@ right-hand sides.  The server
   skip the factorization; with a spill directory, an evicted operator is
   written to disk (hif_save) and brought back by hif_load when it is asked
   for again;
-* batches all waiting requests for one operator into a single multi-column
-  PCG solve (one apply launch sequence for all their right-hand sides);
+* batches waiting requests: those for one operator become one multi-column
+  system, and the systems of every resident operator that has waiting
+  requests (grids of different sizes included) are solved together by one
+  hif_solve_batch, whose preconditioner applications share their launches;
+  each request's result is bitwise the one it gets when served alone;
 * runs admitted jobs on several worker threads, each with its own CUDA stream,
   so that requests that arrive while others are on the GPU are taken up as
   slots and memory free up and their kernels overlap on the device;
@@ -98,13 +101,20 @@ class HifBackend:
         return h, int(h.stats()["factor_bytes"])
 
     def solve(self, h, n, rhs: np.ndarray, stream):
+        return self.solve_batch([h], [n], [rhs], stream)[0]
+
+    def solve_batch(self, handles, ns, rhs_list, stream):
+        """One hif_solve_batch over several operators; [(its, rel, u)] per operator."""
         torch = self.torch
         with torch.cuda.stream(stream):
-            f = torch.from_numpy(rhs).cuda()
-            u = torch.zeros_like(f)
-            its, rel = h.solve(f, u, stream=stream)
-            uh = u.cpu().numpy() if self.keep_u else None
-        return its, rel, uh
+            fs = [torch.from_numpy(np.ascontiguousarray(r)).cuda() for r in rhs_list]
+            us = [torch.zeros_like(f) for f in fs]
+            res = self.hif.solve_batch(handles, fs, us, stream=stream)
+            out = []
+            for (its, rel), u in zip(res, us):
+                out.append((its, rel, u.cpu().numpy() if self.keep_u else None))
+            stream.synchronize()
+        return out
 
     def release(self, h):
         h.close()
@@ -125,10 +135,15 @@ class _Resident:
 
 
 class Server:
-    def __init__(self, backend, mem_budget: int, workers: int = 4, spill_dir: str | None = None):
+    def __init__(self, backend, mem_budget: int, workers: int = 4, spill_dir: str | None = None,
+                 max_ops: int = 8, max_cols: int = 64):
         self.be = backend
         self.budget = int(mem_budget)
         self.workers = workers
+        # one solve job takes the waiting requests of at most max_ops resident
+        # operators and max_cols right-hand sides
+        self.max_ops = max_ops
+        self.max_cols = max_cols
         # with spill_dir, an evicted operator is written to disk (hif_save)
         # and a later request for it loads the file instead of refactoring
         self.spill_dir = spill_dir
@@ -141,6 +156,7 @@ class Server:
         self.done: list = []
         self.failed: list = []
         self.log: list = []        # (time, event, detail)
+        self.batch_sizes: list = []   # operators per solve job
 
     # ---- memory ---------------------------------------------------------------
     def _in_use(self):
@@ -164,7 +180,35 @@ class Server:
 
     # ---- scheduling -------------------------------------------------------------
     def _next_job(self):
-        """Pick waiting requests of one operator that can start now (lock held)."""
+        """Pick work that can start now (lock held).
+
+        A solve job takes the waiting requests of every resident operator not
+        already in a job (up to max_ops operators and max_cols columns); only
+        when there is none, the first waiting operator that is not resident
+        is admitted (its predicted footprint must fit) and factored; its
+        requests then wait for the next solve job with the others.  Returns
+        (keys, batches, reserved bytes) with one request list per key, or
+        None."""
+        keys, batches, cols = [], [], 0
+        for req in list(self.pending):
+            key = req.op_key
+            if key in keys or key in self.inflight_keys or key not in self.resident:
+                continue
+            batch = [r for r in self.pending if r.op_key == key]
+            nc = sum(r.nrhs for r in batch)
+            if keys and (len(keys) >= self.max_ops or cols + nc > self.max_cols):
+                continue
+            keys.append(key)
+            batches.append(batch)
+            cols += nc
+        if keys:
+            for key, batch in zip(keys, batches):
+                self.resident.move_to_end(key)
+                self.resident[key].busy += 1
+                for r in batch:
+                    self.pending.remove(r)
+                self.inflight_keys.add(key)
+            return keys, batches, 0
         seen = set()
         for req in list(self.pending):
             key = req.op_key
@@ -172,13 +216,6 @@ class Server:
                 continue
             seen.add(key)
             batch = [r for r in self.pending if r.op_key == key]
-            if key in self.resident:
-                self.resident.move_to_end(key)
-                self.resident[key].busy += 1
-                for r in batch:
-                    self.pending.remove(r)
-                self.inflight_keys.add(key)
-                return key, batch, 0
             spilled = self.spilled.get(key)
             need = spilled[1] if spilled else self.be.predict_bytes(req.n, req.m)
             if need > self.budget:
@@ -195,8 +232,37 @@ class Server:
                 for r in batch:
                     self.pending.remove(r)
                 self.inflight_keys.add(key)
-                return key, batch, need
+                return [key], [batch], need
         return None
+
+    def _finish(self, keys, batches, results=None, exc=None):
+        """Record a job's outcome (lock not held)."""
+        t1 = time.perf_counter()
+        with self.lock:
+            for k, (key, batch) in enumerate(zip(keys, batches)):
+                if exc is None:
+                    its, rel, u = results[k]
+                    c = 0
+                    for r in batch:
+                        r.iters = list(its[c:c + r.nrhs])
+                        r.relres = list(rel[c:c + r.nrhs])
+                        if u is not None:
+                            r.u = u[c:c + r.nrhs]
+                        c += r.nrhs
+                        r.t_done = t1
+                    self.done.extend(batch)
+                    self.log.append((t1, "done", [r.rid for r in batch]))
+                else:
+                    for r in batch:
+                        r.t_done = t1
+                        r.iters, r.relres = [-1] * r.nrhs, [math.nan] * r.nrhs
+                    self.failed.extend(batch)
+                if key in self.resident:
+                    self.resident[key].busy -= 1
+                self.inflight_keys.discard(key)
+            if exc is not None:
+                self.log.append((t1, "error", repr(exc)))
+            self.lock.notify_all()
 
     def _worker(self, stream):
         while True:
@@ -208,13 +274,15 @@ class Server:
                     job = self._next_job()
                     if job is None:
                         self.lock.wait(0.01)
-            key, batch, reserved = job
-            n, m, seed = key
+            keys, batches, reserved = job
             t0 = time.perf_counter()
-            for r in batch:
-                r.t_start = t0
+            for batch in batches:
+                for r in batch:
+                    r.t_start = t0
             try:
                 if reserved:
+                    key = keys[0]
+                    n, m, seed = key
                     with self.lock:
                         spilled = self.spilled.pop(key, None)
                     if spilled:
@@ -225,50 +293,44 @@ class Server:
                     with self.lock:
                         self.reserved -= reserved
                         reserved = 0
-                        self.resident[key] = _Resident(h, fbytes, busy=1)
-                        for r in batch:
+                        self.resident[key] = _Resident(h, fbytes, busy=0)
+                        self.inflight_keys.discard(key)
+                        # back to the front of the queue: the next solve job
+                        # takes them with every other resident operator's
+                        # waiting requests
+                        for r in reversed(batches[0]):
                             r.factored = True
-                else:
-                    with self.lock:
-                        h = self.resident[key].handle
-                rhs = np.concatenate([inputs.normal_rhs(n, r.nrhs, 10_000 + r.rid)
-                                      for r in batch])
-                its, rel, u = self.be.solve(h, n, rhs, stream)
+                            self.pending.appendleft(r)
+                        self.lock.notify_all()
+                    continue
+                with self.lock:
+                    handles = [self.resident[k].handle for k in keys]
+                rhs = [np.concatenate([inputs.normal_rhs(k[0], r.nrhs, 10_000 + r.rid)
+                                       for r in batch]) for k, batch in zip(keys, batches)]
+                if len(self.batch_sizes) < 100000:
+                    self.batch_sizes.append(len(keys))
+                results = self.be.solve_batch(handles, [k[0] for k in keys], rhs, stream)
             except Exception as exc:     # the job fails; the server carries on
                 with self.lock:
                     self.reserved -= reserved
-                    if key in self.resident:
-                        self.resident[key].busy -= 1
-                    self.inflight_keys.discard(key)
-                    for r in batch:
-                        r.t_done = time.perf_counter()
-                        r.iters, r.relres = [-1] * r.nrhs, [math.nan] * r.nrhs
-                    self.failed.extend(batch)
-                    self.log.append((time.perf_counter(), "error", repr(exc)))
-                    self.lock.notify_all()
+                self._finish(keys, batches, exc=exc)
                 continue
-            t1 = time.perf_counter()
-            c = 0
-            for r in batch:
-                r.iters = list(its[c:c + r.nrhs])
-                r.relres = list(rel[c:c + r.nrhs])
-                if u is not None:
-                    r.u = u[c:c + r.nrhs]
-                c += r.nrhs
-                r.t_done = t1
-            with self.lock:
-                self.resident[key].busy -= 1
-                self.inflight_keys.discard(key)
-                self.done.extend(batch)
-                self.log.append((t1, "done", [r.rid for r in batch]))
-                self.lock.notify_all()
+            self._finish(keys, batches, results)
 
     def run(self, requests, realtime: bool = True):
-        """Serve `requests` (arrival times relative to the start); returns stats."""
+        """Serve `requests` (arrival times relative to the start); returns stats.
+
+        realtime=False: every request is waiting when the workers start."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         self._stop = False
         threads = []
         t_base = time.perf_counter()
+        if not realtime:
+            with self.lock:
+                for r in reqs:
+                    r.arrival = t_base
+                    self.pending.append(r)
+            reqs = []
         for _ in range(self.workers):
             s = self.be.new_stream()
             th = threading.Thread(target=self._worker, args=(s,), daemon=True)
@@ -305,6 +367,9 @@ class Server:
                 "p50_ms": 1e3 * pct(0.50), "p99_ms": 1e3 * pct(0.99),
                 "factorizations": sum(1 for r in self.done if r.factored),
                 "failed": len(self.failed),
+                "operators_per_solve_mean": (sum(self.batch_sizes) / len(self.batch_sizes)
+                                             if self.batch_sizes else 0.0),
+                "operators_per_solve_max": max(self.batch_sizes, default=0),
                 "max_iters": max(max(r.iters) for r in self.done)}
 
     def release_all(self):

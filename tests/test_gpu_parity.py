@@ -346,3 +346,44 @@ def test_fp64_retry_of_fronts_flagged_by_pivot_growth(H):
         assert np.linalg.norm(u - uo) <= 1e-8 * np.linalg.norm(uo), g
     if out[0.0] is not None:
         assert out[1e2][1] <= 1.5 * out[0.0][1], (out[1e2][1], out[0.0][1])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_apply_and_solve_are_bitwise_the_single_ones(H, precision):
+    # factors of different grids (and leaf sizes), different numbers of
+    # right-hand sides: hif_apply_batch / hif_solve_batch run their sweeps in
+    # shared launches, and every factor's result must be bit for bit its own
+    # hif_apply / hif_solve
+    grids = [(16, 4, 3), (24, 3, 1), (32, 4, 5), (8, 4, 17)]
+    hs, fs = [], []
+    for k, (n, m, nr) in enumerate(grids):
+        a = _coeff(n, 1600 + k)
+        hs.append(H.factor(n, m, _dev(a), b_const=0.05 * k, eps=1e-6, precision=precision))
+        fs.append(inputs.normal_rhs(n, nr, 1610 + k))
+    fd = [_dev(f) for f in fs]
+    us = [torch.full_like(f, float("nan")) for f in fd]
+    H.apply_batch(hs, fd, us)
+    torch.cuda.synchronize()
+    for h, f, u in zip(hs, fd, us):
+        ref = torch.empty_like(f)
+        h.apply(f, ref)
+        torch.cuda.synchronize()
+        assert torch.equal(u, ref)
+    # host arrays in the batch too
+    uh = [np.zeros_like(f) for f in fs]
+    H.apply_batch(hs, fs, uh)
+    for u, ub in zip(uh, us):
+        assert np.array_equal(u, ub.cpu().numpy())
+    us = [torch.zeros_like(f) for f in fd]
+    res = H.solve_batch(hs, fd, us)
+    torch.cuda.synchronize()
+    for h, f, u, (its, rel) in zip(hs, fd, us, res):
+        ref = torch.zeros_like(f)
+        its1, rel1 = h.solve(f, ref)
+        torch.cuda.synchronize()
+        assert torch.equal(u, ref) and its == its1 and rel == rel1
+        assert max(rel) <= 1e-10
+    with pytest.raises(H.HifError):
+        H.apply_batch([hs[0], hs[0]], [fd[0], fd[0]], [us[0], us[1]])
+    for h in hs:
+        h.close()
