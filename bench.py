@@ -325,6 +325,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=200.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the serving and 256^3 records of the default line")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="built-in launch shapes instead of timing them first")
     args = ap.parse_args()
     if args.gpus > 1 and int(os.environ.get("WORLD_SIZE", "1")) != args.gpus:
         raise SystemExit(f"--gpus {args.gpus} runs one process per GPU: launch it with "
@@ -369,6 +371,14 @@ def main():
     f_d = torch.from_numpy(f_h).cuda()
     u_d = torch.zeros_like(f_d)
     stream = torch.cuda.current_stream()
+    # launch shapes per size bucket, timed on this operator (bitwise-neutral)
+    tune = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        table = hif.autotune(n, m, a_d, b_const=w["b"], eps=w["eps"], precision=prec, force=True)
+        torch.cuda.synchronize()
+        tune = {"seconds": time.perf_counter() - t0,
+                "table": [l for l in table.splitlines() if l and not l.startswith("# hif")]}
 
     def step(evs=None, keep=False):
         if evs:
@@ -535,6 +545,7 @@ def main():
             "kernels": {p["name"]: round(p["seconds"] / args.steps, 5) for p in
                         sorted(prof, key=lambda p: -p["seconds"])[:12]},
             "peaks": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in peaks.items()},
+            "autotune": tune,
         }
         line.update(extras)
         print(json.dumps(line), flush=True)

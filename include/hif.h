@@ -277,6 +277,34 @@ typedef struct {
 hif_status hif_profile_begin(void);
 hif_status hif_profile_end(hif_kernel_profile* out, int cap, int* count);
 
+/*
+ * Autotuning of the launch shapes (the paper has no counterpart: its dense
+ * algebra is Elemental's).  Two kernels have shapes that do not change a
+ * single bit of any result but decide their speed: the cluster pivoted QR of
+ * the large IDs (CTAs per front, 1-16, and how many fronts share a launch:
+ * all at once, or as many as fit the L2 cache) and the tensor-core products
+ * (K chunk and tile width).  Fronts and products are put into size buckets
+ * (ID: front width x number of fronts; products: shape x waves of tiles).
+ *
+ * hif_autotune -- factor the given operator once while measuring: every
+ * cluster ID without a table entry times its candidate shapes in place on
+ * copies of its own matrices; the tensor-core products record their
+ * shapes, which are then replayed with every tile variant.  The fastest
+ * shape per bucket is kept process-wide and used by every later hif_factor
+ * (the built-in rule elsewhere).  Arguments as for hif_factor; path: a
+ * table file to write (NULL: none); with force = 0 and a readable table for
+ * this device at path, the table is loaded instead of measured.
+ * hif_autotune_load reads such a file (INVALID_ARG if it is malformed or
+ * was written for another device), hif_autotune_clear returns to the
+ * built-in rules, hif_autotune_table copies the current table as text
+ * (*len = its length; buf may be NULL).
+ */
+hif_status hif_autotune(const hif_grid* grid, const double* a, const double* b, double b_const,
+                        const hif_options* opt, const char* path, int force, hif_stream stream);
+hif_status hif_autotune_load(const char* path);
+void hif_autotune_clear(void);
+hif_status hif_autotune_table(char* buf, size_t cap, size_t* len);
+
 /* Release every resource of the handle (NULL is ignored). */
 void hif_destroy(hif_handle h);
 

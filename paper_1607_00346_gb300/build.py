@@ -20,7 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["dense.cu", "tc.cu", "front.cu", "idk.cu", "qr.cu", "solve.cu", "prof.cu", "peaks.cu",
               "hif.cu"]
-CXX_SOURCES = ["symbolic.cpp"]
+CXX_SOURCES = ["symbolic.cpp", "tune.cpp"]
 
 
 def _nvcc() -> str:

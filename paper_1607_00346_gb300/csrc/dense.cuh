@@ -37,6 +37,10 @@ void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Ab
              const float* Bbase, float* Cbase, int* d_flags, cudaStream_t st,
              const char* name = "gemm_tc");
 
+// Autotuning of gemm_tc's tile shape: time the variants on the product
+// shapes recorded during a tuning factorization (tune.h).
+void tune_gemm_from_records(cudaStream_t st);
+
 // C = beta C + alpha op(A) op(B) for a batch of independent problems.
 template <typename T>
 void gemm_batched(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const T* Abase,

@@ -24,13 +24,14 @@
 #include "front.cuh"
 #include "solve.cuh"
 #include "symbolic.h"
+#include "tune.h"
 
 namespace hif {
 
 template <typename T>
 void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* Garena,
-                                 int32_t* perm, T* Farena, double* scratch, int32_t* stepAr,
-                                 T* Fscratch, double eps, cudaStream_t st);
+                                 size_t arena_elems, int32_t* perm, T* Farena, double* scratch,
+                                 int32_t* stepAr, T* Fscratch, double eps, cudaStream_t st);
 size_t id_fscratch_elems(int64_t total_front_dofs);
 bool id_in_shared_memory(int m, int nF, int tsize);
 template <typename T>
@@ -1044,7 +1045,9 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
     for (int f : sel[g]) sub[g].push_back(sd[f]);
     upload_async(sub_d[g], sub[g], &F_.mem, st_);
     interpolative_decomposition<T>(sub_d[g].as<SkelDesc>(), sub[g].data(), (int)sub[g].size(),
-                                   g == 0 ? G.as<T>() : Rbuf.as<T>(), perm_d.as<int32_t>(),
+                                   g == 0 ? G.as<T>() : Rbuf.as<T>(),
+                                   (g == 0 ? G.bytes() : Rbuf.bytes()) / sizeof(T),
+                                   perm_d.as<int32_t>(),
                                    tm.as<T>(), scratch.as<double>(), steps.as<int32_t>(),
                                    fsc.as<T>(), F_.eps, st_);
     HIF_CUDA_TRY(cudaMemcpyAsync(sub[g].data(), sub_d[g].as<void>(),
@@ -1975,6 +1978,74 @@ hif_status hif_solve_batch(const hif_handle* hs, int nh, const double* const* f,
   }
   if (s != HIF_OK) hif::set_last_error("PCG did not reach the tolerance within max_iter");
   return s;
+  HIF_API_END
+}
+
+hif_status hif_autotune(const hif_grid* grid, const double* a, const double* b, double b_const,
+                        const hif_options* opt, const char* path, int force, hif_stream stream) {
+  HIF_API_BEGIN
+  if (path && !force) {
+    if (std::FILE* fh = std::fopen(path, "rb")) {
+      std::string text;
+      char buf[4096];
+      size_t got;
+      while ((got = std::fread(buf, 1, sizeof(buf), fh)) > 0) text.append(buf, got);
+      std::fclose(fh);
+      std::string why;
+      if (hif::tune_parse(text, &why)) return HIF_OK;   // a table for this device
+    }
+  }
+  hif::tune_clear();
+  {
+    // one factorization measures: the cluster IDs time their shapes in
+    // place, the tensor-core products record theirs
+    hif::TuneSession session;
+    hif_handle h = nullptr;
+    const hif_status s = hif_factor(grid, a, b, b_const, opt, stream, &h);
+    if (s != HIF_OK) return s;
+    hif_destroy(h);
+  }
+  hif::tune_gemm_from_records(reinterpret_cast<cudaStream_t>(stream));
+  if (path) {
+    const std::string text = hif::tune_serialize();
+    std::FILE* fh = std::fopen(path, "wb");
+    if (!fh) throw Error{HIF_ERR_INVALID_ARG, std::string("cannot write ") + path};
+    const size_t put = std::fwrite(text.data(), 1, text.size(), fh);
+    std::fclose(fh);
+    if (put != text.size()) throw Error{HIF_ERR_INVALID_ARG, std::string("cannot write ") + path};
+  }
+  return HIF_OK;
+  HIF_API_END
+}
+
+hif_status hif_autotune_load(const char* path) {
+  HIF_API_BEGIN
+  if (!path) throw Error{HIF_ERR_INVALID_ARG, "path must not be NULL"};
+  std::FILE* fh = std::fopen(path, "rb");
+  if (!fh) throw Error{HIF_ERR_INVALID_ARG, std::string("cannot open ") + path};
+  std::string text;
+  char buf[4096];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof(buf), fh)) > 0) text.append(buf, got);
+  std::fclose(fh);
+  std::string why;
+  if (!hif::tune_parse(text, &why)) throw Error{HIF_ERR_INVALID_ARG, "tuning table rejected: " + why};
+  return HIF_OK;
+  HIF_API_END
+}
+
+void hif_autotune_clear(void) { hif::tune_clear(); }
+
+hif_status hif_autotune_table(char* buf, size_t cap, size_t* len) {
+  HIF_API_BEGIN
+  const std::string text = hif::tune_serialize();
+  if (len) *len = text.size();
+  if (buf && cap) {
+    const size_t n = std::min(cap - 1, text.size());
+    std::memcpy(buf, text.data(), n);
+    buf[n] = 0;
+  }
+  return HIF_OK;
   HIF_API_END
 }
 

@@ -30,10 +30,13 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
 #include "front.cuh"
+#include "tune.h"
 #include "warp.cuh"
 
 namespace cg = cooperative_groups;
@@ -510,8 +513,8 @@ bool id_in_shared_memory(int m, int nF, int tsize) {
 
 template <typename T>
 void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* Garena,
-                                 int32_t* perm, T* Farena, double* scratch, int32_t* stepAr,
-                                 T* Fscratch, double eps, cudaStream_t st) {
+                                 size_t arena_elems, int32_t* perm, T* Farena, double* scratch,
+                                 int32_t* stepAr, T* Fscratch, double eps, cudaStream_t st) {
   if (nf == 0) return;
   int nsm = 0, dev = 0;
   HIF_CUDA_TRY(cudaGetDevice(&dev));
@@ -557,76 +560,152 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
     HIF_CUDA_TRY(cudaFreeAsync(d_list, st));
   }
   if (rest.empty()) return;
-  // cluster size: small fronts get one CTA; large fronts (work per step
-  // nF x nR above ~1e6) spread their columns over as many SMs as the batch
-  // leaves free (two CTAs per SM), up to 16, so that one launch fills the GPU
-  std::vector<std::vector<int>> bucket(17);
-  int nbig = 0;
-  for (int f : rest)
-    if ((double)h_f[f].nF * (h_f[f].nF + h_f[f].idm) > 1.0e6) ++nbig;
-  const int cs_big = std::max(1, std::min(16, 2 * nsm / std::max(1, nbig)));
-  for (int f : rest) {
-    const double work = (double)h_f[f].nF * (h_f[f].nF + h_f[f].idm);
-    int cs = work > 1.0e6 ? cs_big : 1;
-    cs = std::min(cs, std::max(1, h_f[f].nF / 8));   // at least 8 columns per CTA
-    bucket[cs].push_back(f);
-  }
   static const bool attr_set = [] {
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_cpqr<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     return true;
   }();
   (void)attr_set;
-  for (int b = 1; b <= 16; ++b) {
-    if (bucket[b].empty()) continue;
-    int CS = b;
-    // the largest cluster of at most b CTAs that the GPU can place
-    while (CS > 1) {
-      cudaLaunchConfig_t q = {};
-      q.gridDim = dim3((unsigned)CS);
-      q.blockDim = dim3(ID_THREADS);
-      cudaLaunchAttribute qa[1];
-      qa[0].id = cudaLaunchAttributeClusterDimension;
-      qa[0].val.clusterDim.x = CS;
-      qa[0].val.clusterDim.y = 1;
-      qa[0].val.clusterDim.z = 1;
-      q.attrs = qa;
-      q.numAttrs = 1;
-      int ncl = 0;
-      if (cudaOccupancyMaxActiveClusters(&ncl, k_cpqr<T>, &q) == cudaSuccess && ncl > 0) break;
-      cudaGetLastError();
-      --CS;
+  // the largest cluster of at most b CTAs that the GPU can place
+  static int placeable[17] = {0};
+  static std::once_flag place_once;
+  std::call_once(place_once, [] {
+    for (int b = 1; b <= 16; ++b) {
+      int CS = b;
+      while (CS > 1) {
+        cudaLaunchConfig_t q = {};
+        q.gridDim = dim3((unsigned)CS);
+        q.blockDim = dim3(ID_THREADS);
+        cudaLaunchAttribute qa[1];
+        qa[0].id = cudaLaunchAttributeClusterDimension;
+        qa[0].val.clusterDim.x = CS;
+        qa[0].val.clusterDim.y = 1;
+        qa[0].val.clusterDim.z = 1;
+        q.attrs = qa;
+        q.numAttrs = 1;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, k_cpqr<T>, &q) == cudaSuccess && ncl > 0) break;
+        cudaGetLastError();
+        --CS;
+      }
+      placeable[b] = CS;
     }
-    int* d_list = nullptr;
-    HIF_CUDA_TRY(cudaMallocAsync(&d_list, sizeof(int) * bucket[b].size(), st));
-    HIF_CUDA_TRY(cudaMemcpyAsync(d_list, bucket[b].data(), sizeof(int) * bucket[b].size(),
-                                 cudaMemcpyHostToDevice, st));
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(bucket[b].size() * CS));
-    cfg.blockDim = dim3(ID_THREADS);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = CS;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    {
-      ProfScope ps("id_cpqr", st);
-      HIF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_cpqr<T>, d_f, (const int*)d_list, Garena, perm,
-                                      Farena, scratch, stepAr, Fscratch, eps));
-      HIF_CHECK_LAUNCH();
+  });
+  // one launch per chunk of `wave` fronts (0: all), clusters of CS CTAs
+  auto launch = [&](const std::vector<int>& fronts, int CS, int wave, SkelDesc* df, T* arena) {
+    CS = placeable[std::max(1, std::min(16, CS))];
+    const int w = wave > 0 ? wave : (int)fronts.size();
+    for (size_t f0 = 0; f0 < fronts.size(); f0 += (size_t)w) {
+      const int cnt = (int)std::min<size_t>((size_t)w, fronts.size() - f0);
+      int* d_list = nullptr;
+      HIF_CUDA_TRY(cudaMallocAsync(&d_list, sizeof(int) * cnt, st));
+      HIF_CUDA_TRY(cudaMemcpyAsync(d_list, fronts.data() + f0, sizeof(int) * cnt,
+                                   cudaMemcpyHostToDevice, st));
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(cnt * CS));
+      cfg.blockDim = dim3(ID_THREADS);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = CS;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      {
+        ProfScope ps("id_cpqr", st);
+        HIF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_cpqr<T>, df, (const int*)d_list, arena, perm,
+                                        Farena, scratch, stepAr, Fscratch, eps));
+        HIF_CHECK_LAUNCH();
+      }
+      HIF_CUDA_TRY(cudaFreeAsync(d_list, st));
     }
-    HIF_CUDA_TRY(cudaFreeAsync(d_list, st));
+  };
+  // built-in rule: small fronts get one CTA; large fronts (work per step
+  // nF x nR above ~1e6) spread their columns over as many SMs as the batch
+  // leaves free (two CTAs per SM), up to 16, at least 8 columns per CTA
+  int nbig = 0;
+  for (int f : rest)
+    if ((double)h_f[f].nF * (h_f[f].nF + h_f[f].idm) > 1.0e6) ++nbig;
+  const int cs_big = std::max(1, std::min(16, 2 * nsm / std::max(1, nbig)));
+  // one bucket per call: the width class of its widest cluster front and the
+  // count class of its cluster fronts; one shape (cluster size, fronts per
+  // launch) for all of them, the cluster size capped per front at nF / 8
+  // CTAs; fronts with the same effective shape share launches
+  int nfmax = 0, nfmin = 1 << 30;
+  size_t maxbytes = 0;
+  for (int f : rest) {
+    nfmax = std::max(nfmax, h_f[f].nF);
+    nfmin = std::min(nfmin, h_f[f].nF);
+    maxbytes = std::max(maxbytes, sizeof(T) * (size_t)h_f[f].idm * h_f[f].nF);
   }
+  const int wcls = id_width_class(nfmax), ccls = id_count_class((int)rest.size());
+  auto run_all = [&](int cs_choice, int wave, SkelDesc* df, T* arena) {
+    std::map<int, std::vector<int>> by_cs;
+    for (int f : rest) {
+      int cs = cs_choice;
+      if (cs <= 0) {   // built-in rule
+        const double work = (double)h_f[f].nF * (h_f[f].nF + h_f[f].idm);
+        cs = work > 1.0e6 ? cs_big : 1;
+      }
+      by_cs[std::min(cs, std::max(1, h_f[f].nF / 8))].push_back(f);
+    }
+    for (auto& [cs, fronts] : by_cs) launch(fronts, cs, wave, df, arena);
+  };
+  IdChoice tuned;
+  if (!tune_id_lookup(wcls, ccls, &tuned) && tune_session_active() && arena_elems > 0) {
+    // time the candidate shapes in place: every run starts from a copy of
+    // the matrices and descriptors as they are now (the ID overwrites them)
+    T* pristine = nullptr;
+    T* work = nullptr;
+    SkelDesc* dwork = nullptr;
+    HIF_CUDA_TRY(cudaMallocAsync(&pristine, sizeof(T) * arena_elems, st));
+    HIF_CUDA_TRY(cudaMallocAsync(&work, sizeof(T) * arena_elems, st));
+    HIF_CUDA_TRY(cudaMallocAsync(&dwork, sizeof(SkelDesc) * nf, st));
+    HIF_CUDA_TRY(cudaMemcpyAsync(pristine, Garena, sizeof(T) * arena_elems, cudaMemcpyDeviceToDevice, st));
+    cudaEvent_t e0, e1;
+    HIF_CUDA_TRY(cudaEventCreate(&e0));
+    HIF_CUDA_TRY(cudaEventCreate(&e1));
+    // fronts resident in L2 together (129 MB, with room to spare)
+    const int l2fit = (int)std::max<size_t>(1, (size_t)(96u << 20) / std::max<size_t>(1, maxbytes));
+    std::vector<int> waves = {0};
+    if (l2fit < (int)rest.size()) waves.push_back(l2fit);
+    std::vector<std::pair<IdChoice, double>> tried;
+    double best = 1e30;
+    for (int cs : {0, 1, 2, 4, 8, 16}) {   // 0: the built-in rule
+      if (cs > 1 && (cs > nfmin / 8 || placeable[cs] != cs)) continue;
+      for (int wv : waves) {
+        HIF_CUDA_TRY(cudaMemcpyAsync(work, pristine, sizeof(T) * arena_elems, cudaMemcpyDeviceToDevice, st));
+        HIF_CUDA_TRY(cudaMemcpyAsync(dwork, d_f, sizeof(SkelDesc) * nf, cudaMemcpyDeviceToDevice, st));
+        HIF_CUDA_TRY(cudaEventRecord(e0, st));
+        run_all(cs, wv, dwork, work);
+        HIF_CUDA_TRY(cudaEventRecord(e1, st));
+        HIF_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        HIF_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        tried.push_back({IdChoice{cs, wv}, 1e-3 * ms});
+        if (ms < best) {
+          best = ms;
+          tuned.cs = cs;
+          tuned.wave = wv;
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    HIF_CUDA_TRY(cudaFreeAsync(dwork, st));
+    HIF_CUDA_TRY(cudaFreeAsync(work, st));
+    HIF_CUDA_TRY(cudaFreeAsync(pristine, st));
+    tune_id_set(wcls, ccls, tuned, tried);
+  }
+  run_all(tuned.cs, tuned.wave, d_f, Garena);
 }
 
-template void interpolative_decomposition<float>(SkelDesc*, const SkelDesc*, int, float*, int32_t*,
-                                                 float*, double*, int32_t*, float*, double,
-                                                 cudaStream_t);
+template void interpolative_decomposition<float>(SkelDesc*, const SkelDesc*, int, float*, size_t,
+                                                 int32_t*, float*, double*, int32_t*, float*,
+                                                 double, cudaStream_t);
 template void interpolative_decomposition<double>(SkelDesc*, const SkelDesc*, int, double*,
-                                                  int32_t*, double*, double*, int32_t*, double*,
-                                                  double, cudaStream_t);
+                                                  size_t, int32_t*, double*, double*, int32_t*,
+                                                  double*, double, cudaStream_t);
 
 }  // namespace hif

@@ -34,6 +34,7 @@
 #include "common.cuh"
 #include "dense.cuh"
 #include "tcgen05.cuh"
+#include "tune.h"
 
 namespace hif {
 
@@ -315,6 +316,74 @@ void launch_tc(const GemmOp* d_ops, int nops, int mt, const float* Abase, const 
   }
 }
 
+namespace {
+
+// tile variants (see tune.h): 0 = KC 16 / 128 x 128, 1 = 16 / 128 x 256,
+// 2 = 32 / 128 x 128
+constexpr int VAR_KC[3] = {16, 16, 32};
+constexpr int VAR_TN[3] = {128, 256, 128};
+constexpr int VAR_PER_SM[3] = {3, 2, 1};
+
+int sm_count() {
+  static const int nsm = [] {
+    int dev = 0, count = 0;
+    HIF_CUDA_TRY(cudaGetDevice(&dev));
+    HIF_CUDA_TRY(cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev));
+    return count;
+  }();
+  return nsm;
+}
+
+void launch_variant(int v, const GemmOp* d_ops, int nops, int mt, const float* Abase,
+                    const float* Bbase, float* Cbase, int* d_flags, cudaStream_t st, int S,
+                    const int64_t* d_woff, float* Wk) {
+  if (v == 2) launch_tc<32, 128>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st, S, d_woff, Wk);
+  else if (v == 1) launch_tc<16, 256>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st, S, d_woff, Wk);
+  else launch_tc<16, 128>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st, S, d_woff, Wk);
+}
+
+// Output tiles of the batch for tile width tn, and the widest product's.
+void tile_counts(const GemmOp* h_ops, int nops, int tn, int* tiles, int* mt) {
+  *tiles = 0;
+  *mt = 1;
+  for (int i = 0; i < nops; ++i) {
+    const int t = ceil_div(h_ops[i].m, TC_M) * ceil_div(h_ops[i].n, tn);
+    *tiles += t;
+    *mt = std::max(*mt, t);
+  }
+}
+
+// Split of K: S minimises the waves per unit of work, ceil(tiles S /
+// capacity) / S, with at least 16 chunks of K per share; only for launches
+// that leave SMs idle, never for triangular (lower) products.  Computed from
+// the built-in variant so that a tuned tile shape never changes it.
+int split_k(const GemmOp* h_ops, int nops, int v) {
+  int tiles = 0, mt = 1, kmin = 1 << 30;
+  bool any_lower = false;
+  tile_counts(h_ops, nops, VAR_TN[v], &tiles, &mt);
+  for (int i = 0; i < nops; ++i) {
+    kmin = std::min(kmin, h_ops[i].k);
+    any_lower = any_lower || h_ops[i].lower;
+  }
+  const int cap = VAR_PER_SM[v] * sm_count();
+  int S = 1;
+  if (!any_lower && nops <= 65535 && tiles < cap) {
+    const int smax =
+        std::max(1, std::min({8, kmin / (16 * VAR_KC[v]), ceil_div(2 * cap, std::max(1, tiles))}));
+    double best = 1e30;
+    for (int q = 1; q <= smax; ++q) {
+      const double cost = (double)ceil_div(tiles * q, cap) / q;
+      if (cost < best - 1e-9) {
+        best = cost;
+        S = q;
+      }
+    }
+  }
+  return S;
+}
+
+}  // namespace
+
 void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Abase,
              const float* Bbase, float* Cbase, int* d_flags, cudaStream_t st, const char* name) {
   if (nops == 0) return;
@@ -325,48 +394,21 @@ void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Ab
     nmax = std::max(nmax, h_ops[i].n);
     fl += 2.0 * h_ops[i].m * (double)h_ops[i].n * h_ops[i].k * (h_ops[i].lower ? 0.5 : 1.0);
   }
-  // few rows (one tile, mostly padding): fewer, longer chunks; wide
-  // products: 128 x 256 tiles (half the A staging per product)
+  // built-in rule: few rows (one tile, mostly padding): fewer, longer
+  // chunks; wide products: 128 x 256 tiles (half the A staging per product)
   const bool narrow = mmax <= 64;
-  const int tn = (!narrow && nmax >= 256) ? 256 : 128;
-  int mt = 1;
-  for (int i = 0; i < nops; ++i)
-    mt = std::max(mt, ceil_div(h_ops[i].m, TC_M) * ceil_div(h_ops[i].n, tn));
+  const int vdef = narrow ? 2 : (nmax >= 256 ? 1 : 0);
+  const int S = split_k(h_ops, nops, vdef);
+  int tiles = 0, mt = 1;
+  tile_counts(h_ops, nops, 128, &tiles, &mt);
+  const int scls = gemm_shape_class(mmax, nmax), wcls = gemm_waves_class(tiles, sm_count());
+  if (tune_session_active()) tune_record_gemm(scls, wcls, h_ops, nops, fl);
+  // a tuned tile shape (every variant accumulates each entry in the same
+  // order; with K split, only variants with the same K chunk keep the split)
+  int v = vdef, vt = -1;
+  if (tune_gemm_lookup(scls, wcls, &vt) && (S == 1 || VAR_KC[vt] == VAR_KC[vdef])) v = vt;
+  tile_counts(h_ops, nops, VAR_TN[v], &tiles, &mt);
   ProfScope ps(name, st, fl, 0.0);
-  // few output tiles and deep K: split K so that the launch fills the GPU;
-  // partial tiles are summed in a fixed order
-  int tiles = 0, kmin = 1 << 30;
-  bool any_lower = false;
-  for (int i = 0; i < nops; ++i) {
-    tiles += ceil_div(h_ops[i].m, TC_M) * ceil_div(h_ops[i].n, tn);
-    kmin = std::min(kmin, h_ops[i].k);
-    any_lower = any_lower || h_ops[i].lower;
-  }
-  static const int nsm = [] {
-    int dev = 0, count = 0;
-    HIF_CUDA_TRY(cudaGetDevice(&dev));
-    HIF_CUDA_TRY(cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev));
-    return count;
-  }();
-  const int kc = narrow ? 32 : 16;
-  const int per_sm = narrow ? 1 : (tn == 256 ? 2 : 3);
-  // S minimises the waves per unit of work, ceil(tiles S / capacity) / S,
-  // with at least 16 chunks of K per share
-  int S = 1;
-  const int cap = per_sm * nsm;
-  if (!any_lower && nops <= 65535 && tiles < cap) {
-    // only launches that leave SMs idle; at most about two waves' worth
-    const int smax =
-        std::max(1, std::min({8, kmin / (16 * kc), ceil_div(2 * cap, std::max(1, tiles))}));
-    double best = 1e30;
-    for (int s = 1; s <= smax; ++s) {
-      const double cost = (double)ceil_div(tiles * s, cap) / s;
-      if (cost < best - 1e-9) {
-        best = cost;
-        S = s;
-      }
-    }
-  }
   int64_t* d_woff = nullptr;
   float* Wk = nullptr;
   if (S > 1) {
@@ -382,10 +424,7 @@ void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Ab
     HIF_CUDA_TRY(cudaMallocAsync(&Wk, sizeof(float) * tot, st));
     HIF_CUDA_TRY(cudaMemcpyAsync(d_woff, woff.data(), sizeof(int64_t) * nops,
                                  cudaMemcpyHostToDevice, st));
-    if (narrow) launch_tc<32, 128>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st, S, d_woff, Wk);
-    else if (tn == 256)
-      launch_tc<16, 256>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st, S, d_woff, Wk);
-    else launch_tc<16, 128>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st, S, d_woff, Wk);
+    launch_variant(v, d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st, S, d_woff, Wk);
     k_splitk_reduce<<<dim3((unsigned)ceil_div(mnmax, 256), nops), 256, 0, st>>>(d_ops, d_woff, Wk,
                                                                                 S, Cbase);
     HIF_CHECK_LAUNCH();
@@ -393,9 +432,106 @@ void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Ab
     HIF_CUDA_TRY(cudaFreeAsync(d_woff, st));
     return;
   }
-  if (narrow) launch_tc<32, 128>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st);
-  else if (tn == 256) launch_tc<16, 256>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st);
-  else launch_tc<16, 128>(d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st);
+  launch_variant(v, d_ops, nops, mt, Abase, Bbase, Cbase, d_flags, st, 1, nullptr, nullptr);
+}
+
+// Time the tile variants on the product shapes recorded during a tuning
+// factorization (one batch per bucket, the one with the most flops), on
+// synthetic operands of those shapes, and keep the fastest per bucket.
+void tune_gemm_from_records(cudaStream_t st) {
+  std::vector<GemmShapeRec> recs = tune_take_gemm_records();
+  int* d_flags = nullptr;
+  HIF_CUDA_TRY(cudaMallocAsync(&d_flags, sizeof(int) * FLAG_COUNT, st));
+  HIF_CUDA_TRY(cudaMemsetAsync(d_flags, 0xff, sizeof(int) * FLAG_COUNT, st));
+  cudaEvent_t e0, e1;
+  HIF_CUDA_TRY(cudaEventCreate(&e0));
+  HIF_CUDA_TRY(cudaEventCreate(&e1));
+  for (GemmShapeRec& r : recs) {
+    // compact operand arenas of the recorded shapes
+    std::vector<GemmOp> ops = r.ops;
+    int64_t na = 0, nb = 0, nc = 0;
+    int mmax = 0, nmax = 0;
+    for (GemmOp& o : ops) {
+      const int64_t asz = (int64_t)o.lda * (o.transA ? o.m : o.k);
+      const int64_t bsz = (int64_t)o.ldb * (o.transB ? o.k : o.n);
+      const int64_t csz = (int64_t)o.ldc * o.n;
+      o.A = na;
+      o.B = nb;
+      o.C = nc;
+      na += asz;
+      nb += bsz;
+      nc += csz;
+      mmax = std::max(mmax, o.m);
+      nmax = std::max(nmax, o.n);
+    }
+    float *A = nullptr, *B = nullptr, *C = nullptr;
+    GemmOp* d_ops = nullptr;
+    HIF_CUDA_TRY(cudaMallocAsync(&A, sizeof(float) * std::max<int64_t>(1, na), st));
+    HIF_CUDA_TRY(cudaMallocAsync(&B, sizeof(float) * std::max<int64_t>(1, nb), st));
+    HIF_CUDA_TRY(cudaMallocAsync(&C, sizeof(float) * std::max<int64_t>(1, nc), st));
+    HIF_CUDA_TRY(cudaMallocAsync(&d_ops, sizeof(GemmOp) * ops.size(), st));
+    HIF_CUDA_TRY(cudaMemsetAsync(A, 0, sizeof(float) * std::max<int64_t>(1, na), st));
+    HIF_CUDA_TRY(cudaMemsetAsync(B, 0, sizeof(float) * std::max<int64_t>(1, nb), st));
+    HIF_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(float) * std::max<int64_t>(1, nc), st));
+    HIF_CUDA_TRY(cudaMemcpyAsync(d_ops, ops.data(), sizeof(GemmOp) * ops.size(),
+                                 cudaMemcpyHostToDevice, st));
+    const int nops = (int)ops.size();
+    const bool narrow = mmax <= 64;
+    const int vdef = narrow ? 2 : (nmax >= 256 ? 1 : 0);
+    const int S = split_k(ops.data(), nops, vdef);
+    double best = 1e30;
+    int vbest = vdef;
+    double secs[3] = {0, 0, 0};
+    for (int v = 0; v < 3; ++v) {
+      if (S > 1 && VAR_KC[v] != VAR_KC[vdef]) continue;
+      int tiles = 0, mt = 1;
+      tile_counts(ops.data(), nops, VAR_TN[v], &tiles, &mt);
+      std::vector<float> ms;
+      for (int rep = 0; rep < 4; ++rep) {
+        int64_t* d_woff = nullptr;
+        float* Wk = nullptr;
+        std::vector<int64_t> woff(nops);
+        if (S > 1) {
+          int64_t tot = 0;
+          for (int i = 0; i < nops; ++i) {
+            woff[i] = tot;
+            tot += (int64_t)S * ops[i].m * ops[i].n;
+          }
+          HIF_CUDA_TRY(cudaMallocAsync(&d_woff, sizeof(int64_t) * nops, st));
+          HIF_CUDA_TRY(cudaMallocAsync(&Wk, sizeof(float) * tot, st));
+          HIF_CUDA_TRY(cudaMemcpyAsync(d_woff, woff.data(), sizeof(int64_t) * nops,
+                                       cudaMemcpyHostToDevice, st));
+        }
+        HIF_CUDA_TRY(cudaEventRecord(e0, st));
+        launch_variant(v, d_ops, nops, mt, A, B, C, d_flags, st, S, d_woff, Wk);
+        HIF_CUDA_TRY(cudaEventRecord(e1, st));
+        HIF_CUDA_TRY(cudaEventSynchronize(e1));
+        float t = 0.f;
+        HIF_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+        if (rep > 0) ms.push_back(t);   // the first run warms up
+        if (Wk) HIF_CUDA_TRY(cudaFreeAsync(Wk, st));
+        if (d_woff) HIF_CUDA_TRY(cudaFreeAsync(d_woff, st));
+      }
+      std::sort(ms.begin(), ms.end());
+      secs[v] = 1e-3 * ms[ms.size() / 2];
+      if (secs[v] < best) {
+        best = secs[v];
+        vbest = v;
+      }
+    }
+    tune_gemm_set(r.shape_cls, r.waves_cls, vbest, secs);
+    HIF_CUDA_TRY(cudaFreeAsync(d_ops, st));
+    HIF_CUDA_TRY(cudaFreeAsync(C, st));
+    HIF_CUDA_TRY(cudaFreeAsync(B, st));
+    HIF_CUDA_TRY(cudaFreeAsync(A, st));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int hflags[FLAG_COUNT];
+  HIF_CUDA_TRY(cudaMemcpyAsync(hflags, d_flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
+  HIF_CUDA_TRY(cudaStreamSynchronize(st));
+  HIF_CUDA_TRY(cudaFree(d_flags));
+  if (hflags[FLAG_TIMEOUT] >= 0) throw Error{HIF_ERR_TIMEOUT, "a tensor-core wait expired while tuning"};
 }
 
 }  // namespace hif

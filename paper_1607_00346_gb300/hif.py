@@ -62,7 +62,8 @@ EXPORTS = ["hif_default_options", "hif_factor", "hif_apply", "hif_apply_noalloc"
            "hif_residual", "hif_solve",
            "hif_query_stats", "hif_predict_bytes", "hif_profile_begin", "hif_profile_end",
            "hif_destroy", "hif_last_error", "hif_version", "hif_save", "hif_load",
-           "hif_measure_peaks", "hif_query_active", "hif_apply_batch", "hif_solve_batch"]
+           "hif_measure_peaks", "hif_query_active", "hif_apply_batch", "hif_solve_batch",
+           "hif_autotune", "hif_autotune_load", "hif_autotune_clear", "hif_autotune_table"]
 
 
 class Peaks(ctypes.Structure):
@@ -124,6 +125,16 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.hif_last_error.restype = ctypes.c_char_p
     lib.hif_version.argtypes = []
     lib.hif_version.restype = ctypes.c_char_p
+    lib.hif_autotune.argtypes = [ctypes.POINTER(Grid), vp, vp, d, ctypes.POINTER(Options),
+                                 ctypes.c_char_p, i, vp]
+    lib.hif_autotune.restype = i
+    lib.hif_autotune_load.argtypes = [ctypes.c_char_p]
+    lib.hif_autotune_load.restype = i
+    lib.hif_autotune_clear.argtypes = []
+    lib.hif_autotune_clear.restype = None
+    lib.hif_autotune_table.argtypes = [ctypes.c_char_p, ctypes.c_size_t,
+                                       ctypes.POINTER(ctypes.c_size_t)]
+    lib.hif_autotune_table.restype = i
     ptrs = ctypes.POINTER(vp)
     lib.hif_apply_batch.argtypes = [ptrs, i, ptrs, ptrs, ctypes.POINTER(ctypes.c_int), vp]
     lib.hif_apply_batch.restype = i
@@ -348,6 +359,36 @@ def solve_batch(handles, fs, us, stream=None, check=True):
         out.append((list(its[c:c + nr[k]]), list(rel[c:c + nr[k]])))
         c += nr[k]
     return out
+
+
+def autotune(n: int, m: int, a, b=None, b_const: float = 0.0, eps: float = 1e-6,
+             precision: int = PREC_FP32, path: str | None = None, force: bool = False,
+             stream=None, periodic: bool = False, **opts) -> str:
+    """hif_autotune on this operator; returns the table (text) now in use."""
+    g = Grid(n, m, 1 if periodic else 0)
+    o = default_options(eps=eps, precision=precision, **opts)
+    ap, _ka = _ptr(a)
+    bp, _kb = _ptr(b)
+    _check(load().hif_autotune(ctypes.byref(g), ap, bp, float(b_const), ctypes.byref(o),
+                               os.fsencode(path) if path else None, int(bool(force)),
+                               _stream(stream)))
+    return autotune_table()
+
+
+def autotune_load(path: str):
+    _check(load().hif_autotune_load(os.fsencode(path)))
+
+
+def autotune_clear():
+    load().hif_autotune_clear()
+
+
+def autotune_table() -> str:
+    n = ctypes.c_size_t()
+    _check(load().hif_autotune_table(None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _check(load().hif_autotune_table(buf, n.value + 1, ctypes.byref(n)))
+    return buf.value.decode()
 
 
 def load_factor(path: str) -> Handle:

@@ -99,3 +99,31 @@ def test_invalid_grid_rejected_before_any_device_work():
     st = hif.load().hif_factor(ctypes.byref(g), a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                None, 0.0, ctypes.byref(o), None, ctypes.byref(out))
     assert st == 1 and not out.value
+
+
+def test_autotune_table_files(tmp_path):
+    # the tuning table is text: a device line and one line per bucket; files
+    # that are malformed or were written for another device are refused and
+    # leave the table as it was
+    from paper_1607_00346_gb300 import hif
+    hif.load()
+    hif.autotune_clear()
+    text = hif.autotune_table()
+    assert text.startswith("#") and "\ndevice " in text
+    for bad in ("gemm 0 0 1\n", "device other_gpu\ngemm 0 0 1\n",
+                "device " + text.split("device ")[1].split()[0] + "\ngemm 9 0 1\n",
+                "device " + text.split("device ")[1].split()[0] + "\nid 0 0 17 0\n"):
+        p = tmp_path / "t.txt"
+        p.write_text(bad)
+        with pytest.raises(hif.HifError) as e:
+            hif.autotune_load(str(p))
+        assert e.value.status == 1
+    assert hif.autotune_table() == text
+    good = tmp_path / "good.txt"
+    tag = text.split("device ")[1].split()[0]
+    good.write_text(f"device {tag}\ngemm 2 1 0\nid 1 2 16 12\n")
+    hif.autotune_load(str(good))
+    t2 = hif.autotune_table()
+    assert "gemm 2 1 0" in t2 and "id 1 2 16 12" in t2
+    hif.autotune_clear()
+    assert "gemm" not in hif.autotune_table().replace("# ", "")
