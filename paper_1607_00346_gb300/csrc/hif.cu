@@ -17,6 +17,7 @@
 #include <numeric>
 #include <type_traits>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -30,9 +31,8 @@ namespace hif {
 
 template <typename T>
 void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* Garena,
-                                 size_t arena_elems, int32_t* perm, T* Farena, double* scratch,
-                                 int32_t* stepAr, T* Fscratch, double eps, cudaStream_t st);
-size_t id_fscratch_elems(int64_t total_front_dofs);
+                                 size_t arena_elems, int32_t* perm, T* Farena, int32_t* stepAr,
+                                 double eps, cudaStream_t st);
 bool id_in_shared_memory(int m, int nF, int tsize);
 template <typename T>
 void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garena, T* Rout,
@@ -584,7 +584,7 @@ class Builder {
                  std::vector<CellDesc>& cdesc, DevBuf& lists_d);
   // returns the number of DOFs the step eliminated (marked dead in alive)
   int64_t skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& alive, DevBuf& Kar,
-                    DevBuf& cdesc_d, SkelPlan* plan = nullptr);
+                    DevBuf& cdesc_d, std::shared_ptr<const SkelPlan> plan);
 
   // Host side of an apply stage (gather list, mat-vec lists, set and
   // accumulate lists).  It depends only on the plan and, for faces and edges,
@@ -680,25 +680,29 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
 
   HIF_CUDA_TRY(cudaStreamCreateWithFlags(&up_st_, cudaStreamNonBlocking));
   const int L = F_.L;
-  std::shared_ptr<CellPlan> prevp;
+  std::shared_ptr<const CellPlan> prevp;
   DevBuf prevK, prevDesc;
   for (int level = 0; level <= L; ++level) {
     level_ = level;
     auto tl = Clock::now();
-    auto cpp = std::make_shared<CellPlan>();
-    CellPlan& cp = *cpp;
+    std::shared_ptr<const CellPlan> cpp;
     tr_.mark(level, "start");
     std::vector<int64_t> mapOff;
     PlanVec32 map;
-    if (have_spec_) {
-      cp = std::move(spec_cells_);
-      mapOff = std::move(spec_mapOff_);
-      map = std::move(spec_map_);
-      have_spec_ = false;
-    } else {
-      sym_.build_cells(level, cp);
-      if (level > 0) sym_.merge_maps(*prevp, cp, mapOff, map);
+    {
+      auto built = std::make_shared<CellPlan>();
+      if (have_spec_) {
+        *built = std::move(spec_cells_);
+        mapOff = std::move(spec_mapOff_);
+        map = std::move(spec_map_);
+        have_spec_ = false;
+      } else {
+        sym_.build_cells(level, *built);
+        if (level > 0) sym_.merge_maps(*prevp, *built, mapOff, map);
+      }
+      cpp = std::move(built);
     }
+    const CellPlan& cp = *cpp;
     tr_.mark(level, "symbolic cells + merge maps");
     // frontal matrices of the level's cells
     std::vector<CellDesc> cdesc(cp.ncell);
@@ -751,12 +755,13 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
     // it while the edge plan is still being built); declared before the
     // futures, so it outlives them
     std::vector<uint8_t> alive_plan;
-    SkelPlan fplan, ep;
+    auto fbuild = std::make_shared<SkelPlan>(), ebuild = std::make_shared<SkelPlan>();
+    std::shared_ptr<const SkelPlan> fplan, eplan;
     std::future<void> face_plan, edge_plan;
     if (level < L && F_.eps > 0.0) {
       alive_plan = alive;
-      face_plan = std::async(std::launch::async, [&]() { sym_.build_skel(cp, 1, alive_plan, fplan); });
-      edge_plan = std::async(std::launch::async, [&]() { sym_.build_skel(cp, 2, alive_plan, ep); });
+      face_plan = std::async(std::launch::async, [&]() { sym_.build_skel(cp, 1, alive_plan, *fbuild); });
+      edge_plan = std::async(std::launch::async, [&]() { sym_.build_skel(cp, 2, alive_plan, *ebuild); });
     }
     cell_step(cpp, Kar, cdesc_d, cdesc, lists_d);
     tr_.mark(level, "cell elimination");
@@ -772,13 +777,19 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
       // the face step starts once its plan is ready; the edge plan goes on
       // meanwhile and is joined after the face step
       face_plan.get();
+      fplan = fbuild;
       tr_.mark(level, "face plan joined");
-      const int64_t dropped = skel_step(cp, 1, alive, Kar, cdesc_d, &fplan);
+      const int64_t dropped = skel_step(cp, 1, alive, Kar, cdesc_d, fplan);
       tr_.mark(level, "faces");
       edge_plan.get();
+      eplan = ebuild;
       start_stage_jobs();
       tr_.mark(level, "edge plan joined");
-      if (dropped) sym_.filter_rows(ep, alive);
+      if (dropped) {
+        auto filtered = std::make_shared<SkelPlan>();
+        sym_.filter_rows(*eplan, alive, *filtered);
+        eplan = std::move(filtered);
+      }
       // the next level's cells, assuming the edges keep every DOF (they
       // usually do), are planned on a host thread while the edges run;
       // rebuilt at the next level if an edge lost DOFs
@@ -791,7 +802,7 @@ void Builder<T>::run(const double* a_dev, const double* b_dev, double b_const) {
         sym_.build_cells_from(level + 1, act, spec_cells_);
         sym_.merge_maps(cp, spec_cells_, spec_mapOff_, spec_map_);
       });
-      skel_step(cp, 2, alive, Kar, cdesc_d, &ep);
+      skel_step(cp, 2, alive, Kar, cdesc_d, eplan);
       spec.get();
       have_spec_ = (alive == alive_faces);
       tr_.mark(level, "edges");
@@ -960,10 +971,8 @@ void Builder<T>::upload_stages(bool all) {
 
 template <typename T>
 int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>& alive,
-                              DevBuf& Kar, DevBuf& cdesc_d, SkelPlan* plan) {
-  SkelPlan own;
-  if (!plan) sym_.build_skel(cp, kind, alive, own);
-  SkelPlan& sp = plan ? *plan : own;
+                              DevBuf& Kar, DevBuf& cdesc_d, std::shared_ptr<const SkelPlan> plan) {
+  const SkelPlan& sp = *plan;
   tr_.mark(level_, kind == 1 ? " symbolic faces" : " symbolic edges");
   const int nf = sp.nfront;
   if (nf == 0) return 0;
@@ -988,14 +997,12 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
     toff += (int64_t)(d.nF / 2) * (d.nF - d.nF / 2);
     F_.stats.flops += 2.0 * d.nR * (double)d.nF * d.nF;
   }
-  DevBuf rowpos_d, sd_d, G, perm_d, scratch, steps, fsc, tm;
+  DevBuf rowpos_d, sd_d, G, perm_d, steps, tm;
   upload_async(rowpos_d, sp.rowPos, &F_.mem, st_);
   upload_async(sd_d, sd, &F_.mem, st_);
   G.alloc_async(sizeof(T) * std::max<int64_t>(1, goff), &F_.mem, st_);
   perm_d.alloc_async(sizeof(int32_t) * poff, &F_.mem, st_);
-  scratch.alloc_async(sizeof(double) * 2 * poff, &F_.mem, st_);
   steps.alloc_async(sizeof(int32_t) * poff, &F_.mem, st_);
-  fsc.alloc_async(sizeof(T) * id_fscratch_elems(poff), &F_.mem, st_);
   tm.alloc(sizeof(T) * std::max<int64_t>(1, toff), &F_.mem);
   skel_gather<T>(sd_d.as<SkelDesc>(), sd.data(), nf, ncp, rowpos_d.as<int32_t>(),
                  cdesc_d.as<CellDesc>(), Kar.as<T>(), G.as<T>(), st_);
@@ -1047,9 +1054,8 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
     interpolative_decomposition<T>(sub_d[g].as<SkelDesc>(), sub[g].data(), (int)sub[g].size(),
                                    g == 0 ? G.as<T>() : Rbuf.as<T>(),
                                    (g == 0 ? G.bytes() : Rbuf.bytes()) / sizeof(T),
-                                   perm_d.as<int32_t>(),
-                                   tm.as<T>(), scratch.as<double>(), steps.as<int32_t>(),
-                                   fsc.as<T>(), F_.eps, st_);
+                                   perm_d.as<int32_t>(), tm.as<T>(), steps.as<int32_t>(), F_.eps,
+                                   st_);
     HIF_CUDA_TRY(cudaMemcpyAsync(sub[g].data(), sub_d[g].as<void>(),
                                  sizeof(SkelDesc) * sub[g].size(), cudaMemcpyDeviceToHost, st_));
   }
@@ -1061,9 +1067,7 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
   for (int g = 0; g < 2; ++g)
     for (size_t i = 0; i < sel[g].size(); ++i) sd[sel[g][i]].k = sub[g][i].k;
   tr_.mark(level_, " gather + ID");
-  scratch.release();
   steps.release();
-  fsc.release();
   Rbuf.release();
   if (prof_enabled()) {
     // algorithmic counts of the ID (§2.3): Householder pivoted QR, 4 flops
@@ -1159,8 +1163,9 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
   s.tmats = std::move(tm);
   const size_t si = F_.stages.size();
   F_.stages.push_back(std::move(s));
-  auto job = [sda, perm = std::move(perm), act, rowDof = std::move(sp.rowDof),
-              rowOff = std::move(sp.rowOff), totalF]() {
+  auto job = [sda, perm = std::move(perm), act, plan, totalF]() {
+    const auto& rowDof = plan->rowDof;
+    const auto& rowOff = plan->rowOff;
     StageHost h;
     int64_t vo = 0;
     for (const SkelDesc& d : sda) {

@@ -49,11 +49,20 @@ constexpr int ID_THREADS = 512;
 constexpr int ID_WARPS = ID_THREADS / 32;
 constexpr int NBK = 16;   // steps per block of deferred updates
 constexpr int RC = 128;   // rows of V staged in shared memory by the block update
+constexpr int CPQR_SMEM_MAX = 200 * 1024;   // dynamic shared memory of k_cpqr, bytes
+// Per-CTA state of its own columns, in dynamic shared memory (local index q
+// of column c = rank + CS q): the downdated squared norm and its reference
+// (double), the F row of the current block, and the step at which the column
+// became a pivot (-1 while it remains).
+template <typename T>
+__host__ __device__ constexpr size_t cpqr_col_bytes() {
+  return 2 * sizeof(double) + NBK * sizeof(T) + sizeof(int);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int* __restrict__ list,
                                                      T* Gar, int32_t* permAr, T* Far,
-                                                     double* scratch, int32_t* stepAr, T* Fsc,
-                                                     double eps) {
+                                                     int32_t* stepAr, double eps) {
   cg::cluster_group cl = cg::this_cluster();
   const int CS = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -64,9 +73,12 @@ __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int*
   T* M = Gar + f.idoff;             // column c at M + c*ld
   int32_t* pv = permAr + f.perm;
   int32_t* stepOf = stepAr + f.perm;
-  double* nrm = scratch + 2 * f.perm;
-  double* ref = nrm + nF;
-  T* Fm = Fsc + f.perm * NBK;       // F(c, l) at Fm[c*NBK + l]
+  const int ncq = (nF + CS - 1) / CS;   // local columns (an upper bound for every rank)
+  extern __shared__ __align__(16) unsigned char colsm[];
+  double* nrm = reinterpret_cast<double*>(colsm);   // nrm[q]
+  double* ref = nrm + ncq;
+  T* Fm = reinterpret_cast<T*>(ref + ncq);          // F(c, l) at Fm[q*NBK + l]
+  int* stepq = reinterpret_cast<int*>(Fm + (size_t)ncq * NBK);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   __shared__ double s_val[ID_WARPS];
   __shared__ int s_idx[ID_WARPS];
@@ -86,9 +98,10 @@ __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int*
   for (int c = rank + CS * warp; c < nF; c += CS * ID_WARPS) {
     const double s = warp_sumsq(M + (int64_t)c * ld, 0, m, lane);
     if (lane == 0) {
-      nrm[c] = s;
-      ref[c] = s;
-      stepOf[c] = -1;
+      const int q = (c - rank) / CS;
+      nrm[q] = s;
+      ref[q] = s;
+      stepq[q] = -1;
     }
   }
   __syncthreads();
@@ -103,8 +116,9 @@ __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int*
       double bv = -1.0;
       int bi = nF;
       for (int c = rank + CS * tid; c < nF; c += CS * ID_THREADS) {
-        if (stepOf[c] >= 0) continue;
-        const double v = nrm[c];
+        const int q = (c - rank) / CS;
+        if (stepq[q] >= 0) continue;
+        const double v = nrm[q];
         if (v > bv || (v == bv && c < bi)) {
           bv = v;
           bi = c;
@@ -169,8 +183,9 @@ __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int*
       T* cp = M + (int64_t)piv * ld;
       // 2. the owner: bring the pivot column up to date, build the reflector
       if (owner == rank) {
+        const int qp = (piv - rank) / CS;
         if (j > 0) {
-          if (tid < NBK) s_fp[tid] = tid < j ? Fm[(int64_t)piv * NBK + tid] : T(0);
+          if (tid < NBK) s_fp[tid] = tid < j ? Fm[(int64_t)qp * NBK + tid] : T(0);
           __syncthreads();
           for (int r = i + tid; r < m; r += ID_THREADS) {
             T vv[NBK];
@@ -203,7 +218,7 @@ __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int*
           s_v0_own = v0;
           cp[i] = (T)alpha;    // R_ii; v0 lives in shared memory
           pv[i] = piv;
-          stepOf[piv] = i;
+          stepq[qp] = i;
         }
         __syncthreads();
         // g_l = v_l^T v_j over rows i..m-1 (v_l is nonzero there, v_j starts at row i)
@@ -231,9 +246,10 @@ __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int*
       __syncthreads();
       const T v0 = s_v0[j], tau = s_tau[j];
       for (int c = rank + CS * warp; c < nF; c += CS * ID_WARPS) {
-        if (stepOf[c] >= 0) continue;
+        const int q = (c - rank) / CS;
+        if (stepq[q] >= 0) continue;
         T* cc = M + (int64_t)c * ld;
-        T* Fc = Fm + (int64_t)c * NBK;
+        T* Fc = Fm + (int64_t)q * NBK;
         T fl[NBK];
 #pragma unroll
         for (int l = 0; l < NBK; ++l) fl[l] = l < j ? Fc[l] : T(0);
@@ -256,8 +272,8 @@ __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int*
           cc[i] = rv;
         }
         // downdate |a_c|^2 by R_ic^2 in double; recompute when mostly cancelled
-        double nv = nrm[c] - (double)rv * (double)rv;
-        if (nv <= 1e-2 * ref[c]) {
+        double nv = nrm[q] - (double)rv * (double)rv;
+        if (nv <= 1e-2 * ref[q]) {
           double s = 0.0;
           for (int r = i + 1 + lane; r < m; r += 32) {
             T a = cc[r];
@@ -267,9 +283,9 @@ __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int*
           }
           for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
           nv = s;
-          if (lane == 0) ref[c] = s;
+          if (lane == 0) ref[q] = s;
         }
-        if (lane == 0) nrm[c] = fmax(nv, 0.0);
+        if (lane == 0) nrm[q] = fmax(nv, 0.0);
       }
       __syncthreads();
       ++i;
@@ -285,9 +301,10 @@ __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int*
         }
         __syncthreads();
         for (int c = rank + CS * warp; c < nF; c += CS * ID_WARPS) {
-          if (stepOf[c] >= 0) continue;
+          const int q = (c - rank) / CS;
+          if (stepq[q] >= 0) continue;
           T* cc = M + (int64_t)c * ld;
-          const T* Fc = Fm + (int64_t)c * NBK;
+          const T* Fc = Fm + (int64_t)q * NBK;
           T fl[NBK];
 #pragma unroll
           for (int l = 0; l < NBK; ++l) fl[l] = l < jdone ? Fc[l] : T(0);
@@ -303,6 +320,8 @@ __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int*
     }
   }
   // redundant columns, in increasing column order, follow the pivots in pv
+  for (int c = rank + CS * tid; c < nF; c += CS * ID_THREADS) stepOf[c] = stepq[(c - rank) / CS];
+  __threadfence();
   cl.sync();
   if (rank == 0 && tid == 0) {
     int t = k;
@@ -505,7 +524,6 @@ __global__ void __launch_bounds__(1024) k_cpqr_smem(SkelDesc* fr, const int* __r
 
 }  // namespace
 
-size_t id_fscratch_elems(int64_t total_front_dofs) { return (size_t)total_front_dofs * NBK; }
 
 bool id_in_shared_memory(int m, int nF, int tsize) {
   return smem_id_bytes(m, nF, tsize) <= (size_t)SMEM_ID_MAX;
@@ -513,8 +531,8 @@ bool id_in_shared_memory(int m, int nF, int tsize) {
 
 template <typename T>
 void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* Garena,
-                                 size_t arena_elems, int32_t* perm, T* Farena, double* scratch,
-                                 int32_t* stepAr, T* Fscratch, double eps, cudaStream_t st) {
+                                 size_t arena_elems, int32_t* perm, T* Farena, int32_t* stepAr,
+                                 double eps, cudaStream_t st) {
   if (nf == 0) return;
   int nsm = 0, dev = 0;
   HIF_CUDA_TRY(cudaGetDevice(&dev));
@@ -562,6 +580,8 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
   if (rest.empty()) return;
   static const bool attr_set = [] {
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_cpqr<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_cpqr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      CPQR_SMEM_MAX));
     return true;
   }();
   (void)attr_set;
@@ -596,6 +616,34 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
     const int w = wave > 0 ? wave : (int)fronts.size();
     for (size_t f0 = 0; f0 < fronts.size(); f0 += (size_t)w) {
       const int cnt = (int)std::min<size_t>((size_t)w, fronts.size() - f0);
+      int nfm = 1;
+      for (int q = 0; q < cnt; ++q) nfm = std::max(nfm, h_f[fronts[f0 + q]].nF);
+      // the CTAs' column state must fit their shared memory (a wider
+      // cluster if not); a cluster that cannot be placed with it shrinks
+      auto smem_for = [&](int cs) { return (size_t)((nfm + cs - 1) / cs) * cpqr_col_bytes<T>(); };
+      while (CS < 16 && smem_for(CS) > (size_t)CPQR_SMEM_MAX) CS = placeable[std::min(16, 2 * CS)];
+      size_t smem = 0;
+      for (;;) {
+        smem = smem_for(CS);
+        if (smem > (size_t)CPQR_SMEM_MAX)
+          throw Error{HIF_ERR_INVALID_ARG, "interpolative decomposition front too wide"};
+        if (CS == 1) break;
+        cudaLaunchConfig_t q = {};
+        q.gridDim = dim3((unsigned)CS);
+        q.blockDim = dim3(ID_THREADS);
+        q.dynamicSmemBytes = smem;
+        cudaLaunchAttribute qa[1];
+        qa[0].id = cudaLaunchAttributeClusterDimension;
+        qa[0].val.clusterDim.x = CS;
+        qa[0].val.clusterDim.y = 1;
+        qa[0].val.clusterDim.z = 1;
+        q.attrs = qa;
+        q.numAttrs = 1;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, k_cpqr<T>, &q) == cudaSuccess && ncl > 0) break;
+        cudaGetLastError();
+        --CS;
+      }
       int* d_list = nullptr;
       HIF_CUDA_TRY(cudaMallocAsync(&d_list, sizeof(int) * cnt, st));
       HIF_CUDA_TRY(cudaMemcpyAsync(d_list, fronts.data() + f0, sizeof(int) * cnt,
@@ -603,7 +651,7 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3((unsigned)(cnt * CS));
       cfg.blockDim = dim3(ID_THREADS);
-      cfg.dynamicSmemBytes = 0;
+      cfg.dynamicSmemBytes = smem;
       cfg.stream = st;
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
@@ -615,7 +663,7 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
       {
         ProfScope ps("id_cpqr", st);
         HIF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_cpqr<T>, df, (const int*)d_list, arena, perm,
-                                        Farena, scratch, stepAr, Fscratch, eps));
+                                        Farena, stepAr, eps));
         HIF_CHECK_LAUNCH();
       }
       HIF_CUDA_TRY(cudaFreeAsync(d_list, st));
@@ -674,6 +722,8 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
     double best = 1e30;
     for (int cs : {0, 1, 2, 4, 8, 16}) {   // 0: the built-in rule
       if (cs > 1 && (cs > nfmin / 8 || placeable[cs] != cs)) continue;
+      if (cs > 0 && (size_t)((nfmax + cs - 1) / cs) * cpqr_col_bytes<T>() > (size_t)CPQR_SMEM_MAX)
+        continue;
       for (int wv : waves) {
         HIF_CUDA_TRY(cudaMemcpyAsync(work, pristine, sizeof(T) * arena_elems, cudaMemcpyDeviceToDevice, st));
         HIF_CUDA_TRY(cudaMemcpyAsync(dwork, d_f, sizeof(SkelDesc) * nf, cudaMemcpyDeviceToDevice, st));
@@ -702,10 +752,9 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
 }
 
 template void interpolative_decomposition<float>(SkelDesc*, const SkelDesc*, int, float*, size_t,
-                                                 int32_t*, float*, double*, int32_t*, float*,
-                                                 double, cudaStream_t);
+                                                 int32_t*, float*, int32_t*, double, cudaStream_t);
 template void interpolative_decomposition<double>(SkelDesc*, const SkelDesc*, int, double*,
-                                                  size_t, int32_t*, double*, double*, int32_t*,
-                                                  double*, double, cudaStream_t);
+                                                  size_t, int32_t*, double*, int32_t*, double,
+                                                  cudaStream_t);
 
 }  // namespace hif

@@ -95,8 +95,21 @@ int32_t Symbolic::pos_in_cell(const CellPlan& cp, int32_t g, int cx, int cy, int
 void Symbolic::build_cells(int level, CellPlan& cp) const { build_cells_from(level, active_, cp); }
 
 void Symbolic::filter_rows(SkelPlan& sp, const std::vector<uint8_t>& alive) const {
+  SkelPlan out;
+  filter_rows(sp, alive, out);
+  sp = std::move(out);
+}
+
+void Symbolic::filter_rows(const SkelPlan& sp, const std::vector<uint8_t>& alive,
+                           SkelPlan& out) const {
   const int ncp = sp.ncellPer;
   const int nf = sp.nfront;
+  out.kind = sp.kind;
+  out.ncellPer = sp.ncellPer;
+  out.nfront = sp.nfront;
+  out.cells = sp.cells;
+  out.nF = sp.nF;
+  out.nR.assign(nf, 0);
   std::vector<int64_t> kept(nf, 0);
   parallel_for(nf, [&](int64_t f) {
     int64_t k = 0;
@@ -116,11 +129,11 @@ void Symbolic::filter_rows(SkelPlan& sp, const std::vector<uint8_t>& alive) cons
       for (int i = 0; i < ncp; ++i) pos[o * ncp + i] = sp.rowPos[r * ncp + i];
       ++o;
     }
-    sp.nR[f] = (int32_t)(kept[f] - sp.nF[f]);
+    out.nR[f] = (int32_t)(kept[f] - sp.nF[f]);
   });
-  sp.rowOff.swap(off);
-  sp.rowDof.swap(dof);
-  sp.rowPos.swap(pos);
+  out.rowOff = std::move(off);
+  out.rowDof = std::move(dof);
+  out.rowPos = std::move(pos);
 }
 
 void Symbolic::build_cells_from(int level, const std::vector<int32_t>& active, CellPlan& cp) const {

@@ -97,8 +97,10 @@ class Symbolic {
   void build_skel(const CellPlan& cp, int kind, const std::vector<uint8_t>& alive,
                   SkelPlan& sp) const;
 
-  // Drop the R rows whose DOF is no longer alive (the plan keeps its order).
+  // Drop the R rows whose DOF is no longer alive (the plan keeps its order),
+  // in place or into a new plan.
   void filter_rows(SkelPlan& sp, const std::vector<uint8_t>& alive) const;
+  void filter_rows(const SkelPlan& sp, const std::vector<uint8_t>& alive, SkelPlan& out) const;
   // build_cells from an explicit active list (sorted global ids).
   void build_cells_from(int level, const std::vector<int32_t>& active, CellPlan& cp) const;
 
