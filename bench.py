@@ -83,8 +83,10 @@ KERNEL_BOUND = {
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
 # kernel label in the bench workload, from the ncu capture summarised in
-# profiles/ (None where no capture of the current kernel exists).
-TRAFFIC_PER_LAUNCH = {}
+# profiles/ (absent where no capture of the current kernel exists):
+# id_cpqr: the six k_cpqr launches of one 128^3 factorization move 206.7 GB
+# (profiles/id_cpqr_traffic_contrast128.md).
+TRAFFIC_PER_LAUNCH = {"id_cpqr": 206.7e9 / 6}
 
 
 def _hbm_peak():

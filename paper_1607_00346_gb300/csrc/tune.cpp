@@ -53,10 +53,14 @@ void tune_gemm_set(int s, int w, int variant, const double* seconds) {
   Table& t = table();
   std::lock_guard<std::mutex> lk(t.mu);
   t.gemm[{s, w}] = variant;
-  char buf[160];
-  std::snprintf(buf, sizeof(buf), "# gemm %d %d: variant 0 %.3f ms, 1 %.3f ms, 2 %.3f ms", s, w,
-                1e3 * seconds[0], 1e3 * seconds[1], 1e3 * seconds[2]);
-  t.notes.push_back(buf);
+  std::string line = "# gemm " + std::to_string(s) + " " + std::to_string(w) + ":";
+  for (int v = 0; v < 3; ++v) {
+    char buf[48];
+    if (seconds[v] > 0.0) std::snprintf(buf, sizeof(buf), " variant %d %.3f ms", v, 1e3 * seconds[v]);
+    else std::snprintf(buf, sizeof(buf), " variant %d not a candidate", v);
+    line += buf;
+  }
+  t.notes.push_back(line);
 }
 
 bool tune_id_lookup(int wc, int cc, IdChoice* c) {

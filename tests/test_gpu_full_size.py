@@ -170,3 +170,30 @@ def test_contrast64_fp64_eight_rhs(H):
         es = _solve_error(h, A, x)
         assert es < (1e-3 if eps == 1e-4 else 1e-5), (eps, es)
         h.close()
+
+
+def test_contrast256_fp32_within_the_memory_budget(H):
+    # the 256^3 workload (N = 16,777,216): a = 10^U(-3,3) iid per point,
+    # b = 0, eps = 1e-4, FP32 factor as the preconditioner of FP64 PCG; the
+    # factorization's peak device memory stays inside the 180 GB budget and
+    # below the admission predictor, and the PCG residual is checked again
+    # with the oracle's assembled FP64 operator
+    w = inputs.workload("contrast256")
+    n, seed = w["n"], w["seed"]
+    a = inputs.make_coeff(n, w["a"], seed)
+    f = inputs.normal_rhs(n, 1, seed + 1)
+    h = H.factor(n, w["m"], _dev(a), b_const=w["b"], eps=w["eps"], precision=H.PREC_FP32)
+    st = h.stats()
+    pred = H.predict_bytes(n, w["m"], eps=w["eps"], precision=H.PREC_FP32)
+    print(f"\n[contrast256] peak {st['peak_bytes'] / 1e9:.1f} GB (predicted {pred / 1e9:.1f}), "
+          f"factor {st['factor_bytes'] / 1e9:.1f} GB, root {st['root_size']}, "
+          f"retried fronts {st['retried_fronts']}, factor {st['factor_seconds']:.2f} s")
+    assert st["levels"] == 6
+    assert st["peak_bytes"] <= 180e9 and st["peak_bytes"] <= pred
+    del a
+    A = stencil.assemble(inputs.make_coeff(n, w["a"], seed), w["b"], n)
+    its, rel, cpu_rel = _pcg_checked(h, A, f[0])
+    print(f"[contrast256] PCG {its[0]} its, relres {rel[0]:.2e}, recomputed {cpu_rel[0]:.2e}")
+    assert rel[0] <= 1e-10 and cpu_rel[0] <= 1e-10 + 1e-12
+    assert its[0] <= 40
+    h.close()
