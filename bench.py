@@ -72,6 +72,7 @@ KERNEL_BOUND = {
     "gemm_tc": "tensor", "chol_block_update_tc": "tensor", "trtri_merge_tc": "tensor",
     "chol_panel": "alu", "chol_trailing_update": "alu", "gemm_batched": "alu",
     "trtri_merge": "alu", "trtri_diag": "alu", "id_cpqr": "alu", "id_cpqr_smem": "alu",
+    "id_cpqr_dsm": "alu",
     "id_rowreduce_panel": "alu", "id_rowreduce_w1": "alu", "skel_z_products": "alu",
     "chol_block_update": "alu",
     "apply_gemv_n": "hbm", "apply_gemv_t": "hbm", "apply_sweeps_graph": "hbm",

@@ -57,6 +57,10 @@ struct SkelDesc {
   int64_t idoff;
   int idm, idld;
 };
+// the kernel that took a front's ID: the streaming cluster kernel (matrix in
+// global memory), one CTA with the matrix in its shared memory, or a cluster
+// with the matrix spread over its CTAs' shared memory
+enum : int8_t { ID_ROUTE_STREAM = 0, ID_ROUTE_SMEM = 1, ID_ROUTE_CLUSTER_SMEM = 2 };
 template <typename T>
 void skel_gather(const SkelDesc* d_f, const SkelDesc* h_f, int nf, int ncp,
                  const int32_t* rowPos, const CellDesc* d_cells, const T* Karena, T* Garena,

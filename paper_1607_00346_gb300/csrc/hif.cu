@@ -32,8 +32,7 @@ namespace hif {
 template <typename T>
 void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* Garena,
                                  size_t arena_elems, int32_t* perm, T* Farena, int32_t* stepAr,
-                                 double eps, cudaStream_t st);
-bool id_in_shared_memory(int m, int nF, int tsize);
+                                 double eps, cudaStream_t st, int8_t* route);
 template <typename T>
 void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garena, T* Rout,
                     const std::vector<int64_t>& rOff, cudaStream_t st);
@@ -1046,16 +1045,18 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
   }
   tr_.mark(level_, " gather + row reduction queued");
   std::vector<SkelDesc> sub[2];
+  std::vector<int8_t> route[2];
   DevBuf sub_d[2];
   for (int g = 0; g < 2; ++g) {
     if (sel[g].empty()) continue;
     for (int f : sel[g]) sub[g].push_back(sd[f]);
+    route[g].assign(sel[g].size(), ID_ROUTE_STREAM);
     upload_async(sub_d[g], sub[g], &F_.mem, st_);
     interpolative_decomposition<T>(sub_d[g].as<SkelDesc>(), sub[g].data(), (int)sub[g].size(),
                                    g == 0 ? G.as<T>() : Rbuf.as<T>(),
                                    (g == 0 ? G.bytes() : Rbuf.bytes()) / sizeof(T),
                                    perm_d.as<int32_t>(), tm.as<T>(), steps.as<int32_t>(), F_.eps,
-                                   st_);
+                                   st_, route[g].data());
     HIF_CUDA_TRY(cudaMemcpyAsync(sub[g].data(), sub_d[g].as<void>(),
                                  sizeof(SkelDesc) * sub[g].size(), cudaMemcpyDeviceToHost, st_));
   }
@@ -1067,6 +1068,17 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
   for (int g = 0; g < 2; ++g)
     for (size_t i = 0; i < sel[g].size(); ++i) sd[sel[g][i]].k = sub[g][i].k;
   tr_.mark(level_, " gather + ID");
+  if (tr_.on) {
+    int64_t kmx = 0, ks = 0, fs = 0;
+    for (int f = 0; f < nf; ++f) {
+      kmx = std::max<int64_t>(kmx, sd[f].k);
+      ks += sd[f].k;
+      fs += sd[f].nF;
+    }
+    std::fprintf(stderr, "[hif] level %d %s ranks: max %lld mean %.1f (%.1f%% of the DOFs kept)\n",
+                 level_, kind == 1 ? "faces" : "edges", (long long)kmx, (double)ks / nf,
+                 100.0 * (double)ks / std::max<int64_t>(1, fs));
+  }
   steps.release();
   Rbuf.release();
   if (prof_enabled()) {
@@ -1074,17 +1086,19 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
     // per entry of the trailing (idm - i) x (nF - i - 1) block at each of
     // the k steps, then T = R11^{-1} R12 (k^2 (nF - k) flops); bytes: the
     // matrix read once, T and the pivots written once
-    double fl[2] = {0.0, 0.0}, by[2] = {0.0, 0.0};
-    for (int f = 0; f < nf; ++f) {
-      const int sm = id_in_shared_memory(sd[f].idm, sd[f].nF, (int)sizeof(T)) ? 1 : 0;
-      const double k = sd[f].k, nF = sd[f].nF;
-      for (int i = 0; i < sd[f].k; ++i)
-        fl[sm] += 4.0 * (double)(sd[f].idm - i) * (sd[f].nF - i - 1);
-      fl[sm] += k * k * (nF - k);
-      by[sm] += sizeof(T) * ((double)sd[f].idm * nF + k * (nF - k)) + 4.0 * nF;
-    }
-    prof_add("id_cpqr", fl[0], by[0]);
-    prof_add("id_cpqr_smem", fl[1], by[1]);
+    double fl[3] = {0.0, 0.0, 0.0}, by[3] = {0.0, 0.0, 0.0};
+    for (int g = 0; g < 2; ++g)
+      for (size_t j = 0; j < sel[g].size(); ++j) {
+        const int f = sel[g][j], sm = route[g][j];
+        const double k = sd[f].k, nF = sd[f].nF;
+        for (int i = 0; i < sd[f].k; ++i)
+          fl[sm] += 4.0 * (double)(sd[f].idm - i) * (sd[f].nF - i - 1);
+        fl[sm] += k * k * (nF - k);
+        by[sm] += sizeof(T) * ((double)sd[f].idm * nF + k * (nF - k)) + 4.0 * nF;
+      }
+    prof_add("id_cpqr", fl[ID_ROUTE_STREAM], by[ID_ROUTE_STREAM]);
+    prof_add("id_cpqr_smem", fl[ID_ROUTE_SMEM], by[ID_ROUTE_SMEM]);
+    prof_add("id_cpqr_dsm", fl[ID_ROUTE_CLUSTER_SMEM], by[ID_ROUTE_CLUSTER_SMEM]);
   }
   // fronts with redundant DOFs are eliminated; the others keep every DOF
   std::vector<int> act;

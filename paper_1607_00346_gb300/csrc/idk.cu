@@ -522,17 +522,503 @@ __global__ void __launch_bounds__(1024) k_cpqr_smem(SkelDesc* fr, const int* __r
   }
 }
 
+// ---- fronts whose ID matrix fits in the shared memory of one cluster ---------------
+// One cluster of CS CTAs (2 to 16) per front.  Column c sits in the shared
+// memory of CTA c % CS (local column c / CS) for the whole factorization, so
+// the pivot steps read and write the matrix on chip instead of streaming it
+// from L2 or HBM once per step.  Unblocked Householder QR with column
+// pivoting, as in k_cpqr_smem: the tail norms are recomputed from the updated
+// entries in the factor precision (no downdating), and the pivot is the
+// largest norm, lowest column index on ties.  Each step:
+//   1. a cluster barrier makes the CTAs' proposals for this step (their best
+//      column with its norm, row-i entry and tail norm, pushed into every
+//      CTA's shared memory) and their column updates of the last step visible;
+//   2. every warp takes the winner among the CS proposals; every CTA copies
+//      the pivot column's rows below the step from its owner into a local
+//      buffer;
+//   3. the warps share the CTA's remaining columns (a compacted list, so the
+//      warps stay balanced as columns become pivots) and apply the reflector
+//      to them: each column segment is read into registers as 16-byte
+//      vectors, kept there between the dot product and the update, and
+//      written back once; the reflector sits in registers for all of the
+//      warp's columns; only the vectors that still hold rows below the step
+//      are touched;
+//   4. the warps' best columns meet in this CTA's proposal for the next step.
+// The proposals are double-buffered by step parity, so one cluster barrier
+// per step orders every exchange.  RPL rows per lane bound m (m <= 32 RPL).
+constexpr int DSM_THREADS = 512;
+constexpr int DSM_WARPS = DSM_THREADS / 32;
+constexpr int DSM_SMEM_MAX = 224 * 1024;   // dynamic shared memory per CTA, bytes
+constexpr int DSM_MAX_CS = 16;
+
+// rows of a column padded to whole 16-byte vectors
+__host__ __device__ inline int dsm_ld(int m, int tsize) {
+  const int ve = 16 / tsize;
+  return (m + ve - 1) / ve * ve;
+}
+
+// dynamic shared memory of one CTA of a CS-CTA cluster: its columns (ncq x
+// ldm), the pivot-column buffer (ldm), tail norms (ncq), R diagonal (kmax),
+// pivot columns (kmax ints), the list of remaining local columns and their
+// places in it (ncq ints each), and done flags (one byte per front column)
+__host__ __device__ inline size_t dsm_id_bytes(int m, int nF, int CS, int tsize) {
+  const size_t ncq = (size_t)((nF + CS - 1) / CS);
+  const size_t kmax = (size_t)(m < nF ? m : nF);
+  const size_t ldm = (size_t)dsm_ld(m, tsize);
+  const size_t b = (ncq * ldm + ldm + ncq + kmax) * tsize + (kmax + 2 * ncq) * 4 + nF;
+  return (b + 15) / 16 * 16;
+}
+
+// one 16-byte vector of shared memory <-> VE values
+__device__ __forceinline__ void ld16(float (&x)[4], const float* p) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  x[0] = v.x;
+  x[1] = v.y;
+  x[2] = v.z;
+  x[3] = v.w;
+}
+__device__ __forceinline__ void ld16(double (&x)[2], const double* p) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  x[0] = v.x;
+  x[1] = v.y;
+}
+__device__ __forceinline__ void st16(float* p, const float (&x)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+}
+__device__ __forceinline__ void st16(double* p, const double (&x)[2]) {
+  *reinterpret_cast<double2*>(p) = make_double2(x[0], x[1]);
+}
+
+template <typename T, int RPL>
+__global__ void __launch_bounds__(DSM_THREADS, 1) k_cpqr_dsm(SkelDesc* fr, const int* __restrict__ list,
+                                                          const T* __restrict__ Gar, int32_t* permAr,
+                                                          T* Far, double eps) {
+  constexpr int VE = 16 / (int)sizeof(T);   // values per 16-byte vector
+  constexpr int NV = RPL / VE;              // vectors per lane
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int fidx = list[blockIdx.x / CS];
+  SkelDesc& fref = fr[fidx];
+  const SkelDesc f = fref;
+  const int nF = f.nF, m = f.idm, ldg = f.idld;
+  const T* Mg = Gar + f.idoff;
+  int32_t* pv = permAr + f.perm;
+  T* Tm = Far + f.Tm;
+  const int ncq = (nF + CS - 1) / CS;   // local columns (an upper bound on every rank)
+  const int kmax = min(m, nF);
+  const int ldm = dsm_ld(m, (int)sizeof(T)), nvc = ldm / VE;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T* A = reinterpret_cast<T*>(dsm);              // local column q at A + q ldm
+  T* vbuf = A + (size_t)ncq * ldm;               // pivot column, row r at vbuf[r]
+  T* tail = vbuf + ldm;                          // |a_c[i+1:]|^2 of local column q
+  T* rdiag = tail + ncq;                         // R_ii
+  int* pvl = reinterpret_cast<int*>(rdiag + kmax);   // pivot column of step i
+  int* lst = pvl + kmax;                             // remaining local columns
+  int* lpos = lst + ncq;                             // place of local column q in lst
+  unsigned char* done = reinterpret_cast<unsigned char*>(lpos + ncq);   // per front column
+  __shared__ T s_wv[DSM_WARPS], s_wh[DSM_WARPS], s_wt[DSM_WARPS];
+  __shared__ int s_wc[DSM_WARPS];
+  // the CTAs' proposals, by step parity and CTA: norm, column, row-i entry,
+  // tail norm (each CTA writes its own slot in every CTA of the cluster)
+  __shared__ T s_qv[2][DSM_MAX_CS], s_qh[2][DSM_MAX_CS], s_qt[2][DSM_MAX_CS];
+  __shared__ int s_qc[2][DSM_MAX_CS];
+  __shared__ int s_nrem;
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  constexpr int nw = DSM_WARPS;
+
+  // the warps' candidates -> this CTA's proposal (largest norm, lowest
+  // column), pushed to every CTA of the cluster
+  auto propose = [&](int par, T cbv, int cbc, T cbh, T cbt) {
+    if (lane == 0) {
+      s_wv[warp] = cbv;
+      s_wc[warp] = cbc;
+      s_wh[warp] = cbh;
+      s_wt[warp] = cbt;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      T v = T(-1), h = T(0), t = T(0);
+      int c = nF;
+      if (lane < nw) {
+        v = s_wv[lane];
+        c = s_wc[lane];
+        h = s_wh[lane];
+        t = s_wt[lane];
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oc = __shfl_xor_sync(0xffffffffu, c, o);
+        const T oh = __shfl_xor_sync(0xffffffffu, h, o);
+        const T ot = __shfl_xor_sync(0xffffffffu, t, o);
+        if (ov > v || (ov == v && oc < c)) {
+          v = ov;
+          c = oc;
+          h = oh;
+          t = ot;
+        }
+      }
+      if (lane < CS) {
+        *cl.map_shared_rank(&s_qv[par][rank], lane) = v;
+        *cl.map_shared_rank(&s_qc[par][rank], lane) = c;
+        *cl.map_shared_rank(&s_qh[par][rank], lane) = h;
+        *cl.map_shared_rank(&s_qt[par][rank], lane) = t;
+      }
+    }
+  };
+
+  // copy the local columns in (zero rows up to ldm), and the norms for step 0
+  for (int e = tid; e < nF; e += DSM_THREADS) done[e] = 0;
+  for (int e = tid; e < ncq; e += DSM_THREADS) {
+    lst[e] = e;
+    lpos[e] = e;
+  }
+  if (tid == 0) s_nrem = max(0, (nF - rank + CS - 1) / CS);   // columns rank, rank + CS, ...
+  {
+    T bv = T(-1), bh = T(0), bt = T(0);
+    int bc = nF;
+    for (int q = warp; q < ncq; q += nw) {
+      const int c = rank + CS * q;
+      if (c >= nF) break;
+      const T* src = Mg + (int64_t)c * ldg;
+      T* dst = A + (size_t)q * ldm;
+      T s = T(0), head = T(0);
+      for (int r = lane; r < ldm; r += 32) {
+        const T x = r < m ? src[r] : T(0);
+        dst[r] = x;
+        if (r == 0) head = x;
+        else s = fma(x, x, s);
+      }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      head = __shfl_sync(0xffffffffu, head, 0);
+      const T full = fma(head, head, s);
+      if (lane == 0) tail[q] = s;
+      if (full > bv) {
+        bv = full;
+        bc = c;
+        bh = head;
+        bt = s;
+      }
+    }
+    for (int r = m + tid; r < ldm; r += DSM_THREADS) vbuf[r] = T(0);
+    cl.sync();   // every CTA of the cluster runs before the first proposal is pushed
+    propose(0, bv, bc, bh, bt);
+  }
+  int k = kmax;
+  T r11 = T(0);
+  for (int i = 0; i < kmax; ++i) {
+    const int cur = i & 1;
+    cl.sync();
+    // 2. the pivot: the best of the CTAs' proposals (every warp, same result)
+    T bv = T(-1), x0 = T(0), tl = T(0);
+    int p = nF;
+    if (lane < CS) {
+      bv = s_qv[cur][lane];
+      p = s_qc[cur][lane];
+      x0 = s_qh[cur][lane];
+      tl = s_qt[cur][lane];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oc = __shfl_xor_sync(0xffffffffu, p, o);
+      const T oh = __shfl_xor_sync(0xffffffffu, x0, o);
+      const T ot = __shfl_xor_sync(0xffffffffu, tl, o);
+      if (ov > bv || (ov == bv && oc < p)) {
+        bv = ov;
+        p = oc;
+        x0 = oh;
+        tl = ot;
+      }
+    }
+    const T nv = sqrt(fmax(bv, T(0)));
+    if (i == 0) r11 = nv;
+    if (p >= nF || (i == 0 ? nv == T(0) : !((double)nv > eps * (double)r11))) {
+      k = i;
+      break;
+    }
+    // reflector of column p over rows i..m-1: v = (x0 - alpha, a_p[i+1:])
+    const T nx = sqrt(fma(x0, x0, tl));
+    const T alpha = x0 >= T(0) ? -nx : nx;
+    const T v0 = x0 - alpha;
+    const T vtv = fma(v0, v0, tl);
+    const T tau = vtv > T(0) ? T(2) / vtv : T(0);
+    const int owner = p % CS, qp = p / CS;
+    {
+      const T* src = cl.map_shared_rank(A + (size_t)qp * ldm, owner);
+      for (int r = i + 1 + tid; r < m; r += DSM_THREADS) vbuf[r] = src[r];
+    }
+    if (tid == 0) {
+      rdiag[i] = alpha;
+      pvl[i] = p;
+      done[p] = 1;
+      if (owner == rank) {   // drop the pivot from the remaining columns
+        const int at = lpos[qp], last = lst[s_nrem - 1];
+        lst[at] = last;
+        lpos[last] = at;
+        --s_nrem;
+      }
+    }
+    __syncthreads();
+    // 3. the remaining local columns: a_c -= tau v (v^T a_c), new tail norms;
+    //    vectors b0 + lane + 32 t (t < tmax) hold the rows from i + 1 on, the
+    //    first lo rows of vector b0 lie above them
+    const int b0 = (i + 1) / VE, lo = i + 1 - VE * b0;
+    const int tmax = (nvc - b0 + 31) / 32;
+    T vr[NV][VE];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      const int g = b0 + lane + 32 * t;
+      if (t < tmax && g < nvc) {
+        ld16(vr[t], vbuf + (size_t)g * VE);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VE; ++e) vr[t][e] = T(0);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int e = 0; e < VE; ++e)
+        if (e < lo) vr[0][e] = T(0);
+    }
+    T cbv = T(-1), cbh = T(0), cbt = T(0);
+    int cbc = nF;
+    const int nrem = s_nrem;
+    for (int li = warp; li < nrem; li += nw) {
+      const int q = lst[li];
+      const int c = rank + CS * q;
+      T* ac = A + (size_t)q * ldm;
+      T ar[NV][VE];
+#pragma unroll
+      for (int t = 0; t < NV; ++t) {
+        const int g = b0 + lane + 32 * t;
+        if (t < tmax && g < nvc) {
+          ld16(ar[t], ac + (size_t)g * VE);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VE; ++e) ar[t][e] = T(0);
+        }
+      }
+      const T aci = ac[i];
+      T acc[VE];
+#pragma unroll
+      for (int e = 0; e < VE; ++e) acc[e] = T(0);
+#pragma unroll
+      for (int t = 0; t < NV; ++t) {
+        if (t >= tmax) break;
+#pragma unroll
+        for (int e = 0; e < VE; ++e) acc[e] = fma(vr[t][e], ar[t][e], acc[e]);
+      }
+      T w = acc[0];
+#pragma unroll
+      for (int e = 1; e < VE; ++e) w += acc[e];
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      w = fma(v0, aci, w);
+      const T tw = tau * w;
+      T sacc[VE];
+#pragma unroll
+      for (int e = 0; e < VE; ++e) sacc[e] = T(0);
+      T head = T(0);
+#pragma unroll
+      for (int t = 0; t < NV; ++t) {
+        if (t >= tmax) break;
+        T x[VE];
+#pragma unroll
+        for (int e = 0; e < VE; ++e) x[e] = fma(-vr[t][e], tw, ar[t][e]);
+        if (t == 0) {
+          // lane 0: rows above i + 1 keep their values, row i + 1 is the head
+#pragma unroll
+          for (int e = 0; e < VE; ++e) {
+            const bool above = lane == 0 && e < lo, hd = lane == 0 && e == lo;
+            if (above) x[e] = ar[0][e];
+            if (hd) head = x[e];
+            if (!above && !hd) sacc[e] = fma(x[e], x[e], sacc[e]);
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < VE; ++e) sacc[e] = fma(x[e], x[e], sacc[e]);
+        }
+        const int g = b0 + lane + 32 * t;
+        if (g < nvc) st16(ac + (size_t)g * VE, x);
+      }
+      T s = sacc[0];
+#pragma unroll
+      for (int e = 1; e < VE; ++e) s += sacc[e];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      head = __shfl_sync(0xffffffffu, head, 0);
+      const T full = fma(head, head, s);
+      __syncwarp();
+      if (lane == 0) {
+        ac[i] = fma(-v0, tw, aci);   // R_ic
+        tail[q] = s;
+      }
+      if (full > cbv || (full == cbv && c < cbc)) {
+        cbv = full;
+        cbc = c;
+        cbh = head;
+        cbt = s;
+      }
+    }
+    // 4. this CTA's proposal for step i + 1
+    propose(cur ^ 1, cbv, cbc, cbh, cbt);
+  }
+  if (rank == 0) {
+    if (tid == 0) fref.k = k;
+    for (int e = tid; e < k; e += DSM_THREADS) pv[e] = pvl[e];
+  }
+  cl.sync();   // every CTA's columns are final
+  // T = R11^{-1} R12 (k x (nF-k), ld = k): one warp per redundant local
+  // column (those left in the list), back substitution in registers;
+  // R_{l,j} sits in row l of column pvl[j] (in its owner's shared memory),
+  // R_jj in rdiag[j]; the redundant columns follow the pivots in increasing
+  // column order
+  const int nred = s_nrem;
+  for (int li = warp; li < nred; li += nw) {
+    const int q = lst[li];
+    const int c = rank + CS * q;
+    int rk = 0;
+    for (int c2 = lane; c2 < c; c2 += 32) rk += done[c2] == 0;
+    for (int o = 16; o > 0; o >>= 1) rk += __shfl_xor_sync(0xffffffffu, rk, o);
+    const T* bc = A + (size_t)q * ldm;
+    T b[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int r = lane + 32 * t;
+      b[t] = r < k ? bc[r] : T(0);
+    }
+#pragma unroll
+    for (int tt = RPL - 1; tt >= 0; --tt) {
+      if (32 * tt >= k) continue;
+      for (int jl = 31; jl >= 0; --jl) {
+        const int j = 32 * tt + jl;
+        if (j >= k) continue;
+        const T xj = __shfl_sync(0xffffffffu, b[tt], jl) / rdiag[j];
+        if (lane == jl) b[tt] = xj;
+        const int pj = pvl[j];
+        const T* rc = cl.map_shared_rank(A + (size_t)(pj / CS) * ldm, pj % CS);
+#pragma unroll
+        for (int t = 0; t <= tt; ++t) {
+          const int r = lane + 32 * t;
+          if (r < j) b[t] = fma(-xj, rc[r], b[t]);
+        }
+      }
+    }
+    T* out = Tm + (int64_t)rk * k;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int r = lane + 32 * t;
+      if (r < k) out[r] = b[t];
+    }
+    if (lane == 0) pv[k + rk] = c;
+  }
+  // no CTA leaves while another may still read its shared memory
+  cl.sync();
+}
+
+
+// k_cpqr_dsm's rows per lane for a front of m rows (0: too tall for it); the
+// widest class holds 64 registers of column data per lane, which FP64 fronts
+// would spill
+inline int dsm_rows_per_lane(int m, int tsize) {
+  return m <= 256 ? 8 : m <= 512 ? 16 : (m <= 1024 && tsize == 4) ? 32 : 0;
+}
+
+// the smallest cluster whose CTAs' shared memory holds the front (0: none)
+inline int dsm_min_cluster(int m, int nF, int tsize) {
+  for (int cs = 2; cs <= DSM_MAX_CS; ++cs)
+    if (dsm_id_bytes(m, nF, cs, tsize) <= (size_t)DSM_SMEM_MAX) return cs;
+  return 0;
+}
+
+template <typename T, int RPL>
+void dsm_attributes() {
+  static const bool set = [] {
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_cpqr_dsm<T, RPL>,
+                                      cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    HIF_CUDA_TRY(cudaFuncSetAttribute(k_cpqr_dsm<T, RPL>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, DSM_SMEM_MAX));
+    return true;
+  }();
+  (void)set;
+}
+
+// whether clusters of CS CTAs with `smem` bytes of dynamic shared memory each
+// can be placed on this GPU (asked once per shape)
+template <typename T, int RPL>
+bool dsm_placeable(int CS, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<int, size_t>, bool> known;
+  std::lock_guard<std::mutex> g(mu);
+  const auto key = std::make_pair(CS, smem);
+  const auto it = known.find(key);
+  if (it != known.end()) return it->second;
+  dsm_attributes<T, RPL>();
+  cudaLaunchConfig_t q = {};
+  q.gridDim = dim3((unsigned)CS);
+  q.blockDim = dim3(DSM_THREADS);
+  q.dynamicSmemBytes = smem;
+  cudaLaunchAttribute qa[1];
+  qa[0].id = cudaLaunchAttributeClusterDimension;
+  qa[0].val.clusterDim.x = CS;
+  qa[0].val.clusterDim.y = 1;
+  qa[0].val.clusterDim.z = 1;
+  q.attrs = qa;
+  q.numAttrs = 1;
+  int ncl = 0;
+  const bool ok = cudaOccupancyMaxActiveClusters(&ncl, k_cpqr_dsm<T, RPL>, &q) == cudaSuccess && ncl > 0;
+  cudaGetLastError();
+  known[key] = ok;
+  return ok;
+}
+
+// one launch of k_cpqr_dsm over `fronts` (all of one rows-per-lane class):
+// the smallest cluster (at least cs_min CTAs) that holds each of them and can
+// be placed; false if there is none (the caller takes the fronts elsewhere)
+template <typename T, int RPL>
+bool launch_cpqr_dsm(const std::vector<int>& fronts, const SkelDesc* h_f, SkelDesc* d_f,
+                     const T* G, int32_t* perm, T* Far, double eps, int cs_min, cudaStream_t st) {
+  if (fronts.empty()) return true;
+  int CS = std::max(2, cs_min);
+  for (int f : fronts) CS = std::max(CS, dsm_min_cluster(h_f[f].idm, h_f[f].nF, (int)sizeof(T)));
+  for (; CS <= DSM_MAX_CS; ++CS) {
+    size_t smem = 0;
+    for (int f : fronts)
+      smem = std::max(smem, dsm_id_bytes(h_f[f].idm, h_f[f].nF, CS, (int)sizeof(T)));
+    smem = (smem + 4095) / 4096 * 4096;
+    if (smem > (size_t)DSM_SMEM_MAX || !dsm_placeable<T, RPL>(CS, smem)) continue;
+    int* d_list = nullptr;
+    HIF_CUDA_TRY(cudaMallocAsync(&d_list, sizeof(int) * fronts.size(), st));
+    HIF_CUDA_TRY(cudaMemcpyAsync(d_list, fronts.data(), sizeof(int) * fronts.size(),
+                                 cudaMemcpyHostToDevice, st));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(fronts.size() * CS));
+    cfg.blockDim = dim3(DSM_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    {
+      ProfScope ps("id_cpqr_dsm", st);   // counts added by the caller (they need k)
+      HIF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_cpqr_dsm<T, RPL>, d_f, (const int*)d_list, G, perm,
+                                      Far, eps));
+      HIF_CHECK_LAUNCH();
+    }
+    HIF_CUDA_TRY(cudaFreeAsync(d_list, st));
+    return true;
+  }
+  return false;
+}
 }  // namespace
 
-
-bool id_in_shared_memory(int m, int nF, int tsize) {
-  return smem_id_bytes(m, nF, tsize) <= (size_t)SMEM_ID_MAX;
-}
 
 template <typename T>
 void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* Garena,
                                  size_t arena_elems, int32_t* perm, T* Farena, int32_t* stepAr,
-                                 double eps, cudaStream_t st) {
+                                 double eps, cudaStream_t st, int8_t* route) {
   if (nf == 0) return;
   int nsm = 0, dev = 0;
   HIF_CUDA_TRY(cudaGetDevice(&dev));
@@ -561,6 +1047,7 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
     } else {
       small[cl].push_back(f);
       small_bytes[cl] = std::max(small_bytes[cl], by);
+      if (route) route[f] = ID_ROUTE_SMEM;
     }
   }
   for (int cl = 0; cl < 3; ++cl) {
@@ -577,6 +1064,35 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
     }
     HIF_CUDA_TRY(cudaFreeAsync(d_list, st));
   }
+  // fronts that fit the shared memory of one cluster: k_cpqr_dsm, one launch
+  // per rows-per-lane class; the rest (and any class whose cluster cannot be
+  // placed) go to the streaming cluster kernel
+  {
+    std::vector<int> dsm[3], keep;
+    for (int f : rest) {
+      const int rpl = dsm_rows_per_lane(h_f[f].idm, (int)sizeof(T));
+      if (rpl > 0 && dsm_min_cluster(h_f[f].idm, h_f[f].nF, (int)sizeof(T)) > 0)
+        dsm[rpl == 8 ? 0 : rpl == 16 ? 1 : 2].push_back(f);
+      else
+        keep.push_back(f);
+    }
+    bool placed[3] = {launch_cpqr_dsm<T, 8>(dsm[0], h_f, d_f, Garena, perm, Farena, eps, 2, st),
+                      launch_cpqr_dsm<T, 16>(dsm[1], h_f, d_f, Garena, perm, Farena, eps, 2, st),
+                      true};   // the widest class is FP32 only
+    if constexpr (sizeof(T) == 4)
+      placed[2] = launch_cpqr_dsm<T, 32>(dsm[2], h_f, d_f, Garena, perm, Farena, eps, 2, st);
+    for (int c = 0; c < 3; ++c)
+      for (int f : dsm[c]) {
+        if (placed[c]) {
+          if (route) route[f] = ID_ROUTE_CLUSTER_SMEM;
+        } else {
+          keep.push_back(f);
+        }
+      }
+    rest.swap(keep);
+  }
+  if (route)
+    for (int f : rest) route[f] = ID_ROUTE_STREAM;
   if (rest.empty()) return;
   static const bool attr_set = [] {
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_cpqr<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -752,9 +1268,10 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
 }
 
 template void interpolative_decomposition<float>(SkelDesc*, const SkelDesc*, int, float*, size_t,
-                                                 int32_t*, float*, int32_t*, double, cudaStream_t);
+                                                 int32_t*, float*, int32_t*, double, cudaStream_t,
+                                                 int8_t*);
 template void interpolative_decomposition<double>(SkelDesc*, const SkelDesc*, int, double*,
                                                   size_t, int32_t*, double*, int32_t*, double,
-                                                  cudaStream_t);
+                                                  cudaStream_t, int8_t*);
 
 }  // namespace hif
