@@ -34,6 +34,9 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
                                  size_t arena_elems, int32_t* perm, T* Farena, int32_t* stepAr,
                                  double eps, cudaStream_t st, int8_t* route);
 template <typename T>
+void id_solve_t(const SkelDesc* d_f, const SkelDesc* h_f, const std::vector<int>& fronts,
+                const T* Garena, const int32_t* perm, T* Farena, cudaStream_t st);
+template <typename T>
 void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garena, T* Rout,
                     const std::vector<int64_t>& rOff, cudaStream_t st);
 
@@ -1068,6 +1071,16 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
   for (int g = 0; g < 2; ++g)
     for (size_t i = 0; i < sel[g].size(); ++i) sd[sel[g][i]].k = sub[g][i].k;
   tr_.mark(level_, " gather + ID");
+  // T = R11^{-1} R12 of the fronts the cluster kernels took (the shared-memory
+  // kernel forms its own)
+  for (int g = 0; g < 2; ++g) {
+    std::vector<int> need;
+    for (size_t i = 0; i < sel[g].size(); ++i)
+      if (route[g][i] != ID_ROUTE_SMEM && sub[g][i].k > 0 && sub[g][i].k < sub[g][i].nF)
+        need.push_back((int)i);
+    id_solve_t<T>(sub_d[g].as<SkelDesc>(), sub[g].data(), need, g == 0 ? G.as<T>() : Rbuf.as<T>(),
+                  perm_d.as<int32_t>(), tm.as<T>(), st_);
+  }
   if (tr_.on) {
     int64_t kmx = 0, ks = 0, fs = 0;
     for (int f = 0; f < nf; ++f) {
@@ -1084,8 +1097,9 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
   if (prof_enabled()) {
     // algorithmic counts of the ID (§2.3): Householder pivoted QR, 4 flops
     // per entry of the trailing (idm - i) x (nF - i - 1) block at each of
-    // the k steps, then T = R11^{-1} R12 (k^2 (nF - k) flops); bytes: the
-    // matrix read once, T and the pivots written once
+    // the k steps; in the shared-memory kernel also T = R11^{-1} R12
+    // (k^2 (nF - k) flops; id_solve_t counts it for the others); bytes: the
+    // matrix read once, T (or R) and the pivots written once
     double fl[3] = {0.0, 0.0, 0.0}, by[3] = {0.0, 0.0, 0.0};
     for (int g = 0; g < 2; ++g)
       for (size_t j = 0; j < sel[g].size(); ++j) {
@@ -1093,8 +1107,12 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
         const double k = sd[f].k, nF = sd[f].nF;
         for (int i = 0; i < sd[f].k; ++i)
           fl[sm] += 4.0 * (double)(sd[f].idm - i) * (sd[f].nF - i - 1);
-        fl[sm] += k * k * (nF - k);
-        by[sm] += sizeof(T) * ((double)sd[f].idm * nF + k * (nF - k)) + 4.0 * nF;
+        if (sm == ID_ROUTE_SMEM) {
+          fl[sm] += k * k * (nF - k);
+          by[sm] += sizeof(T) * ((double)sd[f].idm * nF + k * (nF - k)) + 4.0 * nF;
+        } else {   // the matrix read once, R (k rows) written back, pivots written
+          by[sm] += sizeof(T) * ((double)sd[f].idm * nF + (sm == ID_ROUTE_CLUSTER_SMEM ? k * nF : 0.0)) + 4.0 * nF;
+        }
       }
     prof_add("id_cpqr", fl[ID_ROUTE_STREAM], by[ID_ROUTE_STREAM]);
     prof_add("id_cpqr_smem", fl[ID_ROUTE_SMEM], by[ID_ROUTE_SMEM]);

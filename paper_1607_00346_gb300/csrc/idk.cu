@@ -1,10 +1,18 @@
 // Interpolative decomposition of A_RF for a batch of faces or edges (§2.3):
 // column-pivoted Householder QR stopped at |R_ii| <= eps |R_11|, then
-// T_F = R11^{-1} R12.
+// T_F = R11^{-1} R12.  Three kernels, by the size of the front's matrix:
+//   * k_cpqr_smem: the matrix fits one CTA's shared memory;
+//   * k_cpqr_dsm: it fits the shared memory of a 2-16 CTA cluster;
+//   * k_cpqr (below): the matrix stays in global memory and streams through
+//     the cluster once per pivot step.
+// k_cpqr_smem forms T itself; after the other two, k_id_solve_t forms T from
+// the R they leave in the matrix (blocked back substitution, many CTAs per
+// front).
 //
-// One thread-block cluster per front (1 to 16 CTAs, chosen from the front's
-// size and the batch).  Column j of the gather buffer belongs to CTA j % CS of
-// the cluster and never moves: the pivot order is kept as a permutation.
+// k_cpqr: one thread-block cluster per front (1 to 16 CTAs, chosen from the
+// front's size and the batch).  Column j of the gather buffer belongs to CTA
+// j % CS of the cluster and never moves: the pivot order is kept as a
+// permutation.
 //
 // Blocked with deferred updates (the xLAQPS scheme of LAPACK's pivoted QR):
 // within a block of NBK steps the remaining columns keep their block-start
@@ -61,8 +69,8 @@ __host__ __device__ constexpr size_t cpqr_col_bytes() {
 
 template <typename T>
 __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int* __restrict__ list,
-                                                     T* Gar, int32_t* permAr, T* Far,
-                                                     int32_t* stepAr, double eps) {
+                                                     T* Gar, int32_t* permAr, int32_t* stepAr,
+                                                     double eps) {
   cg::cluster_group cl = cg::this_cluster();
   const int CS = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -329,24 +337,7 @@ __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr(SkelDesc* fr, const int*
       if (stepOf[c] < 0 || stepOf[c] >= k) pv[t++] = c;
     fref.k = k;
   }
-  cl.sync();
-  // T = R11^{-1} R12 (k x (nF-k), ld = k): column-oriented back substitution,
-  // one warp per redundant column
-  T* Tm = Far + f.Tm;
-  for (int t = rank + CS * warp; t < nF - k; t += CS * ID_WARPS) {
-    T* b = Tm + (int64_t)t * k;
-    const T* cj = M + (int64_t)pv[k + t] * ld;
-    for (int r = lane; r < k; r += 32) b[r] = cj[r];
-    __syncwarp();
-    for (int ii = k - 1; ii >= 0; --ii) {
-      const T* rc = M + (int64_t)pv[ii] * ld;   // R[0:ii+1, ii] lives in column pv[ii]
-      const T xi = b[ii] / rc[ii];
-      __syncwarp();
-      if (lane == 0) b[ii] = xi;
-      for (int r = lane; r < ii; r += 32) b[r] = fma(-xi, rc[r], b[r]);
-      __syncwarp();
-    }
-  }
+  // T = R11^{-1} R12 follows in k_id_solve_t (R_{l,j} sits in row l of column pv[j])
 }
 
 // ---- fronts whose ID matrix fits in shared memory ---------------------------------
@@ -546,6 +537,8 @@ __global__ void __launch_bounds__(1024) k_cpqr_smem(SkelDesc* fr, const int* __r
 //   4. the warps' best columns meet in this CTA's proposal for the next step.
 // The proposals are double-buffered by step parity, so one cluster barrier
 // per step orders every exchange.  RPL rows per lane bound m (m <= 32 RPL).
+// At the end each CTA writes rows 0..k-1 of its columns (R, with R_jj in row j
+// of pivot column j) back to the matrix for k_id_solve_t.
 constexpr int DSM_THREADS = 512;
 constexpr int DSM_WARPS = DSM_THREADS / 32;
 constexpr int DSM_SMEM_MAX = 224 * 1024;   // dynamic shared memory per CTA, bytes
@@ -591,8 +584,7 @@ __device__ __forceinline__ void st16(double* p, const double (&x)[2]) {
 
 template <typename T, int RPL>
 __global__ void __launch_bounds__(DSM_THREADS, 1) k_cpqr_dsm(SkelDesc* fr, const int* __restrict__ list,
-                                                          const T* __restrict__ Gar, int32_t* permAr,
-                                                          T* Far, double eps) {
+                                                          T* Gar, int32_t* permAr, double eps) {
   constexpr int VE = 16 / (int)sizeof(T);   // values per 16-byte vector
   constexpr int NV = RPL / VE;              // vectors per lane
   cg::cluster_group cl = cg::this_cluster();
@@ -602,9 +594,8 @@ __global__ void __launch_bounds__(DSM_THREADS, 1) k_cpqr_dsm(SkelDesc* fr, const
   SkelDesc& fref = fr[fidx];
   const SkelDesc f = fref;
   const int nF = f.nF, m = f.idm, ldg = f.idld;
-  const T* Mg = Gar + f.idoff;
+  T* Mg = Gar + f.idoff;
   int32_t* pv = permAr + f.perm;
-  T* Tm = Far + f.Tm;
   const int ncq = (nF + CS - 1) / CS;   // local columns (an upper bound on every rank)
   const int kmax = min(m, nF);
   const int ldm = dsm_ld(m, (int)sizeof(T)), nvc = ldm / VE;
@@ -744,8 +735,14 @@ __global__ void __launch_bounds__(DSM_THREADS, 1) k_cpqr_dsm(SkelDesc* fr, const
     const T tau = vtv > T(0) ? T(2) / vtv : T(0);
     const int owner = p % CS, qp = p / CS;
     {
+      // whole 16-byte vectors from the one holding row i + 1 (rows above it
+      // are masked below; the column's padding rows are zero)
       const T* src = cl.map_shared_rank(A + (size_t)qp * ldm, owner);
-      for (int r = i + 1 + tid; r < m; r += DSM_THREADS) vbuf[r] = src[r];
+      for (int g = (i + 1) / VE + tid; g < nvc; g += DSM_THREADS) {
+        T x[VE];
+        ld16(x, src + (size_t)g * VE);
+        st16(vbuf + (size_t)g * VE, x);
+      }
     }
     if (tid == 0) {
       rdiag[i] = alpha;
@@ -861,59 +858,130 @@ __global__ void __launch_bounds__(DSM_THREADS, 1) k_cpqr_dsm(SkelDesc* fr, const
     // 4. this CTA's proposal for step i + 1
     propose(cur ^ 1, cbv, cbc, cbh, cbt);
   }
+  // the last step's copies and proposals are done: from here on no CTA
+  // touches another's shared memory (so each may leave when it is done)
+  cl.sync();
   if (rank == 0) {
     if (tid == 0) fref.k = k;
     for (int e = tid; e < k; e += DSM_THREADS) pv[e] = pvl[e];
   }
-  cl.sync();   // every CTA's columns are final
-  // T = R11^{-1} R12 (k x (nF-k), ld = k): one warp per redundant local
-  // column (those left in the list), back substitution in registers;
-  // R_{l,j} sits in row l of column pvl[j] (in its owner's shared memory),
-  // R_jj in rdiag[j]; the redundant columns follow the pivots in increasing
-  // column order
+  // R back to the matrix in global memory, for k_id_solve_t: rows 0..k-1 of
+  // every local column (R_{l,j} in row l of column pvl[j]), with R_jj in row j
+  // of the local pivot columns; the redundant columns follow the pivots in
+  // increasing column order
+  for (int e = tid; e < k; e += DSM_THREADS)
+    if (pvl[e] % CS == rank) A[(size_t)(pvl[e] / CS) * ldm + e] = rdiag[e];
+  __syncthreads();
+  for (int q = warp; q < ncq; q += nw) {
+    const int c = rank + CS * q;
+    if (c >= nF) break;
+    T* dst = Mg + (int64_t)c * ldg;
+    const T* src = A + (size_t)q * ldm;
+    for (int r = lane; r < k; r += 32) dst[r] = src[r];
+  }
   const int nred = s_nrem;
   for (int li = warp; li < nred; li += nw) {
-    const int q = lst[li];
-    const int c = rank + CS * q;
+    const int c = rank + CS * lst[li];
     int rk = 0;
     for (int c2 = lane; c2 < c; c2 += 32) rk += done[c2] == 0;
     for (int o = 16; o > 0; o >>= 1) rk += __shfl_xor_sync(0xffffffffu, rk, o);
-    const T* bc = A + (size_t)q * ldm;
-    T b[RPL];
-#pragma unroll
-    for (int t = 0; t < RPL; ++t) {
-      const int r = lane + 32 * t;
-      b[t] = r < k ? bc[r] : T(0);
-    }
-#pragma unroll
-    for (int tt = RPL - 1; tt >= 0; --tt) {
-      if (32 * tt >= k) continue;
-      for (int jl = 31; jl >= 0; --jl) {
-        const int j = 32 * tt + jl;
-        if (j >= k) continue;
-        const T xj = __shfl_sync(0xffffffffu, b[tt], jl) / rdiag[j];
-        if (lane == jl) b[tt] = xj;
-        const int pj = pvl[j];
-        const T* rc = cl.map_shared_rank(A + (size_t)(pj / CS) * ldm, pj % CS);
-#pragma unroll
-        for (int t = 0; t <= tt; ++t) {
-          const int r = lane + 32 * t;
-          if (r < j) b[t] = fma(-xj, rc[r], b[t]);
-        }
-      }
-    }
-    T* out = Tm + (int64_t)rk * k;
-#pragma unroll
-    for (int t = 0; t < RPL; ++t) {
-      const int r = lane + 32 * t;
-      if (r < k) out[r] = b[t];
-    }
     if (lane == 0) pv[k + rk] = c;
   }
-  // no CTA leaves while another may still read its shared memory
-  cl.sync();
 }
 
+
+// ---- T = R11^{-1} R12 for the fronts of the cluster kernels --------------------------
+// Blocked back substitution, one CTA per front and block of NC redundant
+// columns, after the ID kernel has left R in the matrix (R_{l,j} in row l of
+// column pv[j]; the redundant columns are pv[k..nF-1]).  The block of R12 (k
+// rows) sits in shared memory; from the last block of 32 rows up, the 32 x 32
+// diagonal block of R11 is solved for every column (a warp per column, lanes
+// over rows), then the solved rows update the rows above them (a thread per
+// row with its NC sums in registers, R11 read from the matrix, the solved
+// rows read from shared memory as 16-byte vectors).  Factor precision.
+constexpr int TS_THREADS = 256;
+constexpr int TS_SMEM_MAX = 200 * 1024;
+
+template <typename T, int NC>
+__host__ __device__ constexpr int ts_pitch() {
+  return NC + 16 / (int)sizeof(T);   // row pitch of the block: 16-byte rows
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(TS_THREADS) k_id_solve_t(const SkelDesc* __restrict__ fr,
+                                                           const int* __restrict__ list, int cbpf,
+                                                           const T* __restrict__ Gar,
+                                                           const int32_t* __restrict__ permAr,
+                                                           T* Far) {
+  constexpr int VE = 16 / (int)sizeof(T);
+  constexpr int BP = ts_pitch<T, NC>();
+  const int fidx = list[blockIdx.x / cbpf];
+  const int cb = (int)(blockIdx.x % cbpf);
+  const SkelDesc f = fr[fidx];
+  const int nF = f.nF, k = f.k, ld = f.idld;
+  const int nr = nF - k, t0 = cb * NC;
+  if (k == 0 || t0 >= nr) return;
+  const int nc = min(NC, nr - t0);
+  const T* M = Gar + f.idoff;
+  const int32_t* pv = permAr + f.perm;
+  T* Tm = Far + f.Tm;
+  extern __shared__ __align__(16) unsigned char tsm[];
+  T* B = reinterpret_cast<T*>(tsm);   // B[r BP + c]: row r < k of the block's column c
+  __shared__ T s_D[32][33];           // diagonal block of R11
+  __shared__ int s_pc[32];            // its columns
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  constexpr int nw = TS_THREADS / 32;
+  for (int c = warp; c < NC; c += nw) {
+    const T* src = M + (int64_t)pv[k + t0 + min(c, nc - 1)] * ld;
+    for (int r = lane; r < k; r += 32) B[(size_t)r * BP + c] = c < nc ? src[r] : T(0);
+  }
+  for (int r0 = ((k - 1) / 32) * 32; r0 >= 0; r0 -= 32) {
+    const int rn = min(32, k - r0);
+    __syncthreads();   // the last block's updates are done
+    if (tid < 32) s_pc[tid] = pv[r0 + min(tid, rn - 1)];
+    __syncthreads();
+    for (int e = tid; e < 32 * 32; e += TS_THREADS) {
+      const int i = e % 32, j = e / 32;
+      s_D[i][j] = (i < rn && j < rn && i <= j) ? M[(r0 + i) + (int64_t)s_pc[j] * ld] : T(0);
+    }
+    __syncthreads();
+    // D X = B[r0 : r0 + rn, :]
+    for (int c = warp; c < nc; c += nw) {
+      T b = lane < rn ? B[(size_t)(r0 + lane) * BP + c] : T(0);
+      for (int j = rn - 1; j >= 0; --j) {
+        const T xj = __shfl_sync(0xffffffffu, b, j) / s_D[j][j];
+        if (lane == j) b = xj;
+        else if (lane < j) b = fma(-xj, s_D[lane][j], b);
+      }
+      if (lane < rn) B[(size_t)(r0 + lane) * BP + c] = b;
+    }
+    __syncthreads();
+    // the rows above: B[r, :] -= sum_j R_{r, r0 + j} X[j, :]
+    for (int r = tid; r < r0; r += TS_THREADS) {
+      T acc[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] = B[(size_t)r * BP + c];
+      for (int j = 0; j < rn; ++j) {
+        const T rv = M[r + (int64_t)s_pc[j] * ld];
+        const T* x = B + (size_t)(r0 + j) * BP;
+#pragma unroll
+        for (int c = 0; c < NC; c += VE) {
+          T xv[VE];
+          ld16(xv, x + c);
+#pragma unroll
+          for (int e = 0; e < VE; ++e) acc[c + e] = fma(-rv, xv[e], acc[c + e]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) B[(size_t)r * BP + c] = acc[c];
+    }
+  }
+  __syncthreads();
+  for (int c = warp; c < nc; c += nw) {
+    T* dst = Tm + (int64_t)(t0 + c) * k;
+    for (int r = lane; r < k; r += 32) dst[r] = B[(size_t)r * BP + c];
+  }
+}
 
 // k_cpqr_dsm's rows per lane for a front of m rows (0: too tall for it); the
 // widest class holds 64 registers of column data per lane, which FP64 fronts
@@ -974,8 +1042,8 @@ bool dsm_placeable(int CS, size_t smem) {
 // the smallest cluster (at least cs_min CTAs) that holds each of them and can
 // be placed; false if there is none (the caller takes the fronts elsewhere)
 template <typename T, int RPL>
-bool launch_cpqr_dsm(const std::vector<int>& fronts, const SkelDesc* h_f, SkelDesc* d_f,
-                     const T* G, int32_t* perm, T* Far, double eps, int cs_min, cudaStream_t st) {
+bool launch_cpqr_dsm(const std::vector<int>& fronts, const SkelDesc* h_f, SkelDesc* d_f, T* G,
+                     int32_t* perm, double eps, int cs_min, cudaStream_t st) {
   if (fronts.empty()) return true;
   int CS = std::max(2, cs_min);
   for (int f : fronts) CS = std::max(CS, dsm_min_cluster(h_f[f].idm, h_f[f].nF, (int)sizeof(T)));
@@ -1004,7 +1072,7 @@ bool launch_cpqr_dsm(const std::vector<int>& fronts, const SkelDesc* h_f, SkelDe
     {
       ProfScope ps("id_cpqr_dsm", st);   // counts added by the caller (they need k)
       HIF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_cpqr_dsm<T, RPL>, d_f, (const int*)d_list, G, perm,
-                                      Far, eps));
+                                      eps));
       HIF_CHECK_LAUNCH();
     }
     HIF_CUDA_TRY(cudaFreeAsync(d_list, st));
@@ -1076,11 +1144,11 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
       else
         keep.push_back(f);
     }
-    bool placed[3] = {launch_cpqr_dsm<T, 8>(dsm[0], h_f, d_f, Garena, perm, Farena, eps, 2, st),
-                      launch_cpqr_dsm<T, 16>(dsm[1], h_f, d_f, Garena, perm, Farena, eps, 2, st),
+    bool placed[3] = {launch_cpqr_dsm<T, 8>(dsm[0], h_f, d_f, Garena, perm, eps, 2, st),
+                      launch_cpqr_dsm<T, 16>(dsm[1], h_f, d_f, Garena, perm, eps, 2, st),
                       true};   // the widest class is FP32 only
     if constexpr (sizeof(T) == 4)
-      placed[2] = launch_cpqr_dsm<T, 32>(dsm[2], h_f, d_f, Garena, perm, Farena, eps, 2, st);
+      placed[2] = launch_cpqr_dsm<T, 32>(dsm[2], h_f, d_f, Garena, perm, eps, 2, st);
     for (int c = 0; c < 3; ++c)
       for (int f : dsm[c]) {
         if (placed[c]) {
@@ -1179,7 +1247,7 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
       {
         ProfScope ps("id_cpqr", st);
         HIF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_cpqr<T>, df, (const int*)d_list, arena, perm,
-                                        Farena, stepAr, eps));
+                                        stepAr, eps));
         HIF_CHECK_LAUNCH();
       }
       HIF_CUDA_TRY(cudaFreeAsync(d_list, st));
@@ -1273,5 +1341,56 @@ template void interpolative_decomposition<float>(SkelDesc*, const SkelDesc*, int
 template void interpolative_decomposition<double>(SkelDesc*, const SkelDesc*, int, double*,
                                                   size_t, int32_t*, double*, int32_t*, double,
                                                   cudaStream_t, int8_t*);
+
+
+template <typename T>
+void id_solve_t(const SkelDesc* d_f, const SkelDesc* h_f, const std::vector<int>& fronts,
+                const T* Garena, const int32_t* perm, T* Farena, cudaStream_t st) {
+  if (fronts.empty()) return;
+  int kmax = 1, nrmax = 1;
+  for (int f : fronts) {
+    kmax = std::max(kmax, h_f[f].k);
+    nrmax = std::max(nrmax, h_f[f].nF - h_f[f].k);
+  }
+  auto bytes = [&](int pitch) { return (size_t)kmax * pitch * sizeof(T); };
+  int* d_list = nullptr;
+  HIF_CUDA_TRY(cudaMallocAsync(&d_list, sizeof(int) * fronts.size(), st));
+  HIF_CUDA_TRY(cudaMemcpyAsync(d_list, fronts.data(), sizeof(int) * fronts.size(),
+                               cudaMemcpyHostToDevice, st));
+  auto run = [&](auto kern, int nc, size_t smem) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> g(mu);
+    HIF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TS_SMEM_MAX));
+    const int cbpf = ceil_div(nrmax, nc);
+    // k^2 (nF - k) flops; R11 and R12 read, T written
+    double fl = 0.0, by = 0.0;
+    if (prof_enabled())
+      for (int f : fronts) {
+        const double k = h_f[f].k, nr = h_f[f].nF - h_f[f].k;
+        fl += k * k * nr;
+        by += sizeof(T) * (0.5 * k * k + 2.0 * k * nr);
+      }
+    ProfScope ps("id_solve_t", st, fl, by);
+    kern<<<(unsigned)(fronts.size() * cbpf), TS_THREADS, smem, st>>>(d_f, d_list, cbpf, Garena,
+                                                                     perm, Farena);
+    HIF_CHECK_LAUNCH();
+  };
+  if (bytes(ts_pitch<T, 32>()) <= (size_t)TS_SMEM_MAX)
+    run(k_id_solve_t<T, 32>, 32, bytes(ts_pitch<T, 32>()));
+  else if (bytes(ts_pitch<T, 16>()) <= (size_t)TS_SMEM_MAX)
+    run(k_id_solve_t<T, 16>, 16, bytes(ts_pitch<T, 16>()));
+  else if (bytes(ts_pitch<T, 8>()) <= (size_t)TS_SMEM_MAX)
+    run(k_id_solve_t<T, 8>, 8, bytes(ts_pitch<T, 8>()));
+  else if (bytes(ts_pitch<T, 4>()) <= (size_t)TS_SMEM_MAX)
+    run(k_id_solve_t<T, 4>, 4, bytes(ts_pitch<T, 4>()));
+  else
+    throw Error{HIF_ERR_INVALID_ARG, "interpolative decomposition rank too large"};
+  HIF_CUDA_TRY(cudaFreeAsync(d_list, st));
+}
+
+template void id_solve_t<float>(const SkelDesc*, const SkelDesc*, const std::vector<int>&,
+                                const float*, const int32_t*, float*, cudaStream_t);
+template void id_solve_t<double>(const SkelDesc*, const SkelDesc*, const std::vector<int>&,
+                                 const double*, const int32_t*, double*, cudaStream_t);
 
 }  // namespace hif
