@@ -74,6 +74,10 @@ KERNEL_BOUND = {
     "trtri_merge": "alu", "trtri_diag": "alu", "id_cpqr": "alu", "id_cpqr_smem": "alu",
     "id_cpqr_dsm": "alu",
     "id_rowreduce_panel": "alu", "id_rowreduce_w1": "alu", "skel_z_products": "alu",
+    "id_rowreduce_block_tc": "tensor", "id_rowreduce_block": "alu", "id_rowreduce_blockt": "alu",
+    "id_rowreduce_gram_tc": "tensor", "id_rowreduce_gram": "alu", "id_rowreduce_vta_tc": "tensor",
+    "id_rowreduce_vta": "alu", "id_rowreduce_tw_tc": "tensor", "id_rowreduce_tw": "alu",
+    "id_solve_t": "alu",
     "chol_block_update": "alu",
     "apply_gemv_n": "hbm", "apply_gemv_t": "hbm", "apply_sweeps_graph": "hbm",
     "apply_gather": "hbm", "apply_scatter": "hbm", "apply_accumulate": "hbm",
@@ -546,7 +550,7 @@ def main():
                  if k in ("kernel", "bound", "achieved", "frac", "share", "unit")}
                 for r in roof_top], "cpu_baseline": cpu, "fp64_form": fp64_form,
             "kernels": {p["name"]: round(p["seconds"] / args.steps, 5) for p in
-                        sorted(prof, key=lambda p: -p["seconds"])[:12]},
+                        sorted(prof, key=lambda p: -p["seconds"])[:24]},
             "peaks": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in peaks.items()},
             "autotune": tune,
         }

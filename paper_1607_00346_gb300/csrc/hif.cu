@@ -38,7 +38,8 @@ void id_solve_t(const SkelDesc* d_f, const SkelDesc* h_f, const std::vector<int>
                 const T* Garena, const int32_t* perm, T* Farena, cudaStream_t st);
 template <typename T>
 void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garena, T* Rout,
-                    const std::vector<int64_t>& rOff, cudaStream_t st);
+                    const std::vector<int64_t>& rOff, int* d_flags, bool tensor_cores,
+                    cudaStream_t st);
 
 namespace {
 thread_local std::string g_last_error;
@@ -1022,7 +1023,8 @@ int64_t Builder<T>::skel_step(const CellPlan& cp, int kind, std::vector<uint8_t>
       rtot += (int64_t)sd[sel[1][i]].nF * sd[sel[1][i]].nF;
     }
     Rbuf.alloc_async(sizeof(T) * rtot, &F_.mem, st_);
-    reduce_rows_qr<T>(sd.data(), sel[1], G.as<T>(), Rbuf.as<T>(), roff, st_);
+    reduce_rows_qr<T>(sd.data(), sel[1], G.as<T>(), Rbuf.as<T>(), roff, flags_.as<int>(),
+                      F_.opt.tensor_cores != 0, st_);
     for (size_t i = 0; i < sel[1].size(); ++i) {
       SkelDesc& d = sd[sel[1][i]];
       d.idoff = roff[i];

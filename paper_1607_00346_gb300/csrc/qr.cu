@@ -10,13 +10,18 @@
 // then runs on the small square R.
 //
 // Blocked Householder QR, panel by panel (32 columns):
-//   * k_qr_panel (one CTA per front): Householder reflectors of the panel's
-//     columns (norms accumulated in double), the explicit reflector matrix V
-//     and the triangular T of the compact form Q = I - V T V^T (forward
-//     accumulation: T_{j+1} = [T_j, -tau_j T_j V_j^T v_j; 0, tau_j]);
+//   * the panel: Householder reflectors of its columns, the explicit
+//     reflector matrix V and the triangular T of the compact form
+//     Q = I - V T V^T (forward accumulation: T_{j+1} = [T_j, -tau_j T_j
+//     V_j^T v_j; 0, tau_j]); k_qr_panel_cluster keeps the panel in the shared
+//     memory of a cluster (row slices, one exchange per column), k_qr_panel
+//     (one CTA per front, the panel in global memory, norms in double) takes
+//     panels too tall for 16 CTAs;
 //   * trailing columns: W = T^T V^T A and A -= V W, two kernels that stream
 //     the trailing columns from HBM once each (k_qr_w1/k_qr_w2, k_qr_update).
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <cstdlib>
 #include <type_traits>
 #include <vector>
@@ -35,6 +40,14 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int QB = 32;          // panel width
+constexpr int QB2 = 128;        // block width: trailing columns are updated once per block
+
+// Panel p (32 columns) of the block starting at p0 keeps its reflectors in
+// the block's V (rows relative to p0, ld = m): column p - p0 on, row p - p0 on,
+// so V(r, j) of the panel (r relative to p) sits at V + voff + r + j m; its T
+// is the ((p - p0) / 32)-th 32 x 32 matrix of the block's four.
+__host__ __device__ inline int64_t qr_voff(int p, int p0, int m) { return (int64_t)(p - p0) * (m + 1); }
+__host__ __device__ inline int64_t qr_toff(int p, int p0) { return (int64_t)((p - p0) / QB) * QB * QB; }
 constexpr int QR_THREADS = 512;
 constexpr int QR_WARPS = QR_THREADS / 32;
 
@@ -49,13 +62,13 @@ struct QRDesc {
 
 template <typename T>
 __global__ void __launch_bounds__(QR_THREADS) k_qr_panel(const QRDesc* __restrict__ ds, T* Gar,
-                                                         T* Var, T* Tar, int p) {
+                                                         T* Var, T* Tar, int p, int p0) {
   const QRDesc d = ds[blockIdx.x];
   if (p >= d.n) return;
   const int jb = min(QB, d.n - p);
   const int m = d.m, ld = d.ld;
   T* A = Gar + d.A;
-  T* V = Var + d.V;
+  T* V = Var + d.V + qr_voff(p, p0, m);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   __shared__ double s_red[QR_WARPS];
   __shared__ double s_tau[QB], s_v0[QB];
@@ -87,8 +100,8 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_panel(const QRDesc* __restric
     }
     __syncthreads();
     const T v0 = (T)s_v0[j], tau = (T)s_tau[j];
-    // explicit reflector column j of V (rows p..m-1)
-    for (int r = p + tid; r < m; r += QR_THREADS)
+    // explicit reflector column j of V (rows p0..m-1 of the block's V)
+    for (int r = p0 + tid; r < m; r += QR_THREADS)
       V[(r - p) + (int64_t)j * m] = r < c ? T(0) : (r == c ? v0 : col[r]);
     // the rest of the panel
     for (int jj = j + 1 + warp; jj < jb; jj += QR_WARPS) {
@@ -127,7 +140,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_panel(const QRDesc* __restric
     }
   }
   __syncthreads();
-  T* Tt = Tar + d.Tt;
+  T* Tt = Tar + d.Tt + qr_toff(p, p0);
   for (int e = tid; e < QB * QB; e += QR_THREADS) {
     const int i = e % QB, j = e / QB;
     Tt[e] = (i < jb && j < jb) ? (T)s_T[i][j] : T(0);
@@ -136,22 +149,35 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_panel(const QRDesc* __restric
 
 // The same panel factorization spread over a thread-block cluster: the
 // panel's active rows (p..m-1) are split into CS contiguous slices held in
-// the shared memory of the cluster's CTAs.  Per column: each CTA adds up its
-// slice's part of the tail norm, the parts meet in distributed shared memory
-// and every warp forms the same reflector from them (added by a fixed
-// butterfly across lanes, one lane per CTA); then each CTA computes its
-// slice's part of the reflector's products with the remaining panel
-// columns (summed over each warp's lanes by a transposing butterfly), the
-// parts meet again, and each CTA updates its slice.  Two cluster barriers per
-// column; the panel is read and written once.  Sums run in the factor
-// precision (FP64 arithmetic is slow here).
-constexpr int QRC_THREADS = 256;
-constexpr int QRC_WARPS = QRC_THREADS / 32;
+// the shared memory of the cluster's CTAs.  One exchange per column: before
+// column j is reduced, every CTA holds its slice's parts (rows below j) of
+// the tail norm |a_j|^2, of the products a_j^T a_jj with the remaining panel
+// columns (jj > j) and of v_l^T a_j with the earlier reflectors (l < j), and
+// pushes them into every CTA's shared memory (the owner of row j also pushes
+// that row).  After one cluster barrier every CTA adds the CS parts in the
+// same order and forms the same reflector, the same w_jj = v^T a_jj =
+// v0 a_jj[j] + (a_j^T a_jj below j) and the same column j of T
+// (T[0:j, j] = -tau_j T[0:j, 0:j] V^T v_j, with v_l^T v_j = v_l[j] v0 +
+// (v_l^T a_j below j)).  The pass that then updates the slice
+// (a_jj -= tau w_jj v) also takes the parts for column j + 1 from the updated
+// entries.  Per column: one cluster barrier, two CTA barriers, one read and
+// write of the slice; the parts are double-buffered by column parity.  Sums
+// run in the factor precision (FP64 arithmetic is slow here).
+constexpr int QRC_MAX_CS = 16;
+constexpr int QRC_MAX_WARPS = 16;
+// threads per CTA: 512 in FP32; 256 in FP64 (each thread keeps 64 sums and
+// reflector weights in registers)
+template <typename T>
+__host__ __device__ constexpr int qrc_threads() {
+  return sizeof(T) == 4 ? 512 : 256;
+}
 
 template <typename T>
-__global__ void __launch_bounds__(QRC_THREADS) k_qr_panel_cluster(const QRDesc* __restrict__ ds,
-                                                                 T* Gar, T* Var, T* Tar, int p,
-                                                                 int rb) {
+__global__ void __launch_bounds__(qrc_threads<T>()) k_qr_panel_cluster(const QRDesc* __restrict__ ds,
+                                                                      T* Gar, T* Var, T* Tar,
+                                                                      int p, int p0, int rb) {
+  constexpr int QRC_THREADS = qrc_threads<T>();
+  constexpr int QRC_WARPS = QRC_THREADS / 32;
   cg::cluster_group cl = cg::this_cluster();
   const int CS = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -161,72 +187,31 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_panel_cluster(const QRDesc* 
   const int m = d.m, ld = d.ld, mp = m - p;
   const int r0 = rank * rb, r1 = min(mp, r0 + rb);   // this CTA's rows, relative to p
   T* A = Gar + d.A;
-  T* V = Var + d.V;
+  T* V = Var + d.V + qr_voff(p, p0, m);
   extern __shared__ __align__(16) unsigned char qsm[];
   T* P = reinterpret_cast<T*>(qsm);                  // slice: P[i + j rb], i = row - p - r0
-  __shared__ T s_nrm[2], s_x0[2];                    // this CTA's parts, by column parity
-  __shared__ T s_dot[2][QB];
-  __shared__ T s_red[QRC_WARPS][QB];
-  __shared__ T s_G[QB][QB + 1];                      // Gram matrix parts, then the sum
-  __shared__ double s_tau[QB], s_v0[QB];
-  __shared__ double s_T[QB][QB + 1];
-  __shared__ double s_Gsum[QB][QB + 1];
-  __shared__ T s_w[QB];                              // tau w_jj of the current column
+  // parts pushed by every CTA, by column parity: [CTA][jj] = the slice's sum
+  // below row j of a_j a_jj (jj > j), a_j^2 (jj = j) or v_jj a_j (jj < j)
+  __shared__ T s_part[2][QRC_MAX_CS][QB];
+  __shared__ T s_row[2][QB];                         // row j of the panel
+  __shared__ T s_red[QRC_MAX_WARPS][QB];
+  __shared__ T s_sum[QB];
+  __shared__ T s_tw[QB];                             // tau w_jj of the current column
+  __shared__ T s_v0[QB];
+  __shared__ T s_T[QB][QB + 1];
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int nr = max(0, r1 - r0);
   for (int e = tid; e < nr * jb; e += QRC_THREADS) {
     const int i = e % nr, j = e / nr;
-    P[i + (int64_t)j * rb] = A[(p + r0 + i) + (int64_t)(p + j) * ld];
+    P[i + j * rb] = A[(p + r0 + i) + (int64_t)(p + j) * ld];
   }
-  __syncthreads();
-  // thread tid owns the slice rows i = tid + QRC_THREADS k throughout, so
-  // the column updates and the next column's norm part need no barrier
-  T s = T(0);   // this thread's part of the tail norm of the current column
-  for (int i = tid; i < nr; i += QRC_THREADS)
-    if (r0 + i > 0) s = fma(P[i], P[i], s);
-  for (int j = 0; j < jb; ++j) {
-    const int par = j & 1;
-    // 1. tail norm parts (rows below the diagonal) and x0 from its owner meet
-    //    in distributed shared memory; every warp forms the same reflector
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) s_red[warp][0] = s;
-    __syncthreads();
-    if (tid == 0) {
-      T t = T(0);
-      for (int w = 0; w < QRC_WARPS; ++w) t += s_red[w][0];
-      s_nrm[par] = t;
-      if (j >= r0 && j < r1) s_x0[par] = P[(j - r0) + (int64_t)j * rb];
-    }
-    cl.sync();
-    T tail = lane < CS ? *cl.map_shared_rank(&s_nrm[par], lane) : T(0);
-    for (int o = 16; o > 0; o >>= 1) tail += __shfl_xor_sync(0xffffffffu, tail, o);
-    const T x0 = *cl.map_shared_rank(&s_x0[par], min(CS - 1, j / rb));
-    const T nx = sqrt(fma(x0, x0, tail));
-    const T alpha = x0 >= T(0) ? -nx : nx;
-    const T v0 = x0 - alpha;
-    const T vtv = fma(v0, v0, tail);
-    const T tau = vtv > T(0) ? T(2) / vtv : T(0);
-    if (tid == 0) {
-      s_tau[j] = (double)tau;
-      s_v0[j] = (double)v0;
-      if (j >= r0 && j < r1) P[(j - r0) + (int64_t)j * rb] = alpha;   // R_jj (v0 is kept apart)
-    }
-    const int nrem = jb - j - 1;
-    if (nrem == 0) break;
-    // 2. parts of w_jj = v^T a_jj for the remaining panel columns (v = v0 at
-    //    row j, the column's entries below it), summed over the warp by a
-    //    transposing butterfly (lane l ends with column l)
-    T acc[QB];
-#pragma unroll
-    for (int jj = 0; jj < QB; ++jj) acc[jj] = T(0);
-    for (int i = tid; i < nr; i += QRC_THREADS) {
-      const int row = r0 + i;
-      if (row < j) continue;
-      const T vi = row == j ? v0 : P[i + (int64_t)j * rb];
-#pragma unroll
-      for (int jj = 0; jj < QB; ++jj)
-        if (jj > j && jj < jb) acc[jj] = fma(vi, P[i + (int64_t)jj * rb], acc[jj]);
-    }
+  for (int e = tid; e < QB * (QB + 1); e += QRC_THREADS) (&s_T[0][0])[e] = T(0);
+  cl.sync();   // every CTA runs (and holds its slice) before the first push
+
+  // sum acc[] over the warp (lane l ends with entry l), then over the warps;
+  // push column c's parts (and row c from its owner) into every CTA
+  T acc[QB];
+  auto push = [&](int c, int par, T r_prev) {
 #pragma unroll
     for (int o = QB / 2; o > 0; o >>= 1) {
       const bool up = (lane & o) != 0;
@@ -239,90 +224,122 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_panel_cluster(const QRDesc* 
     }
     s_red[warp][lane] = acc[0];
     __syncthreads();
+    if (tid == 2 * QB && c >= 1 && c - 1 >= r0 && c - 1 < r1)   // R of the column just reduced
+      P[(c - 1 - r0) + (c - 1) * rb] = r_prev;
     if (tid < QB) {
       T t = T(0);
       for (int w = 0; w < QRC_WARPS; ++w) t += s_red[w][tid];
-      s_dot[par][tid] = t;
+      for (int q = 0; q < CS; ++q) *cl.map_shared_rank(&s_part[par][rank][tid], q) = t;
+    } else if (tid < 2 * QB && c >= r0 && c < r1) {
+      const int jj = tid - QB;
+      const T x = jj < jb ? P[(c - r0) + jj * rb] : T(0);
+      for (int q = 0; q < CS; ++q) *cl.map_shared_rank(&s_row[par][jj], q) = x;
     }
-    cl.sync();
-    // warp w adds the cluster's parts of columns w + QRC_WARPS q
-    for (int jj = warp; jj < QB; jj += QRC_WARPS) {
-      T t = lane < CS ? *cl.map_shared_rank(&s_dot[par][jj], lane) : T(0);
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) s_w[jj] = tau * t;
+  };
+
+  // parts of column 0
+#pragma unroll
+  for (int jj = 0; jj < QB; ++jj) acc[jj] = T(0);
+  for (int i = tid; i < nr; i += QRC_THREADS) {
+    if (r0 + i == 0) continue;
+    const T x = P[i];
+    acc[0] = fma(x, x, acc[0]);
+#pragma unroll
+    for (int jj = 1; jj < QB; ++jj)
+      if (jj < jb) acc[jj] = fma(x, P[i + jj * rb], acc[jj]);
+  }
+  push(0, 0, T(0));
+  for (int j = 0; j < jb; ++j) {
+    const int par = j & 1;
+    cl.sync();   // column j's parts are in every CTA
+    if (tid < QB) {
+      T t = T(0);
+      for (int q = 0; q < CS; ++q) t += s_part[par][q][tid];
+      s_sum[tid] = t;
     }
     __syncthreads();
-    // 3. update the slice, a_jj -= (tau w_jj) v, and take this thread's part
-    //    of the next column's tail norm on the way
-    s = T(0);
+    const T x0 = s_row[par][j], tail = s_sum[j];
+    const T nx = sqrt(fma(x0, x0, tail));
+    const T alpha = x0 >= T(0) ? -nx : nx;
+    const T v0 = x0 - alpha;
+    const T vtv = fma(v0, v0, tail);
+    const T tau = vtv > T(0) ? T(2) / vtv : T(0);
+    if (tid < QB) {
+      s_tw[tid] = (tid > j && tid < jb) ? tau * fma(v0, s_row[par][tid], s_sum[tid]) : T(0);
+    } else if (tid < 2 * QB) {
+      // column j of T: row l < j is -tau sum_{i=l}^{j-1} T[l][i] v_i^T v_j
+      const int l = tid - QB;
+      if (l < j) {
+        T t = T(0);
+        for (int i2 = l; i2 < j; ++i2) t = fma(s_T[l][i2], fma(s_row[par][i2], v0, s_sum[i2]), t);
+        s_T[l][j] = -tau * t;
+      } else if (l == j) {
+        s_T[j][j] = tau;
+        s_v0[j] = v0;
+      }
+    }
+    __syncthreads();
+    if (j + 1 == jb) {
+      if (tid == 0 && j >= r0 && j < r1) P[(j - r0) + j * rb] = alpha;   // R_jj
+      break;
+    }
+    // a_jj -= (tau w_jj) v on the slice's rows from j on, and the parts of
+    // column j + 1 from the updated entries (rows below j + 1)
+    T tw[QB];
+#pragma unroll
+    for (int jj = 0; jj < QB; ++jj) tw[jj] = s_tw[jj];
+    const T twn = s_tw[j + 1];
+#pragma unroll
+    for (int jj = 0; jj < QB; ++jj) acc[jj] = T(0);
+    T tl = T(0);
     for (int i = tid; i < nr; i += QRC_THREADS) {
       const int row = r0 + i;
       if (row < j) continue;
-      const T vi = row == j ? v0 : P[i + (int64_t)j * rb];
-      for (int jj = j + 1; jj < jb; ++jj) {
-        const T x = fma(-s_w[jj], vi, P[i + (int64_t)jj * rb]);
-        P[i + (int64_t)jj * rb] = x;
-        if (jj == j + 1 && row > j + 1) s = fma(x, x, s);
+      const T vi = row == j ? v0 : P[i + j * rb];
+      const T xj1 = fma(-twn, vi, P[i + (j + 1) * rb]);
+      P[i + (j + 1) * rb] = xj1;
+      const T xn = row > j + 1 ? xj1 : T(0);
+      tl = fma(xn, xn, tl);
+#pragma unroll
+      for (int jj = 0; jj < QB; ++jj) {
+        if (jj < jb && jj != j + 1) {
+          T x = P[i + jj * rb];
+          if (jj > j + 1) {
+            x = fma(-tw[jj], vi, x);
+            P[i + jj * rb] = x;
+          }
+          acc[jj] = fma(xn, x, acc[jj]);
+        }
       }
     }
+#pragma unroll
+    for (int jj = 0; jj < QB; ++jj)
+      if (jj == j + 1) acc[jj] = tl;
+    push(j + 1, par ^ 1, alpha);   // also R_jj = alpha
   }
   __syncthreads();
   // reflectors to V (rows p..m-1, zeros above each diagonal), the slice back
-  // to A, and this slice's part of the Gram matrix V^T V
+  // to A, and T from the first CTA
   for (int e = tid; e < nr * QB; e += QRC_THREADS) {
     const int i = e % nr, j = e / nr, row = r0 + i;
     T v = T(0);
     if (j < jb) {
-      if (row == j) v = (T)s_v0[j];
-      else if (row > j) v = P[i + (int64_t)j * rb];
-      A[(p + row) + (int64_t)(p + j) * ld] = P[i + (int64_t)j * rb];
+      if (row == j) v = s_v0[j];
+      else if (row > j) v = P[i + j * rb];
+      A[(p + row) + (int64_t)(p + j) * ld] = P[i + j * rb];
     }
     V[row + (int64_t)j * m] = v;
   }
-  for (int e = warp; e < jb * jb; e += QRC_WARPS) {
-    const int a = e % jb, b = e / jb;
-    if (a > b) continue;
-    T g = T(0);
-    for (int i = lane; i < nr; i += 32) {
-      const int row = r0 + i;
-      const T va = row == a ? (T)s_v0[a] : (row > a ? P[i + (int64_t)a * rb] : T(0));
-      const T vb = row == b ? (T)s_v0[b] : (row > b ? P[i + (int64_t)b * rb] : T(0));
-      g = fma(va, vb, g);
-    }
-    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-    if (lane == 0) {
-      s_G[a][b] = g;
-      s_G[b][a] = g;
-    }
-  }
-  cl.sync();
   if (rank == 0) {
-    for (int e = tid; e < jb * jb; e += QRC_THREADS) {
-      const int a = e % jb, b = e / jb;
-      double t = 0.0;
-      for (int q2 = 0; q2 < CS; ++q2) t += (double)*cl.map_shared_rank(&s_G[a][b], q2);
-      s_Gsum[a][b] = t;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      for (int j = 0; j < jb; ++j) {
-        for (int i = 0; i < QB; ++i) s_T[i][j] = 0.0;
-        s_T[j][j] = s_tau[j];
-        for (int i = 0; i < j; ++i) {
-          double t = 0.0;
-          for (int l = i; l < j; ++l) t += s_T[i][l] * s_Gsum[l][j];
-          s_T[i][j] = -s_tau[j] * t;
-        }
-      }
-    }
-    __syncthreads();
-    T* Tt = Tar + d.Tt;
+    // the block's rows above the panel: zero in the panel's reflectors
+    const int vtop = p - p0;
+    for (int e = tid; e < vtop * QB; e += QRC_THREADS) V[(e % vtop - vtop) + (int64_t)(e / vtop) * m] = T(0);
+    T* Tt = Tar + d.Tt + qr_toff(p, p0);
     for (int e = tid; e < QB * QB; e += QRC_THREADS) {
       const int i = e % QB, j = e / QB;
-      Tt[e] = (i < jb && j < jb) ? (T)s_T[i][j] : T(0);
+      Tt[e] = (i < jb && j < jb) ? s_T[i][j] : T(0);
     }
   }
-  cl.sync();   // no CTA leaves while others may still read its shared memory
 }
 
 // R (n x n, ld = n, zeros below the diagonal) from rows 0..n-1 of the factored matrix
@@ -402,18 +419,18 @@ constexpr size_t w1_smem_bytes() {
 template <typename T>
 __global__ void __launch_bounds__(W1_THREADS, sizeof(T) == 4 ? 2 : 1)
     k_qr_w1(const QRDesc* __restrict__ ds, const T* __restrict__ Gar, const T* __restrict__ Var,
-            T* Wp, const int64_t* __restrict__ wpo, int p, int S) {
+            T* Wp, const int64_t* __restrict__ wpo, int p, int p0, int S) {
   const QRDesc d = ds[blockIdx.y];
   if (p >= d.n) return;
   const int jb = min(QB, d.n - p);
-  const int nt = d.n - p - jb;
+  const int nt = min(d.n, p0 + QB2) - p - jb;   // the block's columns right of the panel
   const int c0 = (int)(blockIdx.x / S) * W1_NC, s = (int)(blockIdx.x % S);
   if (nt <= 0 || c0 >= nt) return;
   const int mp = d.m - p;
   const int nch = (mp + W1_KC - 1) / W1_KC;
   const int kc0 = (int)((int64_t)nch * s / S), kc1 = (int)((int64_t)nch * (s + 1) / S);
   const T* A = Gar + d.A + p + (int64_t)(p + jb) * d.ld;   // A_t(0, 0)
-  const T* V = Var + d.V;                                   // V(r, j) = V[r + j m]
+  const T* V = Var + d.V + qr_voff(p, p0, d.m);            // V(r, j) = V[r + j m]
   extern __shared__ __align__(16) unsigned char w1sm[];
   T* ring = reinterpret_cast<T*>(w1sm);   // stage: As[k W1_AP + c], then Vs[k W1_VP + j]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -497,13 +514,14 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_qr_w2(const QRDesc* __restrict__ ds,
                                                const T* __restrict__ Wp,
                                                const int64_t* __restrict__ wpo,
-                                               const T* __restrict__ Tar, T* War, int p, int S) {
+                                               const T* __restrict__ Tar, T* War, int p, int p0,
+                                               int S) {
   const QRDesc d = ds[blockIdx.y];
   if (p >= d.n) return;
   const int jb = min(QB, d.n - p);
-  const int nt = d.n - p - jb;
+  const int nt = min(d.n, p0 + QB2) - p - jb;
   __shared__ T Ts[QB][QB + 1];   // Ts[i][j] = T(i, j)
-  const T* Tt = Tar + d.Tt;
+  const T* Tt = Tar + d.Tt + qr_toff(p, p0);
   for (int e = threadIdx.x; e < QB * QB; e += 128) Ts[e % QB][e / QB] = Tt[e];
   __syncthreads();
   const int c = blockIdx.x * 128 + threadIdx.x;
@@ -530,17 +548,17 @@ __global__ void __launch_bounds__(128) k_qr_w2(const QRDesc* __restrict__ ds,
 template <typename T>
 __global__ void __launch_bounds__(256) k_qr_update(const QRDesc* __restrict__ ds, T* Gar,
                                                    const T* __restrict__ Var,
-                                                   const T* __restrict__ War, int p) {
+                                                   const T* __restrict__ War, int p, int p0) {
   const QRDesc d = ds[blockIdx.y];
   if (p >= d.n) return;
   const int jb = min(QB, d.n - p);
-  const int nt = d.n - p - jb;
+  const int nt = min(d.n, p0 + QB2) - p - jb;
   const int mp = d.m - p;
   const int tm = (mp + 127) / 128, tn = (nt + 63) / 64;
   if (nt <= 0 || (int)blockIdx.x >= tm * tn) return;
   const int rb = (int)(blockIdx.x % tm) * 128, cb = (int)(blockIdx.x / tm) * 64;
   T* A = Gar + d.A + p + (int64_t)(p + jb) * d.ld;
-  const T* V = Var + d.V;
+  const T* V = Var + d.V + qr_voff(p, p0, d.m);
   const T* W = War + d.W;
   __shared__ __align__(16) T Vs[QB][128];
   __shared__ __align__(16) T Ws[QB][64 + 4];
@@ -602,16 +620,54 @@ __global__ void __launch_bounds__(256) k_qr_update(const QRDesc* __restrict__ ds
   }
 }
 
+
+// T of a 128-column block from the Gram matrix G = V^T V of its reflectors
+// (G[l + j 128]) and their tau (the diagonals of its four panel T's): T[j][j]
+// = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j], column by column; thread
+// i owns row i.  One CTA per front.
+template <typename T>
+__global__ void __launch_bounds__(QB2) k_qr_tblk(const QRDesc* __restrict__ ds,
+                                                 const T* __restrict__ Gb,
+                                                 const T* __restrict__ Tar, T* Tb) {
+  const QRDesc d = ds[blockIdx.x];
+  const T* G = Gb + (int64_t)blockIdx.x * QB2 * QB2;
+  const T* Tp = Tar + d.Tt;
+  T* To = Tb + (int64_t)blockIdx.x * QB2 * QB2;
+  extern __shared__ __align__(16) unsigned char tbs[];
+  T* sT = reinterpret_cast<T*>(tbs);   // sT[i (QB2 + 1) + j]
+  __shared__ T s_g[QB2], s_tau[QB2];
+  const int i = threadIdx.x;
+  s_tau[i] = Tp[(i / QB) * QB * QB + (i % QB) * (QB + 1)];
+  for (int j = 0; j < QB2; ++j) sT[i * (QB2 + 1) + j] = T(0);
+  for (int j = 0; j < QB2; ++j) {
+    __syncthreads();
+    s_g[i] = G[i + (int64_t)j * QB2];
+    __syncthreads();
+    const T tau = s_tau[j];
+    if (i < j) {
+      T t = T(0);
+      for (int l = i; l < j; ++l) t = fma(sT[i * (QB2 + 1) + l], s_g[l], t);
+      sT[i * (QB2 + 1) + j] = -tau * t;
+    } else if (i == j) {
+      sT[i * (QB2 + 1) + j] = tau;
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < QB2; ++j) To[i + (int64_t)j * QB2] = sT[i * (QB2 + 1) + j];
+}
 }  // namespace
 
 constexpr size_t QRC_SMEM_MAX = 160 * 1024;
 
-// Whether a cluster of cs CTAs with rb panel rows each can be placed (the
-// first call per precision also lifts the kernel's cluster-size and shared
-// memory limits).
+// How many clusters of cs CTAs with rb panel rows each the GPU holds at once
+// (0: none; asked once per shape; the first call per precision also lifts
+// the kernel's cluster-size and shared memory limits).
 template <typename T>
-bool panel_cluster_fits_t(int cs, int rb) {
-  static const bool attr = [] {   // initialised once, also under concurrent factorizations
+int panel_clusters_active_t(int cs, int rb) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> known;
+  std::lock_guard<std::mutex> g(mu);
+  static const bool attr = [] {
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel_cluster<T>,
                                       cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     HIF_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel_cluster<T>,
@@ -621,10 +677,13 @@ bool panel_cluster_fits_t(int cs, int rb) {
   }();
   (void)attr;
   const size_t smem = (size_t)rb * QB * sizeof(T);
-  if (smem > QRC_SMEM_MAX) return false;
+  if (smem > QRC_SMEM_MAX) return 0;
+  const auto key = std::make_pair(cs, rb);
+  const auto it = known.find(key);
+  if (it != known.end()) return it->second;
   cudaLaunchConfig_t q = {};
   q.gridDim = dim3((unsigned)cs);
-  q.blockDim = dim3(QRC_THREADS);
+  q.blockDim = dim3(qrc_threads<T>());
   q.dynamicSmemBytes = smem;
   cudaLaunchAttribute qa[1];
   qa[0].id = cudaLaunchAttributeClusterDimension;
@@ -634,21 +693,46 @@ bool panel_cluster_fits_t(int cs, int rb) {
   q.attrs = qa;
   q.numAttrs = 1;
   int ncl = 0;
-  if (cudaOccupancyMaxActiveClusters(&ncl, k_qr_panel_cluster<T>, &q) == cudaSuccess && ncl > 0)
-    return true;
-  cudaGetLastError();
-  return false;
+  if (cudaOccupancyMaxActiveClusters(&ncl, k_qr_panel_cluster<T>, &q) != cudaSuccess) {
+    cudaGetLastError();
+    ncl = 0;
+  }
+  known[key] = std::max(0, ncl);
+  return known[key];
 }
 
-inline bool panel_cluster_fits(int cs, int rb, int tsize) {
-  return tsize == 8 ? panel_cluster_fits_t<double>(cs, rb) : panel_cluster_fits_t<float>(cs, rb);
+inline int panel_clusters_active(int cs, int rb, int tsize) {
+  return tsize == 8 ? panel_clusters_active_t<double>(cs, rb)
+                    : panel_clusters_active_t<float>(cs, rb);
+}
+
+// The cluster size for a panel launch over nact fronts of at most maxmp rows
+// (0: none fits, the panel streams through k_qr_panel): the one that
+// minimises waves x (per-column cost of a CTA), the cost of a column being a
+// fixed part (barriers, exchange) worth QRC_FIXED_ROWS rows plus its rows.
+constexpr int QRC_FIXED_ROWS = 256;
+inline int panel_cluster_size(int nact, int maxmp, int tsize) {
+  int best = 0;
+  double best_cost = 0.0;
+  for (int cs = 1; cs <= QRC_MAX_CS; ++cs) {
+    const int rb = ceil_div(maxmp, cs);
+    const int act = panel_clusters_active(cs, rb, tsize);
+    if (act <= 0) continue;
+    const double cost = (double)ceil_div(nact, act) * (QRC_FIXED_ROWS + rb);
+    if (best == 0 || cost < best_cost) {
+      best = cs;
+      best_cost = cost;
+    }
+  }
+  return best;
 }
 
 // Unpivoted QR of the R rows of fronts `which` (in place in the gather
 // arena); their n x n triangular factors go to Rout at rOff (ld = n).
 template <typename T>
 void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garena, T* Rout,
-                    const std::vector<int64_t>& rOff, cudaStream_t st) {
+                    const std::vector<int64_t>& rOff, int* d_flags, bool tensor_cores,
+                    cudaStream_t st) {
   const int nq = (int)which.size();
   if (nq == 0) return;
   // fronts sorted by n (largest first) so that the fronts still factoring a
@@ -671,9 +755,9 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
     d.W = woff;
     d.Tt = toff;
     d.pad = 0;
-    voff += (int64_t)d.m * QB;
+    voff += (int64_t)d.m * QB2;          // the block's reflectors
     woff += (int64_t)QB * d.n;
-    toff += QB * QB;
+    toff += (QB2 / QB) * QB * QB;         // the block's four panel T's
     ro[i] = rOff[ord[i]];
   }
   T *Var = nullptr, *War = nullptr, *Tar = nullptr;
@@ -693,16 +777,20 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
   // split of the rows of W = V^T A_t: enough CTAs for two waves at two per
   // SM; the partials' workspace holds the largest split of any panel
   constexpr int W1_SPLIT_MAX = 8;
-  auto w1_split = [&](int p) {
+  // the block's columns right of panel p (block start p0)
+  auto nt_in = [&](const QRDesc& d, int p, int p0) {
+    return std::min(d.n, p0 + QB2) - p - std::min(QB, d.n - p);
+  };
+  auto w1_split = [&](int p, int p0) {
     int tiles = 0;
     for (int i = 0; i < nq && qd[i].n > p; ++i) {
-      const int nt = qd[i].n - p - std::min(QB, qd[i].n - p);
+      const int nt = nt_in(qd[i], p, p0);
       if (nt > 0) tiles += ceil_div(nt, W1_NC);
     }
     return tiles == 0 ? 0 : std::max(1, std::min(W1_SPLIT_MAX, ceil_div(4 * nsm, tiles)));
   };
   int smax = 0;
-  for (int p = 0; p < nmax; p += QB) smax = std::max(smax, w1_split(p));
+  for (int p = 0; p < nmax; p += QB) smax = std::max(smax, w1_split(p, p / QB2 * QB2));
   std::vector<int64_t> wpo(nq);
   int64_t wptot = 0;
   for (int i = 0; i < nq; ++i) {
@@ -720,7 +808,24 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
     return true;
   }();
   (void)w1_attr;
+  // the block update's workspace: the Gram matrix of the block's
+  // reflectors, the block's T, and W' = V^T A_t, W = T^T W'
+  int64_t w2tot = 0;
+  std::vector<int64_t> w2o(nq);
+  for (int i = 0; i < nq; ++i) {
+    w2o[i] = w2tot;
+    w2tot += (int64_t)QB2 * qd[i].n;
+  }
+  const bool blocks = nmax > QB2;
+  T *Gb = nullptr, *Tb = nullptr, *W1b = nullptr, *W2b = nullptr;
+  if (blocks) {
+    HIF_CUDA_TRY(cudaMallocAsync(&Gb, sizeof(T) * nq * QB2 * QB2, st));
+    HIF_CUDA_TRY(cudaMallocAsync(&Tb, sizeof(T) * nq * QB2 * QB2, st));
+    HIF_CUDA_TRY(cudaMallocAsync(&W1b, sizeof(T) * w2tot, st));
+    HIF_CUDA_TRY(cudaMallocAsync(&W2b, sizeof(T) * w2tot, st));
+  }
   for (int p = 0; p < nmax; p += QB) {
+    const int p0 = p / QB2 * QB2;
     int nact = 0;
     while (nact < nq && qd[nact].n > p) ++nact;
     {
@@ -736,17 +841,16 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
           pb += 3.0 * sizeof(T) * mp * jb;
         }
       ProfScope ps("id_rowreduce_panel", st, pf, pb);
-      // few fronts: spread each panel over a cluster that keeps it in shared
-      // memory (as many CTAs per front as fill two per SM, up to 16); many
-      // fronts already fill the GPU with one CTA each
-      int cs = std::min(16, 2 * nsm / std::max(1, nact));
-      while (cs > 1 && !panel_cluster_fits(cs, ceil_div(maxmp, cs), (int)sizeof(T))) --cs;
+      // each panel in the shared memory of a cluster (the size that
+      // finishes the batch first); panels too tall for 16 CTAs stream from
+      // L2 (k_qr_panel)
+      const int cs = panel_cluster_size(nact, maxmp, (int)sizeof(T));
       const int rb = ceil_div(maxmp, std::max(1, cs));
       const size_t smem = (size_t)rb * QB * sizeof(T);
-      if (cs > 1 && smem <= QRC_SMEM_MAX) {
+      if (cs > 0) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(nact * cs));
-        cfg.blockDim = dim3(QRC_THREADS);
+        cfg.blockDim = dim3(qrc_threads<T>());
         cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
         cudaLaunchAttribute at[1];
@@ -757,20 +861,20 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
         cfg.attrs = at;
         cfg.numAttrs = 1;
         HIF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_qr_panel_cluster<T>, (const QRDesc*)d_qd, Garena,
-                                        Var, Tar, p, rb));
+                                        Var, Tar, p, p0, rb));
       } else {
-        k_qr_panel<T><<<nact, QR_THREADS, 0, st>>>(d_qd, Garena, Var, Tar, p);
+        k_qr_panel<T><<<nact, QR_THREADS, 0, st>>>(d_qd, Garena, Var, Tar, p, p0);
       }
       HIF_CHECK_LAUNCH();
     }
-    // trailing columns: W = T^T V^T A_t (partials over row splits, then
-    // their sum and T^T), A_t -= V W
-    const int S = w1_split(p);
-    if (S == 0) continue;
+    // the block's columns right of the panel: W = T^T V^T A_t (partials
+    // over row splits, then their sum and T^T), A_t -= V W
+    const int S = w1_split(p, p0);
+    if (S > 0) {
     int ct = 0, ntmax = 0, ut = 0;
     double f1 = 0, b1 = 0, b2 = 0;
     for (int i = 0; i < nact; ++i) {
-      const int jb = std::min(QB, qd[i].n - p), nt = qd[i].n - p - jb, mp = qd[i].m - p;
+      const int jb = std::min(QB, qd[i].n - p), nt = nt_in(qd[i], p, p0), mp = qd[i].m - p;
       if (nt <= 0) continue;
       ct = std::max(ct, ceil_div(nt, W1_NC));
       ntmax = std::max(ntmax, nt);
@@ -782,17 +886,78 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
     {
       ProfScope ps("id_rowreduce_w1", st, f1, b1);
       k_qr_w1<T><<<dim3((unsigned)(ct * S), nact), W1_THREADS, w1_smem_bytes<T>(), st>>>(
-          d_qd, Garena, Var, Wp, d_wpo, p, S);
+          d_qd, Garena, Var, Wp, d_wpo, p, p0, S);
       HIF_CHECK_LAUNCH();
       k_qr_w2<T><<<dim3((unsigned)ceil_div(ntmax, 128), nact), 128, 0, st>>>(d_qd, Wp, d_wpo, Tar,
-                                                                           War, p, S);
+                                                                           War, p, p0, S);
       HIF_CHECK_LAUNCH();
     }
     {
       ProfScope ps("id_rowreduce_update", st, f1, b2);
-      k_qr_update<T><<<dim3((unsigned)ut, nact), 256, 0, st>>>(d_qd, Garena, Var, War, p);
+      k_qr_update<T><<<dim3((unsigned)ut, nact), 256, 0, st>>>(d_qd, Garena, Var, War, p, p0);
       HIF_CHECK_LAUNCH();
     }
+    }
+    // after the block's last panel: the columns right of the block, once
+    // per block, by matrix products (tensor cores in FP32):
+    // G = V^T V -> the block's T;  W' = V^T A_t;  W = T^T W';  A_t -= V W
+    if (p + QB < p0 + QB2 && p + QB < nmax) continue;
+    int nb = 0;
+    while (nb < nq && qd[nb].n > p0 + QB2) ++nb;
+    if (nb == 0) continue;
+    std::vector<GemmOp> og(nb), o1(nb), o2(nb), ou(nb);
+    double fg = 0, fa = 0;
+    for (int i = 0; i < nb; ++i) {
+      const QRDesc& d = qd[i];
+      const int mp0 = d.m - p0, nt = d.n - p0 - QB2;
+      const int64_t at = d.A + p0 + (int64_t)(p0 + QB2) * d.ld;   // A_t(0, 0)
+      og[i] = GemmOp{d.V, d.V, (int64_t)i * QB2 * QB2, QB2, QB2, mp0, d.m, d.m, QB2, 1, 0, 1.f, 0.f, 0, 0};
+      o1[i] = GemmOp{d.V, at, w2o[i], QB2, nt, mp0, d.m, d.ld, QB2, 1, 0, 1.f, 0.f, 0, 0};
+      o2[i] = GemmOp{(int64_t)i * QB2 * QB2, w2o[i], w2o[i], QB2, nt, QB2, QB2, QB2, QB2, 1, 0, 1.f, 0.f, 0, 0};
+      ou[i] = GemmOp{d.V, w2o[i], at, mp0, nt, QB2, d.m, QB2, d.ld, 0, 0, -1.f, 1.f, 0, 0};
+      fg += 2.0 * QB2 * QB2 * mp0;
+      fa += 4.0 * QB2 * (double)nt * mp0;
+    }
+    GemmOp* d_ops = nullptr;
+    HIF_CUDA_TRY(cudaMallocAsync(&d_ops, sizeof(GemmOp) * 4 * nb, st));
+    HIF_CUDA_TRY(cudaMemcpyAsync(d_ops, og.data(), sizeof(GemmOp) * nb, cudaMemcpyHostToDevice, st));
+    HIF_CUDA_TRY(cudaMemcpyAsync(d_ops + nb, o1.data(), sizeof(GemmOp) * nb, cudaMemcpyHostToDevice, st));
+    HIF_CUDA_TRY(cudaMemcpyAsync(d_ops + 2 * nb, o2.data(), sizeof(GemmOp) * nb, cudaMemcpyHostToDevice, st));
+    HIF_CUDA_TRY(cudaMemcpyAsync(d_ops + 3 * nb, ou.data(), sizeof(GemmOp) * nb, cudaMemcpyHostToDevice, st));
+    auto gemm = [&](const GemmOp* dop, const GemmOp* hop, const T* Ab, const T* Bb, T* Cb,
+                    const char* tc_name, const char* name) {
+      if constexpr (std::is_same<T, float>::value) {
+        if (tensor_cores) {
+          gemm_tc(dop, hop, nb, Ab, Bb, Cb, d_flags, st, tc_name);
+          return;
+        }
+      }
+      gemm_batched<T>(dop, hop, nb, Ab, Bb, Cb, st, name);
+    };
+    gemm(d_ops, og.data(), Var, Var, Gb, "id_rowreduce_gram_tc", "id_rowreduce_gram");
+    {
+      static const bool tb_attr = [] {
+        HIF_CUDA_TRY(cudaFuncSetAttribute(k_qr_tblk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(sizeof(T) * QB2 * (QB2 + 1))));
+        return true;
+      }();
+      (void)tb_attr;
+      ProfScope ps("id_rowreduce_blockt", st, (double)nb * QB2 * QB2 * QB2 / 3.0, 0.0);
+      k_qr_tblk<T><<<nb, QB2, sizeof(T) * QB2 * (QB2 + 1), st>>>(d_qd, Gb, Tar, Tb);
+      HIF_CHECK_LAUNCH();
+    }
+    gemm(d_ops + nb, o1.data(), Var, Garena, W1b, "id_rowreduce_vta_tc", "id_rowreduce_vta");
+    gemm(d_ops + 2 * nb, o2.data(), Tb, W1b, W2b, "id_rowreduce_tw_tc", "id_rowreduce_tw");
+    gemm(d_ops + 3 * nb, ou.data(), Var, W2b, Garena, "id_rowreduce_block_tc", "id_rowreduce_block");
+    HIF_CUDA_TRY(cudaFreeAsync(d_ops, st));
+    (void)fg;
+    (void)fa;
+  }
+  if (blocks) {
+    HIF_CUDA_TRY(cudaFreeAsync(W2b, st));
+    HIF_CUDA_TRY(cudaFreeAsync(W1b, st));
+    HIF_CUDA_TRY(cudaFreeAsync(Tb, st));
+    HIF_CUDA_TRY(cudaFreeAsync(Gb, st));
   }
   {
     ProfScope ps("id_rowreduce_extract", st);
@@ -810,8 +975,8 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
 }
 
 template void reduce_rows_qr<float>(const SkelDesc*, const std::vector<int>&, float*, float*,
-                                    const std::vector<int64_t>&, cudaStream_t);
+                                    const std::vector<int64_t>&, int*, bool, cudaStream_t);
 template void reduce_rows_qr<double>(const SkelDesc*, const std::vector<int>&, double*, double*,
-                                     const std::vector<int64_t>&, cudaStream_t);
+                                     const std::vector<int64_t>&, int*, bool, cudaStream_t);
 
 }  // namespace hif

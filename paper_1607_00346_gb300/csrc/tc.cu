@@ -147,14 +147,29 @@ __global__ void __launch_bounds__(TC_M + TN, KC == 16 ? (TN == 128 ? 3 : 2) : 1)
   const int64_t ldx = isA ? o.lda : o.ldb;
   const bool kfast = isA ? (o.transA != 0) : (o.transB == 0);   // k contiguous in memory
   const bool rin = base + row < lim;
+  // K contiguous in memory: value q of a thread is (kr(q), kk(q)) so that
+  // one warp instruction reads 8 rows x 4 consecutive k (16 bytes per row)
+  // and stores 32 consecutive words of the core-matrix layout; otherwise a
+  // thread owns one row (consecutive threads read consecutive rows)
+  const int gw = isA ? warp : warp - TC_M / 32;   // warp within the operand's group
+  constexpr int GA = TC_M / 32, GB = TN / 32;
+  const int G = isA ? GA : GB;
+  auto kr = [&](int q) { return (q / (KC / 4)) * (G * 8) + gw * 8 + lane / 4; };
+  auto kq = [&](int q) { return (q % (KC / 4)) * 4 + lane % 4; };
   auto load = [&](int ch, float (&v)[KC]) {
     const int k0 = (cbeg + ch) * KC;
+    if (kfast) {
 #pragma unroll
-    for (int k = 0; k < KC; ++k) {
-      const int kk = k0 + k;
-      v[k] = (rin && kk < o.k) ? (kfast ? X[(int64_t)kk + (int64_t)(base + row) * ldx]
-                                        : X[(int64_t)(base + row) + (int64_t)kk * ldx])
-                               : 0.f;
+      for (int q = 0; q < KC; ++q) {
+        const int r = kr(q), kk = k0 + kq(q);
+        v[q] = (base + r < lim && kk < o.k) ? X[(int64_t)kk + (int64_t)(base + r) * ldx] : 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        const int kk = k0 + k;
+        v[k] = (rin && kk < o.k) ? X[(int64_t)(base + row) + (int64_t)kk * ldx] : 0.f;
+      }
     }
   };
   auto step = [&](int ch, float (&v)[KC]) -> bool {
@@ -163,7 +178,17 @@ __global__ void __launch_bounds__(TC_M + TN, KC == 16 ? (TN == 128 ? 3 : 2) : 1)
     if (ch >= 2 && !wait_buf(s)) s_fail = 1;   // buffer s is free again
     __syncthreads();
     if (s_fail) return false;
-    {
+    if (kfast) {
+      unsigned char* hi = buf + (isA ? 0 : 2 * TILE_A);
+      unsigned char* lo = hi + (isA ? TILE_A : TILE_B);
+#pragma unroll
+      for (int q = 0; q < KC; ++q) {
+        const float h = tf32_hi(v[q]);
+        const int off = core_off<KC>(kr(q), kq(q));
+        *reinterpret_cast<float*>(hi + off) = h;
+        *reinterpret_cast<float*>(lo + off) = tf32_hi(v[q] - h);
+      }
+    } else {
       unsigned char* hi = buf + (isA ? 0 : 2 * TILE_A);
       unsigned char* lo = hi + (isA ? TILE_A : TILE_B);
 #pragma unroll
