@@ -177,38 +177,58 @@ __global__ void __launch_bounds__(256) k_merge(const MergeDesc* __restrict__ par
   }
 }
 
+// One CTA per 32 x 32 tile of a front's gather block.  The cells' frontal
+// matrices hold only their lower triangles, so an entry (x, y) with x < y is
+// read as (y, x): the tile is accumulated in shared memory in two passes per
+// cell, lanes over the tile's rows for the entries read down a column
+// (x >= y) and lanes over its columns for the transposed ones (x < y), so
+// both read consecutive addresses; the cells are added in order.
+constexpr int GT = 32;   // gather tile
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_skel_gather(const SkelDesc* __restrict__ fr, int ncp,
                                                      const int32_t* __restrict__ rowPos,
                                                      const CellDesc* __restrict__ cells,
                                                      const T* __restrict__ Kar, T* Gar) {
   const SkelDesc f = fr[blockIdx.y];
-  const int rows = f.nF + f.nR;
-  const int64_t tot = (int64_t)rows * f.nF;
-  const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  if ((int64_t)blockIdx.x * 256 >= tot) return;
+  const int rows = f.nF + f.nR, cols = f.nF;
+  const int tr = (rows + GT - 1) / GT, tc = (cols + GT - 1) / GT;
+  if ((int)blockIdx.x >= tr * tc) return;
+  const int r0 = (int)(blockIdx.x % tr) * GT, c0 = (int)(blockIdx.x / tr) * GT;
+  __shared__ T tile[GT][GT + 1];   // tile[c][r]
+  __shared__ int xr[4][GT], yc[4][GT];
   __shared__ int64_t cK[4];
   __shared__ int cn[4], cp[4];
+  const int tx = threadIdx.x % GT, ty = threadIdx.x / GT;   // ty < 8
+  const int32_t* rp = rowPos + f.rows;
   if (threadIdx.x < ncp) {
     const CellDesc cd = cells[f.cell[threadIdx.x]];
     cK[threadIdx.x] = cd.K;
     cn[threadIdx.x] = cd.n;
     cp[threadIdx.x] = cd.p;
   }
-  __syncthreads();
-  if (e >= tot) return;
-  const int r = (int)(e % rows), c = (int)(e / rows);
-  const int32_t* rp = rowPos + f.rows;
-  T sum = T(0);
-  for (int i = 0; i < ncp; ++i) {
-    const int x = rp[(int64_t)r * ncp + i], y = rp[(int64_t)c * ncp + i];
-    if (x >= 0 && y >= 0) {
-      const int hi_ = max(x, y), lo_ = min(x, y);
-      const int64_t nc = cn[i], p = cp[i];
-      sum += Kar[cK[i] + (p + hi_) + (p + lo_) * nc];
-    }
+  if (ty < ncp) {
+    xr[ty][tx] = r0 + tx < rows ? rp[(int64_t)(r0 + tx) * ncp + ty] : -1;
+    yc[ty][tx] = c0 + tx < cols ? rp[(int64_t)(c0 + tx) * ncp + ty] : -1;
   }
-  Gar[f.G + e] = sum;
+  for (int q = ty; q < GT; q += 8) tile[q][tx] = T(0);
+  __syncthreads();
+  for (int i = 0; i < ncp; ++i) {
+    const T* K = Kar + cK[i];
+    const int64_t nc = cn[i], p = cp[i];
+    for (int q = ty; q < GT; q += 8) {   // lanes over rows: (x, y) with x >= y
+      const int x = xr[i][tx], y = yc[i][q];
+      if (x >= 0 && y >= 0 && x >= y) tile[q][tx] += K[(p + x) + (p + y) * nc];
+    }
+    __syncthreads();
+    for (int q = ty; q < GT; q += 8) {   // lanes over columns: (x, y) with x < y, read as (y, x)
+      const int x = xr[i][q], y = yc[i][tx];
+      if (x >= 0 && y >= 0 && x < y) tile[tx][q] += K[(p + y) + (p + x) * nc];
+    }
+    __syncthreads();
+  }
+  for (int q = ty; q < GT; q += 8)
+    if (r0 + tx < rows && c0 + q < cols) Gar[f.G + (r0 + tx) + (int64_t)(c0 + q) * rows] = tile[q][tx];
 }
 
 template <typename T>
@@ -302,15 +322,16 @@ void skel_gather(const SkelDesc* d_f, const SkelDesc* h_f, int nf, int ncp,
                  const int32_t* rowPos, const CellDesc* d_cells, const T* Karena, T* Garena,
                  cudaStream_t st) {
   int64_t mx = 1;
-  for (int i = 0; i < nf; ++i) mx = std::max<int64_t>(mx, (int64_t)(h_f[i].nF + h_f[i].nR) * h_f[i].nF);
+  for (int i = 0; i < nf; ++i)
+    mx = std::max<int64_t>(mx, (int64_t)ceil_div(h_f[i].nF + h_f[i].nR, GT) * ceil_div(h_f[i].nF, GT));
   for (int f0 = 0; f0 < nf; f0 += MAX_GRID_Y) {
     const int nb = std::min(MAX_GRID_Y, nf - f0);
     double by = 0;
     if (prof_enabled())
       for (int i = f0; i < f0 + nb; ++i) by += sizeof(T) * (double)(h_f[i].nF + h_f[i].nR) * h_f[i].nF;
     ProfScope ps("skel_gather", st, 0.0, by);
-    k_skel_gather<T><<<dim3(ceil_div(mx, 256), nb), 256, 0, st>>>(d_f + f0, ncp, rowPos, d_cells,
-                                                                  Karena, Garena);
+    k_skel_gather<T><<<dim3((unsigned)mx, nb), 256, 0, st>>>(d_f + f0, ncp, rowPos, d_cells,
+                                                             Karena, Garena);
     HIF_CHECK_LAUNCH();
   }
 }
