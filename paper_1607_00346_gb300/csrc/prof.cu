@@ -1,6 +1,7 @@
 // Kernel profiler: CUDA events around every launch of the library while
 // profiling is on, aggregated per kernel name with the launch's algorithmic
 // flops and bytes (counted on the host from the descriptors).
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -99,10 +100,12 @@ ProfScope::ProfScope(const char* name, cudaStream_t st, double flops, double byt
   k0_ = launch_counter();
   HIF_CUDA_TRY(cudaEventRecord(a_, st_));
   active_ = true;
+  nvtxRangePushA(name);   // lets a profiler select the launches of one label
 }
 
 ProfScope::~ProfScope() {
   if (!active_) return;
+  nvtxRangePop();
   ProfState& s = state();
   std::lock_guard<std::mutex> lk(s.mu);
   cudaEventRecord(b_, st_);

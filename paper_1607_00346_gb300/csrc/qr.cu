@@ -165,8 +165,8 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_panel(const QRDesc* __restric
 // run in the factor precision (FP64 arithmetic is slow here).
 constexpr int QRC_MAX_CS = 16;
 constexpr int QRC_MAX_WARPS = 16;
-// threads per CTA: 512 in FP32; 256 in FP64 (each thread keeps 64 sums and
-// reflector weights in registers)
+// threads per CTA: 512 in FP32; 256 in FP64 (each thread keeps 32 partial
+// sums and half a row of the panel in registers)
 template <typename T>
 __host__ __device__ constexpr int qrc_threads() {
   return sizeof(T) == 4 ? 512 : 256;
@@ -198,12 +198,23 @@ __global__ void __launch_bounds__(qrc_threads<T>()) k_qr_panel_cluster(const QRD
   __shared__ T s_sum[QB];
   __shared__ T s_tw[QB];                             // tau w_jj of the current column
   __shared__ T s_v0[QB];
-  __shared__ T s_T[QB][QB + 1];
+  __shared__ T s_tau[QB];
+  __shared__ T s_T[QB][QB + 1];                      // V^T V above the diagonal, then T
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int nr = max(0, r1 - r0);
-  for (int e = tid; e < nr * jb; e += QRC_THREADS) {
-    const int i = e % nr, j = e / nr;
-    P[i + j * rb] = A[(p + r0 + i) + (int64_t)(p + j) * ld];
+  // the slice, eight loads in flight per thread
+  for (int e0 = 0; e0 < nr * jb; e0 += 8 * QRC_THREADS) {
+    T x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + tid + u * QRC_THREADS;
+      x[u] = e < nr * jb ? A[(p + r0 + e % nr) + (int64_t)(p + e / nr) * ld] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + tid + u * QRC_THREADS;
+      if (e < nr * jb) P[e % nr + (e / nr) * rb] = x[u];
+    }
   }
   for (int e = tid; e < QB * (QB + 1); e += QRC_THREADS) (&s_T[0][0])[e] = T(0);
   cl.sync();   // every CTA runs (and holds its slice) before the first push
@@ -267,14 +278,12 @@ __global__ void __launch_bounds__(qrc_threads<T>()) k_qr_panel_cluster(const QRD
     if (tid < QB) {
       s_tw[tid] = (tid > j && tid < jb) ? tau * fma(v0, s_row[par][tid], s_sum[tid]) : T(0);
     } else if (tid < 2 * QB) {
-      // column j of T: row l < j is -tau sum_{i=l}^{j-1} T[l][i] v_i^T v_j
+      // v_l^T v_j = v_l[j] v0 + (v_l^T a_j below row j), kept for T
       const int l = tid - QB;
       if (l < j) {
-        T t = T(0);
-        for (int i2 = l; i2 < j; ++i2) t = fma(s_T[l][i2], fma(s_row[par][i2], v0, s_sum[i2]), t);
-        s_T[l][j] = -tau * t;
+        s_T[l][j] = fma(s_row[par][l], v0, s_sum[l]);
       } else if (l == j) {
-        s_T[j][j] = tau;
+        s_tau[j] = tau;
         s_v0[j] = v0;
       }
     }
@@ -285,30 +294,36 @@ __global__ void __launch_bounds__(qrc_threads<T>()) k_qr_panel_cluster(const QRD
     }
     // a_jj -= (tau w_jj) v on the slice's rows from j on, and the parts of
     // column j + 1 from the updated entries (rows below j + 1)
-    T tw[QB];
-#pragma unroll
-    for (int jj = 0; jj < QB; ++jj) tw[jj] = s_tw[jj];
-    const T twn = s_tw[j + 1];
 #pragma unroll
     for (int jj = 0; jj < QB; ++jj) acc[jj] = T(0);
     T tl = T(0);
     for (int i = tid; i < nr; i += QRC_THREADS) {
       const int row = r0 + i;
       if (row < j) continue;
+      // column j + 1 first (its updated entry weights the products), then
+      // the other columns in two halves: each half's loads in flight
+      // together, then its update (columns > j) and products
       const T vi = row == j ? v0 : P[i + j * rb];
-      const T xj1 = fma(-twn, vi, P[i + (j + 1) * rb]);
+      const T xj1 = fma(-s_tw[j + 1], vi, P[i + (j + 1) * rb]);
       P[i + (j + 1) * rb] = xj1;
       const T xn = row > j + 1 ? xj1 : T(0);
       tl = fma(xn, xn, tl);
 #pragma unroll
-      for (int jj = 0; jj < QB; ++jj) {
-        if (jj < jb && jj != j + 1) {
-          T x = P[i + jj * rb];
-          if (jj > j + 1) {
-            x = fma(-tw[jj], vi, x);
-            P[i + jj * rb] = x;
+      for (int h = 0; h < QB; h += QB / 2) {
+        T x[QB / 2];
+#pragma unroll
+        for (int u = 0; u < QB / 2; ++u) {
+          const int jj = h + u;
+          x[u] = (jj < jb && jj != j + 1) ? P[i + jj * rb] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < QB / 2; ++u) {
+          const int jj = h + u;
+          if (jj > j + 1 && jj < jb) {
+            x[u] = fma(-s_tw[jj], vi, x[u]);
+            P[i + jj * rb] = x[u];
           }
-          acc[jj] = fma(xn, x, acc[jj]);
+          if (jj < jb && jj != j + 1) acc[jj] = fma(xn, x[u], acc[jj]);
         }
       }
     }
@@ -334,6 +349,17 @@ __global__ void __launch_bounds__(qrc_threads<T>()) k_qr_panel_cluster(const QRD
     // the block's rows above the panel: zero in the panel's reflectors
     const int vtop = p - p0;
     for (int e = tid; e < vtop * QB; e += QRC_THREADS) V[(e % vtop - vtop) + (int64_t)(e / vtop) * m] = T(0);
+    // T column by column from the products kept above its diagonal:
+    // T[l][j] = -tau_j sum_{i=l}^{j-1} T[l][i] (v_i^T v_j), T[j][j] = tau_j
+    for (int j = 0; j < jb; ++j) {
+      T t = T(0);
+      if (tid < j)
+        for (int i2 = tid; i2 < j; ++i2) t = fma(s_T[tid][i2], s_T[i2][j], t);
+      __syncthreads();
+      if (tid < j) s_T[tid][j] = -s_tau[j] * t;
+      else if (tid == j) s_T[j][j] = s_tau[j];
+      __syncthreads();
+    }
     T* Tt = Tar + d.Tt + qr_toff(p, p0);
     for (int e = tid; e < QB * QB; e += QRC_THREADS) {
       const int i = e % QB, j = e / QB;
