@@ -87,11 +87,12 @@ KERNEL_BOUND = {
 }
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
-# kernel label in the bench workload, from the ncu capture summarised in
+# kernel label in the bench workload, from the ncu captures summarised in
 # profiles/ (absent where no capture of the current kernel exists):
-# id_cpqr: the six k_cpqr launches of one 128^3 factorization move 206.7 GB
-# (profiles/id_cpqr_traffic_contrast128.md).
-TRAFFIC_PER_LAUNCH = {"id_cpqr": 206.7e9 / 6}
+# gemm_tc: the 12 Schur-product launches of one 128^3 factorization move
+# 53.8 GB (profiles/gemm_tc_traffic_contrast128.md); id_cpqr: its 4 k_cpqr
+# launches move 78.7 GB (profiles/id_cpqr_traffic_contrast128.md).
+TRAFFIC_PER_LAUNCH = {"gemm_tc": 53.76e9 / 12, "id_cpqr": 78.73e9 / 4}
 
 
 def _hbm_peak():
