@@ -991,8 +991,8 @@ inline int dsm_rows_per_lane(int m, int tsize) {
 }
 
 // the smallest cluster whose CTAs' shared memory holds the front (0: none)
-inline int dsm_min_cluster(int m, int nF, int tsize) {
-  for (int cs = 2; cs <= DSM_MAX_CS; ++cs)
+inline int dsm_min_cluster(int m, int nF, int tsize, int cs_from = 2) {
+  for (int cs = cs_from; cs <= DSM_MAX_CS; ++cs)
     if (dsm_id_bytes(m, nF, cs, tsize) <= (size_t)DSM_SMEM_MAX) return cs;
   return 0;
 }
@@ -1045,8 +1045,9 @@ template <typename T, int RPL>
 bool launch_cpqr_dsm(const std::vector<int>& fronts, const SkelDesc* h_f, SkelDesc* d_f, T* G,
                      int32_t* perm, double eps, int cs_min, cudaStream_t st) {
   if (fronts.empty()) return true;
-  int CS = std::max(2, cs_min);
-  for (int f : fronts) CS = std::max(CS, dsm_min_cluster(h_f[f].idm, h_f[f].nF, (int)sizeof(T)));
+  int CS = std::max(1, cs_min);
+  for (int f : fronts)
+    CS = std::max(CS, dsm_min_cluster(h_f[f].idm, h_f[f].nF, (int)sizeof(T), std::max(1, cs_min)));
   for (; CS <= DSM_MAX_CS; ++CS) {
     size_t smem = 0;
     for (int f : fronts)
@@ -1106,11 +1107,19 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
   constexpr int class_threads[3] = {128, 256, 1024};
   std::vector<int> small[3], rest;
   size_t small_bytes[3] = {0, 0, 0};
+  // fronts of the widest one-CTA class go to k_cpqr_dsm on one CTA when
+  // they fit it (its column passes hold the column in registers as 16-byte
+  // vectors)
+  std::vector<int> one[3];
   for (int f = 0; f < nf; ++f) {
     const size_t by = smem_id_bytes(h_f[f].idm, h_f[f].nF, (int)sizeof(T));
     int cl = 0;
     while (cl < 3 && by > class_max[cl]) ++cl;
-    if (cl == 3) {
+    const int rpl = dsm_rows_per_lane(h_f[f].idm, (int)sizeof(T));
+    if (cl == 2 && rpl > 0 &&
+        dsm_id_bytes(h_f[f].idm, h_f[f].nF, 1, (int)sizeof(T)) <= (size_t)DSM_SMEM_MAX) {
+      one[rpl == 8 ? 0 : rpl == 16 ? 1 : 2].push_back(f);
+    } else if (cl == 3) {
       rest.push_back(f);
     } else {
       small[cl].push_back(f);
@@ -1131,6 +1140,20 @@ void interpolative_decomposition(SkelDesc* d_f, const SkelDesc* h_f, int nf, T* 
       HIF_CHECK_LAUNCH();
     }
     HIF_CUDA_TRY(cudaFreeAsync(d_list, st));
+  }
+  {
+    bool placed[3] = {launch_cpqr_dsm<T, 8>(one[0], h_f, d_f, Garena, perm, eps, 1, st),
+                      launch_cpqr_dsm<T, 16>(one[1], h_f, d_f, Garena, perm, eps, 1, st), true};
+    if constexpr (sizeof(T) == 4)
+      placed[2] = launch_cpqr_dsm<T, 32>(one[2], h_f, d_f, Garena, perm, eps, 1, st);
+    for (int c = 0; c < 3; ++c)
+      for (int f : one[c]) {
+        if (placed[c]) {
+          if (route) route[f] = ID_ROUTE_CLUSTER_SMEM;
+        } else {
+          rest.push_back(f);   // not expected: a one-CTA cluster always fits
+        }
+      }
   }
   // fronts that fit the shared memory of one cluster: k_cpqr_dsm, one launch
   // per rows-per-lane class; the rest (and any class whose cluster cannot be
