@@ -284,7 +284,8 @@ hif_status hif_profile_end(hif_kernel_profile* out, int cap, int* count);
  * the large IDs (CTAs per front, 1-16, and how many fronts share a launch:
  * all at once, or as many as fit the L2 cache) and the tensor-core products
  * (K chunk and tile width).  Fronts and products are put into size buckets
- * (ID: front width x number of fronts; products: shape x waves of tiles).
+ * (ID: front width x number of fronts; products: rows, width and depth of
+ * the batch x waves of tiles).
  *
  * hif_autotune -- factor the given operator once while measuring: every
  * cluster ID without a table entry times its candidate shapes in place on

@@ -412,11 +412,12 @@ int split_k(const GemmOp* h_ops, int nops, int v) {
 void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Abase,
              const float* Bbase, float* Cbase, int* d_flags, cudaStream_t st, const char* name) {
   if (nops == 0) return;
-  int mmax = 0, nmax = 0;
+  int mmax = 0, nmax = 0, kmax = 0;
   double fl = 0;
   for (int i = 0; i < nops; ++i) {
     mmax = std::max(mmax, h_ops[i].m);
     nmax = std::max(nmax, h_ops[i].n);
+    kmax = std::max(kmax, h_ops[i].k);
     fl += 2.0 * h_ops[i].m * (double)h_ops[i].n * h_ops[i].k * (h_ops[i].lower ? 0.5 : 1.0);
   }
   // built-in rule: few rows (one tile, mostly padding): fewer, longer
@@ -426,7 +427,7 @@ void gemm_tc(const GemmOp* d_ops, const GemmOp* h_ops, int nops, const float* Ab
   const int S = split_k(h_ops, nops, vdef);
   int tiles = 0, mt = 1;
   tile_counts(h_ops, nops, 128, &tiles, &mt);
-  const int scls = gemm_shape_class(mmax, nmax), wcls = gemm_waves_class(tiles, sm_count());
+  const int scls = gemm_shape_class(mmax, nmax, kmax), wcls = gemm_waves_class(tiles, sm_count());
   if (tune_session_active()) tune_record_gemm(scls, wcls, h_ops, nops, fl);
   // a tuned tile shape (every variant accumulates each entry in the same
   // order; with K split, only variants with the same K chunk keep the split)

@@ -29,7 +29,11 @@ thread_local int t_session = 0;
 
 }  // namespace
 
-int gemm_shape_class(int mmax, int nmax) { return mmax <= 64 ? 0 : (nmax < 256 ? 1 : 2); }
+int gemm_shape_class(int mmax, int nmax, int kmax) {
+  // rows and width of the widest product; + 3 for shallow batches (K <= 256),
+  // whose tiles are dominated by the C read and write rather than the K loop
+  return (mmax <= 64 ? 0 : (nmax < 256 ? 1 : 2)) + (kmax <= 256 ? 3 : 0);
+}
 
 int gemm_waves_class(int tiles, int nsm) {
   const double w = (double)tiles / (2.0 * nsm);
@@ -145,7 +149,7 @@ bool tune_parse(const std::string& text, std::string* why) {
     } else if (kind == "gemm") {
       int s = -1, w = -1, v = -1;
       ls >> s >> w >> v;
-      if (!ls || s < 0 || s > 2 || w < 0 || w > 2 || v < 0 || v > 2) {
+      if (!ls || s < 0 || s > 5 || w < 0 || w > 2 || v < 0 || v > 2) {
         if (why) *why = "bad line: " + line;
         return false;
       }

@@ -18,7 +18,7 @@ namespace hif {
 // 2 = 32 / 128 x 128.  Every variant accumulates each output entry with the
 // same sequence of K = 8 tensor-core steps, so they agree bitwise (when K
 // is split across CTAs only variants with the default chunk are allowed).
-int gemm_shape_class(int mmax, int nmax);
+int gemm_shape_class(int mmax, int nmax, int kmax);
 int gemm_waves_class(int tiles, int nsm);
 
 // Cluster ID (k_cpqr): bucket = (width class of the call's widest cluster

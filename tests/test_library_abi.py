@@ -121,9 +121,10 @@ def test_autotune_table_files(tmp_path):
     assert hif.autotune_table() == text
     good = tmp_path / "good.txt"
     tag = text.split("device ")[1].split()[0]
-    good.write_text(f"device {tag}\ngemm 2 1 0\nid 1 2 16 12\n")
+    # shape classes 0-2 (rows/width), 3-5 the same for shallow batches (K <= 256)
+    good.write_text(f"device {tag}\ngemm 2 1 0\ngemm 5 2 1\nid 1 2 16 12\n")
     hif.autotune_load(str(good))
     t2 = hif.autotune_table()
-    assert "gemm 2 1 0" in t2 and "id 1 2 16 12" in t2
+    assert "gemm 2 1 0" in t2 and "gemm 5 2 1" in t2 and "id 1 2 16 12" in t2
     hif.autotune_clear()
     assert "gemm" not in hif.autotune_table().replace("# ", "")
