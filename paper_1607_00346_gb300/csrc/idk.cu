@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(1024) k_cpqr_smem(SkelDesc* fr, const int* __r
 }
 
 // ---- fronts whose ID matrix fits in the shared memory of one cluster ---------------
-// One cluster of CS CTAs (2 to 16) per front.  Column c sits in the shared
+// One cluster of CS CTAs (1 to 16) per front.  Column c sits in the shared
 // memory of CTA c % CS (local column c / CS) for the whole factorization, so
 // the pivot steps read and write the matrix on chip instead of streaming it
 // from L2 or HBM once per step.  Unblocked Householder QR with column
@@ -537,8 +537,10 @@ __global__ void __launch_bounds__(1024) k_cpqr_smem(SkelDesc* fr, const int* __r
 //   4. the warps' best columns meet in this CTA's proposal for the next step.
 // The proposals are double-buffered by step parity, so one cluster barrier
 // per step orders every exchange.  RPL rows per lane bound m (m <= 32 RPL).
-// At the end each CTA writes rows 0..k-1 of its columns (R, with R_jj in row j
-// of pivot column j) back to the matrix for k_id_solve_t.
+// At the end each CTA writes rows 0..k-1 of its columns (R, with R_jj in row
+// i of the column pivoted at step i) back to the matrix for k_id_solve_t.
+// Fronts of 64-220 KB, which fit one CTA, run here with CS = 1 (the column
+// passes from registers beat k_cpqr_smem's on them).
 constexpr int DSM_THREADS = 512;
 constexpr int DSM_WARPS = DSM_THREADS / 32;
 constexpr int DSM_SMEM_MAX = 224 * 1024;   // dynamic shared memory per CTA, bytes

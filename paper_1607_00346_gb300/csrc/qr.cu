@@ -17,12 +17,16 @@
 //     memory of a cluster (row slices, one exchange per column), k_qr_panel
 //     (one CTA per front, the panel in global memory, norms in double) takes
 //     panels too tall for 16 CTAs;
-//   * trailing columns: W = T^T V^T A and A -= V W, two kernels that stream
-//     the trailing columns from HBM once each (k_qr_w1/k_qr_w2, k_qr_update).
+//   * the columns right of the panel inside its 128-column block: W = T^T
+//     V^T A and A -= V W, two kernels that stream those columns once each
+//     (k_qr_w1/k_qr_w2, k_qr_update);
+//   * after a block's last panel, the columns right of the block, once per
+//     block, by tensor-core products: G = V^T V, the block's T from G and
+//     the panels' tau (k_qr_tblk), W' = V^T A_t, W = T^T W', A_t -= V W.
 #include <algorithm>
+#include <cstdlib>
 #include <map>
 #include <mutex>
-#include <cstdlib>
 #include <type_traits>
 #include <vector>
 
@@ -158,11 +162,13 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr_panel(const QRDesc* __restric
 // same order and forms the same reflector, the same w_jj = v^T a_jj =
 // v0 a_jj[j] + (a_j^T a_jj below j) and the same column j of T
 // (T[0:j, j] = -tau_j T[0:j, 0:j] V^T v_j, with v_l^T v_j = v_l[j] v0 +
-// (v_l^T a_j below j)).  The pass that then updates the slice
-// (a_jj -= tau w_jj v) also takes the parts for column j + 1 from the updated
-// entries.  Per column: one cluster barrier, two CTA barriers, one read and
-// write of the slice; the parts are double-buffered by column parity.  Sums
-// run in the factor precision (FP64 arithmetic is slow here).
+// (v_l^T a_j below j); the products are kept and T is formed once after the
+// column loop).  The pass that then updates the slice (a_jj -= tau w_jj v)
+// also takes the parts for column j + 1 from the updated entries; each row is
+// read in two halves whose loads are in flight together.  Per column: one
+// cluster barrier, two CTA barriers, one read and write of the slice; the
+// parts are double-buffered by column parity.  Sums run in the factor
+// precision (FP64 arithmetic is slow here).
 constexpr int QRC_MAX_CS = 16;
 constexpr int QRC_MAX_WARPS = 16;
 // threads per CTA: 512 in FP32; 256 in FP64 (each thread keeps 32 partial
