@@ -158,20 +158,32 @@ __global__ void __launch_bounds__(256) k_merge(const MergeDesc* __restrict__ par
     }
   }
   __syncthreads();
+  // the children that hold row i / column j of the tile (bit q): an entry
+  // visits only the children that hold both, in increasing q as before
+  __shared__ unsigned s_rm[64], s_cm[64];
+  if (threadIdx.x < 64) {
+    unsigned r = 0u, c = 0u;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      r |= (rmap[q][threadIdx.x] >= 0 ? 1u : 0u) << q;
+      c |= (cmap[q][threadIdx.x] >= 0 ? 1u : 0u) << q;
+    }
+    s_rm[threadIdx.x] = r;
+    s_cm[threadIdx.x] = c;
+  }
+  __syncthreads();
   T* K = Kp + pd.K;
   for (int e = threadIdx.x; e < 64 * 64; e += 256) {
     const int i = e % 64, j = e / 64;
     const int a = ti * 64 + i, b = tj * 64 + j;
     if (a >= n || b >= n || a < b) continue;
     T sum = T(0);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (unsigned msk = s_rm[i] & s_cm[j]; msk != 0u; msk &= msk - 1u) {
+      const int q = __ffs(msk) - 1;
       const int x = rmap[q][i], y = cmap[q][j];
-      if (x >= 0 && y >= 0) {
-        const int hi_ = max(x, y), lo_ = min(x, y);
-        const int64_t ncq = cn[q], pq = cp[q];
-        sum += Kc[cK[q] + (pq + hi_) + (pq + lo_) * ncq];
-      }
+      const int hi_ = max(x, y), lo_ = min(x, y);
+      const int64_t ncq = cn[q], pq = cp[q];
+      sum += Kc[cK[q] + (pq + hi_) + (pq + lo_) * ncq];
     }
     K[(int64_t)a + (int64_t)b * n] = sum;
   }
