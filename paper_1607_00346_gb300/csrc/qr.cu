@@ -903,32 +903,32 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
     // over row splits, then their sum and T^T), A_t -= V W
     const int S = w1_split(p, p0);
     if (S > 0) {
-    int ct = 0, ntmax = 0, ut = 0;
-    double f1 = 0, b1 = 0, b2 = 0;
-    for (int i = 0; i < nact; ++i) {
-      const int jb = std::min(QB, qd[i].n - p), nt = nt_in(qd[i], p, p0), mp = qd[i].m - p;
-      if (nt <= 0) continue;
-      ct = std::max(ct, ceil_div(nt, W1_NC));
-      ntmax = std::max(ntmax, nt);
-      ut = std::max(ut, ceil_div(mp, 128) * ceil_div(nt, 64));
-      f1 += 2.0 * jb * (double)nt * mp;
-      b1 += sizeof(T) * ((double)mp * nt + (double)mp * jb);
-      b2 += 2.0 * sizeof(T) * (double)mp * nt;
-    }
-    {
-      ProfScope ps("id_rowreduce_w1", st, f1, b1);
-      k_qr_w1<T><<<dim3((unsigned)(ct * S), nact), W1_THREADS, w1_smem_bytes<T>(), st>>>(
-          d_qd, Garena, Var, Wp, d_wpo, p, p0, S);
-      HIF_CHECK_LAUNCH();
-      k_qr_w2<T><<<dim3((unsigned)ceil_div(ntmax, 128), nact), 128, 0, st>>>(d_qd, Wp, d_wpo, Tar,
-                                                                           War, p, p0, S);
-      HIF_CHECK_LAUNCH();
-    }
-    {
-      ProfScope ps("id_rowreduce_update", st, f1, b2);
-      k_qr_update<T><<<dim3((unsigned)ut, nact), 256, 0, st>>>(d_qd, Garena, Var, War, p, p0);
-      HIF_CHECK_LAUNCH();
-    }
+      int ct = 0, ntmax = 0, ut = 0;
+      double f1 = 0, b1 = 0, b2 = 0;
+      for (int i = 0; i < nact; ++i) {
+        const int jb = std::min(QB, qd[i].n - p), nt = nt_in(qd[i], p, p0), mp = qd[i].m - p;
+        if (nt <= 0) continue;
+        ct = std::max(ct, ceil_div(nt, W1_NC));
+        ntmax = std::max(ntmax, nt);
+        ut = std::max(ut, ceil_div(mp, 128) * ceil_div(nt, 64));
+        f1 += 2.0 * jb * (double)nt * mp;
+        b1 += sizeof(T) * ((double)mp * nt + (double)mp * jb);
+        b2 += 2.0 * sizeof(T) * (double)mp * nt;
+      }
+      {
+        ProfScope ps("id_rowreduce_w1", st, f1, b1);
+        k_qr_w1<T><<<dim3((unsigned)(ct * S), nact), W1_THREADS, w1_smem_bytes<T>(), st>>>(
+            d_qd, Garena, Var, Wp, d_wpo, p, p0, S);
+        HIF_CHECK_LAUNCH();
+        k_qr_w2<T><<<dim3((unsigned)ceil_div(ntmax, 128), nact), 128, 0, st>>>(d_qd, Wp, d_wpo, Tar,
+                                                                             War, p, p0, S);
+        HIF_CHECK_LAUNCH();
+      }
+      {
+        ProfScope ps("id_rowreduce_update", st, f1, b2);
+        k_qr_update<T><<<dim3((unsigned)ut, nact), 256, 0, st>>>(d_qd, Garena, Var, War, p, p0);
+        HIF_CHECK_LAUNCH();
+      }
     }
     // after the block's last panel: the columns right of the block, once
     // per block, by matrix products (tensor cores in FP32):
@@ -938,7 +938,6 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
     while (nb < nq && qd[nb].n > p0 + QB2) ++nb;
     if (nb == 0) continue;
     std::vector<GemmOp> og(nb), o1(nb), o2(nb), ou(nb);
-    double fg = 0, fa = 0;
     for (int i = 0; i < nb; ++i) {
       const QRDesc& d = qd[i];
       const int mp0 = d.m - p0, nt = d.n - p0 - QB2;
@@ -947,8 +946,6 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
       o1[i] = GemmOp{d.V, at, w2o[i], QB2, nt, mp0, d.m, d.ld, QB2, 1, 0, 1.f, 0.f, 0, 0};
       o2[i] = GemmOp{(int64_t)i * QB2 * QB2, w2o[i], w2o[i], QB2, nt, QB2, QB2, QB2, QB2, 1, 0, 1.f, 0.f, 0, 0};
       ou[i] = GemmOp{d.V, w2o[i], at, mp0, nt, QB2, d.m, QB2, d.ld, 0, 0, -1.f, 1.f, 0, 0};
-      fg += 2.0 * QB2 * QB2 * mp0;
-      fa += 4.0 * QB2 * (double)nt * mp0;
     }
     GemmOp* d_ops = nullptr;
     HIF_CUDA_TRY(cudaMallocAsync(&d_ops, sizeof(GemmOp) * 4 * nb, st));
@@ -982,8 +979,6 @@ void reduce_rows_qr(const SkelDesc* h_f, const std::vector<int>& which, T* Garen
     gemm(d_ops + 2 * nb, o2.data(), Tb, W1b, W2b, "id_rowreduce_tw_tc", "id_rowreduce_tw");
     gemm(d_ops + 3 * nb, ou.data(), Var, W2b, Garena, "id_rowreduce_block_tc", "id_rowreduce_block");
     HIF_CUDA_TRY(cudaFreeAsync(d_ops, st));
-    (void)fg;
-    (void)fa;
   }
   if (blocks) {
     HIF_CUDA_TRY(cudaFreeAsync(W2b, st));
